@@ -1,0 +1,21 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA device (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: longer CPU-only statistical checks")
+
+
+@pytest.fixture(scope="session")
+def orc():
+    from oracle import py_oracle
+    py_oracle.build()
+    py_oracle.lib()
+    return py_oracle
