@@ -1,0 +1,314 @@
+"""Benchmark: Wallace pool-regeneration pass at scale on one GB300.
+
+Workload (one step = one pass over the whole pool, all of its steps: strided
+gather, transform, store, exact sum of squares, chi-squared finaliser with
+the next pass's parameter draw, and the returned half of the pool written to
+an output buffer in HBM as N(0,1) values):
+    n = 4, N = 2^24 (pool of 2^26 binary32 values, 256 MiB, double-buffered),
+    A = J/2 - I, seed 7, frac = 1/2 (R = 2^25 values returned per pass).
+
+Prints one JSON line.  `value` is returned N(0,1) variates per second over
+all ranks (each rank runs an independent generator, stream id = rank: weak
+scaling, no data-path collective).  `--impl reference` times the plain-C
+oracle of the same workload on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N(0,1) variates/s, % HBM roofline; batched vs plain pass, oracle bit-exact"
+UNIT = "variates/s"
+N_SUB, N_LEN, SEED, FRAC = 4, 1 << 24, 7, 0.5
+NU = N_SUB * N_LEN
+R = int(FRAC * NU)
+BYTES_PER_PASS = 8 * NU + 4 * R          # pool read + pool write + returned output
+WORKLOAD = (f"Wallace pass, n=4, N=2^24 (2^26-value FP32 pool), A=J/2-I, seed {SEED}, "
+            f"frac=1/2 (R=2^25 returned per pass, mu=0 sigma=1, written to HBM)")
+PROFILE = os.path.join(ROOT, "profiles", "wl_tiled_pass_n4_N2p24.txt")
+KERNEL_SOURCES = ["paper_1004_3114_gb300/csrc/wl_tiled.cu", "paper_1004_3114_gb300/csrc/wl_common.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """dram bytes per launch from the committed ncu summary, if it still
+    describes the current kernel source (else None)."""
+    try:
+        kv = {}
+        with open(PROFILE) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(passes: int):
+    """The oracle as it stands (single thread) on the same workload: creation
+    excluded, then `passes` passes each returning R values."""
+    from oracle import py_oracle as orc
+    g = orc.Generator(N_SUB, N_LEN, SEED, FRAC)
+    import numpy as np
+    out = np.empty(R, dtype=np.float32)
+    t0 = time.perf_counter()
+    for _ in range(passes):
+        orc.lib().orc_fill32(g._h, out, R, np.float32(0.0), np.float32(1.0))
+    dt = time.perf_counter() - t0
+    g.close()
+    return passes * R / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    warm, steps = max(args.warmup, 0), max(args.steps, 1)
+    from oracle import py_oracle as orc
+    import numpy as np
+    g = orc.Generator(N_SUB, N_LEN, SEED, FRAC)
+    out = np.empty(R, dtype=np.float32)
+    for _ in range(warm):
+        orc.lib().orc_fill32(g._h, out, R, np.float32(0.0), np.float32(1.0))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        orc.lib().orc_fill32(g._h, out, R, np.float32(0.0), np.float32(1.0))
+    dt = time.perf_counter() - t0
+    value = steps * R / dt
+    sample = f"{steps} full oracle passes of the workload (creation excluded), 1 thread"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * dt / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded generator state; no dataset)",
+        "config": {"workload": WORKLOAD, "n": N_SUB, "N": N_LEN, "frac": FRAC,
+                   "returned_per_step": R, "oracle": "plain C, FP32 mode, gcc -O2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1004_3114_gb300 import wallace as W
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=dev)
+
+    stream = torch.cuda.Stream(device=dev)
+    g = W.Wallace(N_SUB, N_LEN, SEED, FRAC, stream_id=rank, stream=stream)
+    out = torch.empty(R, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            g.fill(out)
+    g.sync()
+    torch.cuda.synchronize()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    g.set_timing(True)
+    st0 = g.stats()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clocks:
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.steps):
+                g.fill(out)
+            ev1.record(stream)
+        ev1.synchronize()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    st1 = g.stats()
+    g.set_timing(False)
+    launches = st1.kernel_launches - st0.kernel_launches
+    kernel_ms = (st1.kernel_ms - st0.kernel_ms) / max(launches, 1)
+    status = g.sync()
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI into pinned HOST memory (D2H inside the timed region)
+    host = torch.empty(R, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    g.fill_host(host)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.fill_host(host)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # plain strided-gather pass on the same pool, for comparison
+    cmp = {}
+    if rank == 0 and not args.no_compare:
+        g.set_variant(W.VARIANT_GATHER)
+        g.set_timing(True)
+        s0 = g.stats()
+        with torch.cuda.stream(stream):
+            for _ in range(10):
+                g.fill(out)
+        s1 = g.stats()
+        g.set_variant(W.VARIANT_AUTO)
+        gms = (s1.kernel_ms - s0.kernel_ms) / max(s1.kernel_launches - s0.kernel_launches, 1)
+        cmp = {"plain_gather_pass_ms": gms,
+               "plain_gather_GBps": BYTES_PER_PASS / (gms * 1e-3) / 1e9}
+    g.close()
+
+    if rank == 0:
+        peak, peak_kind = hbm_peak()
+        achieved = BYTES_PER_PASS / (kernel_ms * 1e-3) / 1e9
+        value = world * args.steps * R / (ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded generator state; no dataset)",
+            "config": {"workload": WORKLOAD, "n": N_SUB, "N": N_LEN, "frac": FRAC,
+                       "returned_per_step": R, "passes_per_step": 1,
+                       "parallelism": f"{world} independent generator(s), stream id = rank",
+                       "l2": "inputs larger than L2: 2 x 256 MiB pools + 128 MiB output"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": profiled_traffic(), "kernel": "wl_tiled pass",
+                         "kernel_ms": kernel_ms, "algorithmic_bytes_per_launch": BYTES_PER_PASS},
+            "e2e": {"value": world * e2e_steps * R / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * R},
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+            "status": int(status),
+        }
+        if cmp:
+            line["compare"] = cmp
+        if not args.no_cpu_baseline:
+            v, dt = cpu_baseline(args.cpu_passes)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"{args.cpu_passes} oracle passes of the same "
+                                              f"workload ({dt:.1f} s, creation excluded)"}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-passes", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * wallace.h -- C ABI of a GB300 (sm_103a) implementation of Wallace's normal
+ * random number generator in the vectorised form of Brent's RANN4
+ * (R. P. Brent, "A fast vectorised implementation of Wallace's normal random
+ * number generator", 1997).
+ *
+ * One generator ("handle") keeps a pool of nu = n*N binary32 normal variates
+ * in device memory, viewed as n sub-vectors of length N (Section 2).  A pass
+ * (Section 2, footnote: "the process of regenerating the pool") replaces the
+ * pool with
+ *     x'_i[j] = c * ((2/n) * sum_k g_k - g_i),   g_k = x_k[(alpha_k j + gamma_k) mod N]
+ * for j = 0..N-1 (Eq. 1 with A = (2/n)J - I, n in {4, 8}), where the strides
+ * alpha_k and offsets gamma_k are redrawn every pass from the generator's own
+ * uniform source (Sections 3, 7, 8; gcd rule Eq. 2) and c rescales the pool's
+ * sum of squares to a chi-squared sample (Section 4, Eq. 3).  Of each new pool
+ * the first R = min(floor(frac*nu), nu-1) values are returned to the user
+ * (Section 6, throw-away factor f = 1/frac); the last value is never returned.
+ *
+ * Conventions for every call:
+ *   - All compute runs in CUDA kernels on the handle's stream (default: the
+ *     legacy default stream; see wallace_set_stream).  Calls are asynchronous
+ *     unless stated otherwise.
+ *   - Pointers documented as "device" must point to device memory of the
+ *     device that was current when the handle was created, be aligned to
+ *     their element size, and stay valid until the work on the handle's
+ *     stream that uses them has completed.  The caller owns them.
+ *   - Return value: WALLACE_OK (0) or a positive status.  Status bits found on
+ *     the device (WALLACE_ECORRUPT) are sticky and surface at the next call
+ *     that synchronises (wallace_sync, wallace_stats, wallace_get_pool*);
+ *     they stay set until wallace_clear_error.  A failed CUDA call sets
+ *     WALLACE_ECUDA, also sticky.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef WALLACE_H
+#define WALLACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wallace wallace_t;
+
+/* status codes (bit flags; a call may return several OR-ed together) */
+#define WALLACE_OK        0
+#define WALLACE_EINVAL    1   /* an argument is out of range                      */
+#define WALLACE_ENOMEM    2   /* device or host allocation failed                 */
+#define WALLACE_ECORRUPT  4   /* sum-of-squares monitor tripped (Section 8)       */
+#define WALLACE_ECUDA     8   /* a CUDA runtime call failed                       */
+#define WALLACE_ETIMEOUT 16   /* a bounded device-side wait gave up               */
+#define WALLACE_ESTATE   32   /* call not valid in the handle's current mode      */
+
+/* pool precision */
+#define WALLACE_FP32      0   /* binary32 pool; exact integer sum of squares, binary64 scale */
+#define WALLACE_FP64POOL  1   /* binary64 pool (reference mode for precision studies)        */
+
+/* pass kernel selection (wallace_set_variant) */
+#define WALLACE_VARIANT_AUTO    0  /* pick by pool size                                 */
+#define WALLACE_VARIANT_GATHER  1  /* direct strided gather from HBM, one pass/launch   */
+#define WALLACE_VARIANT_TILED   2  /* lane-tiled gather staged in shared memory         */
+#define WALLACE_VARIANT_FUSED   3  /* whole pool in shared memory, many passes/launch   */
+
+/* Scalars of the most recent pass (or of the initial pool after create). */
+typedef struct {
+    uint64_t q_lo, q_hi;  /* exact sum-of-squares integer Q (128-bit): sum floor(y^2 2^32)
+                             (FP32) or sum floor(fl(y*y) 2^64) (FP64POOL)                */
+    double q;             /* Q as a real sum of squares                                  */
+    double S;             /* chi-squared target from the withheld value (Eq. 3)          */
+    double c;             /* scale the next pass applies, sqrt(S/q)                      */
+    float c32;            /* c rounded to binary32                                       */
+    double drift;         /* q_k / S_{k-1} - 1 (0 for the initial pool)                  */
+    int64_t passes;       /* passes completed                                            */
+    int32_t status;       /* sticky WALLACE_* bits                                       */
+    int32_t bad;          /* a pool value was non-finite or |y| >= 256                   */
+    uint64_t lcg;         /* uniform generator state after the last draw                 */
+    int32_t alpha[8];     /* strides of the most recent pass                             */
+    int64_t gamma[8];     /* offsets of the most recent pass                             */
+    int64_t R;            /* values returned per pass                                    */
+    int64_t cursor;       /* index in the current pool of the next value to return       */
+    double kernel_ms;     /* summed pass-kernel time when timing is on                   */
+    int64_t kernel_launches; /* pass kernels timed                                       */
+} wallace_stats_t;
+
+/*
+ * wallace_create -- make a generator and its initial pool.
+ *   n      sub-vectors per pool, 4 or 8 (A = (2/n)J - I; Section 2, Section 9)
+ *   N      sub-vector length, 4 <= N and n*N <= 2^30 (Section 2: pool of nN)
+ *   seed   32-bit seed of the uniform source (Section 8)
+ *   frac   returned fraction 1/f, 0 < frac <= 1 (Section 6); R must be >= 1
+ *   out    receives the handle
+ * The initial pool is filled on the device by Box-Muller from the uniform
+ * source (Sections 5 and 8) and is not itself returned; its last value sets
+ * the first chi-squared target (Eq. 3).  Allocates 2*n*round_up(N,64)
+ * elements of device memory plus a small state block.
+ * Errors: WALLACE_EINVAL (bad n, N, frac), WALLACE_ENOMEM, WALLACE_ECUDA.
+ */
+int wallace_create(int n, int64_t N, uint32_t seed, double frac, wallace_t **out);
+
+/*
+ * wallace_create_ex -- as wallace_create, plus:
+ *   stream_id  appended to the seed (Section 8: DP_VRANU4 appends the
+ *              processor number so that processors get different sequences)
+ *   mode       WALLACE_FP32 or WALLACE_FP64POOL
+ *   cuda_stream  cudaStream_t to run on (NULL: legacy default stream)
+ */
+int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, double frac,
+                      int mode, void *cuda_stream, wallace_t **out);
+
+/* wallace_destroy -- synchronise the handle's stream and free everything. NULL-safe. */
+void wallace_destroy(wallace_t *h);
+
+/*
+ * wallace_pass -- advance one pass (Section 2, Eq. 1; Section 4, Eq. 3).
+ * The R returned values of the new pool become the next values that
+ * wallace_fill hands out; any values of the previous pool not yet handed
+ * out are skipped.  Asynchronous.
+ */
+int wallace_pass(wallace_t *h);
+
+/*
+ * wallace_fill -- write the next `count` values of the returned stream,
+ * mapped to N(mu, sigma^2) as mu + sigma*y (binary32 multiply, then add;
+ * Section 7 and Section 8: size, mean and variance may change every call).
+ *   out    device pointer to `count` floats (caller-owned)
+ * Runs as many passes as needed; each pass writes its returned prefix
+ * straight into `out` from the pass kernel.  Splitting a request into several
+ * calls yields the same stream.  FP32 mode only (WALLACE_ESTATE otherwise).
+ * Asynchronous.
+ */
+int wallace_fill(wallace_t *h, float *out, int64_t count, float mu, float sigma);
+
+/* wallace_fill64 -- as wallace_fill for a WALLACE_FP64POOL handle; binary64 out. */
+int wallace_fill64(wallace_t *h, double *out, int64_t count, double mu, double sigma);
+
+/*
+ * wallace_fill_host -- as wallace_fill, but `host_out` is a HOST pointer to
+ * `count` floats.  The values are produced on the device in chunks and
+ * copied back while the next chunk is generated.  Page-locked memory gives
+ * asynchronous copies; pageable memory works but is slower.  Synchronous:
+ * returns when all values are in host memory.
+ */
+int wallace_fill_host(wallace_t *h, float *host_out, int64_t count, float mu, float sigma);
+
+/* wallace_set_stream -- run subsequent work on `cuda_stream` (a cudaStream_t). */
+int wallace_set_stream(wallace_t *h, void *cuda_stream);
+
+/* wallace_set_variant -- choose the pass kernel (WALLACE_VARIANT_*); all
+ * variants produce bit-identical pools.  EINVAL for an unknown variant or a
+ * FUSED request on a pool too large for shared memory. */
+int wallace_set_variant(wallace_t *h, int variant);
+
+/* wallace_set_timing -- when on, every pass kernel is bracketed by CUDA
+ * events on the handle's stream; the summed time appears in kernel_ms. */
+int wallace_set_timing(wallace_t *h, int on);
+
+/* wallace_sync -- wait for the handle's stream; returns the sticky status. */
+int wallace_sync(wallace_t *h);
+
+/* wallace_stats -- synchronise and copy the scalars of the last pass. */
+int wallace_stats(wallace_t *h, wallace_stats_t *out);
+
+/*
+ * wallace_get_pool -- synchronise and copy the current pool to HOST memory
+ * `host_out` (nu floats, sub-vector-major: x_0[0..N-1], x_1[0..N-1], ...).
+ * In FP64POOL mode each value is rounded to binary32.
+ */
+int wallace_get_pool(wallace_t *h, float *host_out);
+
+/* wallace_get_pool64 -- as wallace_get_pool into nu doubles (exact in both modes). */
+int wallace_get_pool64(wallace_t *h, double *host_out);
+
+/*
+ * wallace_set_pool -- overwrite the current pool from HOST memory (nu floats,
+ * same layout).  Models a caller who writes over the work area; the next
+ * pass's sum-of-squares check (Section 8) then reports WALLACE_ECORRUPT.
+ */
+int wallace_set_pool(wallace_t *h, const float *host_in);
+
+/* wallace_clear_error -- reset the sticky status bits. */
+int wallace_clear_error(wallace_t *h);
+
+/* wallace_returned_per_pass -- R for the handle (host value, no sync). */
+int64_t wallace_returned_per_pass(const wallace_t *h);
+
+/* wallace_strerror -- static text for a status code (lowest set bit). */
+const char *wallace_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WALLACE_H */

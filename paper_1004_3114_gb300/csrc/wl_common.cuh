@@ -1,0 +1,345 @@
+// Device-side building blocks shared by the kernels of the Wallace generator
+// (Brent, "A fast vectorised implementation of Wallace's normal random
+// number generator", 1997): per-generator device state, the uniform source,
+// per-pass parameter draw, sum-of-squares terms and reductions, and the
+// end-of-pass finaliser (chi-squared rescale, Eq. 3, and drift monitor).
+//
+// Every floating-point operation whose result reaches the pool is written
+// with an explicit IEEE round-to-nearest intrinsic (__fadd_rn, __dmul_rn, ...)
+// so the compiler can neither contract nor reorder it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define WL_OK 0
+#define WL_ECORRUPT 4
+#define WL_ETIMEOUT 16
+
+// Parameters of one pass (Eq. 1): strides alpha_i and offsets gamma_i, and
+// the scale c folded into A (Section 4).
+struct WlParams {
+    int32_t alpha[8];
+    int64_t gamma[8];
+    float c32;
+    float pad_;
+    double c64;
+};
+
+// One generator's device state.  The finaliser of a pass writes `next`;
+// the following pass reads it.  The accumulators are zero between passes.
+struct WlDevState {
+    WlParams next;          // parameters for the next pass
+    WlParams last;          // parameters the most recent pass used
+    uint64_t lcg;           // uniform generator state
+    uint64_t acc_lo;        // running Q of the pass in flight (128-bit)
+    uint64_t acc_hi;
+    uint32_t acc_bad;       // a value was non-finite or |y| >= 256
+    uint32_t ticket;        // CTAs finished in the pass in flight
+    uint64_t q_lo, q_hi;    // Q of the most recent pool
+    double q, S, S_prev, c, drift;
+    int32_t have_prev;
+    int32_t status;         // sticky WL_* bits
+    int32_t bad;
+    int32_t pad_;
+    int64_t passes;
+};
+
+// ---- uniform source --------------------------------------------------------
+// 64-bit LCG with Knuth's MMIX multiplier and increment, top 32 bits returned;
+// seeded through SplitMix64 (Steele, Lea, Flood 2014) of (stream<<32 | seed).
+#define WL_LCG_A 6364136223846793005ull
+#define WL_LCG_C 1442695040888963407ull
+
+__device__ __forceinline__ uint32_t wl_lcg_step(uint64_t &s)
+{
+    s = s * WL_LCG_A + WL_LCG_C;
+    return (uint32_t)(s >> 32);
+}
+
+__device__ __forceinline__ uint64_t wl_seed_mix(uint32_t seed, uint32_t stream)
+{
+    uint64_t z = (((uint64_t)stream << 32) | (uint64_t)seed) + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// State after m steps, by composing the affine map s -> a s + c with itself
+// (binary powering; F. B. Brown, "Random number generation with arbitrary
+// strides", 1994).
+__device__ __forceinline__ uint64_t wl_lcg_jump(uint64_t s, uint64_t m)
+{
+    uint64_t A = 1, C = 0, ap = WL_LCG_A, cp = WL_LCG_C;
+    while (m) {
+        if (m & 1) {
+            A = ap * A;
+            C = ap * C + cp;
+        }
+        cp = ap * cp + cp;
+        ap = ap * ap;
+        m >>= 1;
+    }
+    return A * s + C;
+}
+
+// ---- per-pass parameters ---------------------------------------------------
+// Strides are distinct, odd, > 1 and coprime to N (Eq. 2, Sections 3 and 7);
+// row i of the table offers two choices picked by the top bit of one uniform
+// (RANN4 picks from {3,5} and {7,11}, Section 8).  Rows 0-3 divide 315 and
+// rows 4-7 divide 3465, which bounds the lane count of the tiled kernel.
+// Fallbacks: the row's other entry, then the smallest free odd number > 1
+// coprime to N.  The offset is floor(U N / 2^32), uniform on {0..N-1}.
+__device__ __forceinline__ int64_t wl_gcd(int64_t a, int64_t b)
+{
+    while (b) {
+        int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+__device__ __forceinline__ bool wl_stride_free(int32_t a, int64_t N, const int32_t *used, int k)
+{
+    if (wl_gcd(a, N) != 1)
+        return false;
+    for (int t = 0; t < k; t++)
+        if (used[t] == a)
+            return false;
+    return true;
+}
+
+__device__ inline void wl_draw_params(int n, int64_t N, uint64_t &s, int32_t *alpha, int64_t *gamma)
+{
+    const int32_t tab[8][2] = {{3, 5}, {7, 9}, {15, 21}, {35, 45},
+                               {11, 33}, {55, 77}, {99, 165}, {231, 385}};
+    for (int i = 0; i < n; i++) {
+        uint32_t pick = wl_lcg_step(s) >> 31;
+        int32_t a = tab[i][pick];
+        if (!wl_stride_free(a, N, alpha, i)) {
+            a = tab[i][1 - pick];
+            if (!wl_stride_free(a, N, alpha, i)) {
+                a = 3;
+                while (!wl_stride_free(a, N, alpha, i))
+                    a += 2;
+            }
+        }
+        alpha[i] = a;
+        uint32_t u = wl_lcg_step(s);
+        gamma[i] = (int64_t)(((uint64_t)u * (uint64_t)N) >> 32);
+    }
+}
+
+// ---- the transform (Section 2; A = (2/n)J - I, scaled by c) ----------------
+__device__ __forceinline__ void wl_xform4(const float *g, float c, float *y)
+{
+    float s = __fadd_rn(__fadd_rn(g[0], g[1]), __fadd_rn(g[2], g[3]));
+    float h = __fmul_rn(s, 0.5f);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        y[k] = __fmul_rn(__fsub_rn(h, g[k]), c);
+}
+
+__device__ __forceinline__ void wl_xform8(const float *g, float c, float *y)
+{
+    float ab = __fadd_rn(__fadd_rn(g[0], g[1]), __fadd_rn(g[2], g[3]));
+    float de = __fadd_rn(__fadd_rn(g[4], g[5]), __fadd_rn(g[6], g[7]));
+    float h = __fmul_rn(__fadd_rn(ab, de), 0.25f);
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+        y[k] = __fmul_rn(__fsub_rn(h, g[k]), c);
+}
+
+__device__ __forceinline__ void wl_xform4d(const double *g, double c, double *y)
+{
+    double s = __dadd_rn(__dadd_rn(g[0], g[1]), __dadd_rn(g[2], g[3]));
+    double h = __dmul_rn(s, 0.5);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        y[k] = __dmul_rn(__dsub_rn(h, g[k]), c);
+}
+
+__device__ __forceinline__ void wl_xform8d(const double *g, double c, double *y)
+{
+    double ab = __dadd_rn(__dadd_rn(g[0], g[1]), __dadd_rn(g[2], g[3]));
+    double de = __dadd_rn(__dadd_rn(g[4], g[5]), __dadd_rn(g[6], g[7]));
+    double h = __dmul_rn(__dadd_rn(ab, de), 0.25);
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+        y[k] = __dmul_rn(__dsub_rn(h, g[k]), c);
+}
+
+// ---- sum of squares (Section 4; Section 8 drift monitor) -------------------
+// Binary32 pool: term = floor(y^2 2^32), computed exactly in integers from the
+// significand m and exponent: y = m 2^(e-150) so y^2 2^32 = m^2 2^(2e-268).
+// |y| >= 256 (exponent field >= 135, including Inf/NaN) flags the pool.
+__device__ __forceinline__ uint64_t wl_term32(float y, uint32_t &bad)
+{
+    uint32_t u = __float_as_uint(y) & 0x7fffffffu;
+    uint32_t e = u >> 23;
+    bad |= (e >= 135u);
+    uint32_t m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
+    uint32_t ee = e ? e : 1u;
+    uint32_t rs = 268u - 2u * ee;          // >= 0 for e <= 134
+    uint64_t sq = (uint64_t)m * (uint64_t)m;
+    uint64_t t = (rs < 64u) ? (sq >> rs) : 0ull;
+    return (e >= 135u) ? 0ull : t;
+}
+
+// Binary64 pool: term = floor(fl(y*y) 2^64) as a 128-bit integer.
+__device__ __forceinline__ void wl_term64(double y, uint64_t &lo, uint64_t &hi, uint32_t &bad)
+{
+    lo = 0;
+    hi = 0;
+    if (!(fabs(y) < 256.0)) {
+        bad = 1;
+        return;
+    }
+    double t = __dmul_rn(y, y);
+    uint64_t u = (uint64_t)__double_as_longlong(t);
+    int e = (int)((u >> 52) & 0x7ff);
+    uint64_t m = (u & ((1ull << 52) - 1)) | (e ? (1ull << 52) : 0ull);
+    int sh = (e ? e : 1) - 1075 + 64;      // t 2^64 = m 2^sh
+    if (sh >= 0) {
+        lo = m << sh;
+        hi = sh ? (m >> (64 - sh)) : 0ull;
+    } else if (sh > -64) {
+        lo = m >> (-sh);
+    }
+}
+
+__device__ __forceinline__ void wl_add128(uint64_t &lo, uint64_t &hi, uint64_t alo, uint64_t ahi)
+{
+    uint64_t r = lo + alo;
+    hi += ahi + (r < lo ? 1ull : 0ull);
+    lo = r;
+}
+
+// Warp, then CTA, then device reduction of a 128-bit sum and the bad flag
+// into the state accumulators.  Integer sums: independent of order.
+// Must be called by every thread of the CTA; `red` holds 3 * (warps) words.
+__device__ __forceinline__ void wl_cta_reduce_to_state(uint64_t lo, uint64_t hi, uint32_t bad,
+                                                       WlDevState *st, uint64_t *red)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        uint64_t olo = __shfl_down_sync(0xffffffffu, lo, off);
+        uint64_t ohi = __shfl_down_sync(0xffffffffu, hi, off);
+        wl_add128(lo, hi, olo, ohi);
+    }
+    bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        red[warp] = lo;
+        red[nw + warp] = hi;
+        red[2 * nw + warp] = bad;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        lo = lane < nw ? red[lane] : 0ull;
+        hi = lane < nw ? red[nw + lane] : 0ull;
+        bad = lane < nw ? (uint32_t)red[2 * nw + lane] : 0u;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            uint64_t olo = __shfl_down_sync(0xffffffffu, lo, off);
+            uint64_t ohi = __shfl_down_sync(0xffffffffu, hi, off);
+            wl_add128(lo, hi, olo, ohi);
+        }
+        bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
+        if (lane == 0) {
+            unsigned long long old = atomicAdd((unsigned long long *)&st->acc_lo,
+                                               (unsigned long long)lo);
+            uint64_t carry = ((uint64_t)old + lo < (uint64_t)old) ? 1ull : 0ull;
+            if (hi + carry)
+                atomicAdd((unsigned long long *)&st->acc_hi, (unsigned long long)(hi + carry));
+            if (bad)
+                atomicOr(&st->acc_bad, 1u);
+        }
+    }
+}
+
+// ---- end of pass: chi-squared rescale (Eq. 3) and drift monitor ------------
+// One thread.  x is the withheld last value of the new pool; with
+// r = sqrt(2 nu - 1), S = (x + r)^2 / 2; the next pass scales A by
+// c = sqrt(S / q).  q / S_prev - 1 beyond 1e-3 means the pool was overwritten
+// (Section 8).  Then the next pass's parameters are drawn.
+__device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu, double x,
+                                   bool fp64, bool is_pass)
+{
+    volatile WlDevState *vs = st;
+    uint64_t lo = vs->acc_lo, hi = vs->acc_hi;
+    uint32_t bad = vs->acc_bad;
+    double q;
+    if (!fp64) {
+        q = __dmul_rn(__ull2double_rn(lo), 1.0 / 4294967296.0);
+        if (hi != 0)
+            bad = 1;
+    } else {
+        q = __dadd_rn(__ull2double_rn(hi), __dmul_rn(__ull2double_rn(lo), 1.0 / 18446744073709551616.0));
+    }
+    double r = __dsqrt_rn(__dsub_rn(__dmul_rn(2.0, (double)nu), 1.0));
+    double xr = __dadd_rn(x, r);
+    double S = __dmul_rn(__dmul_rn(xr, xr), 0.5);
+    double c = 1.0;
+    int32_t status = st->status;
+    if (bad || !(q > 0.0))
+        status |= WL_ECORRUPT;
+    else
+        c = __dsqrt_rn(__ddiv_rn(S, q));
+    double drift = 0.0;
+    if (st->have_prev) {
+        drift = __dsub_rn(__ddiv_rn(q, st->S_prev), 1.0);
+        if (!(fabs(drift) <= 1e-3))
+            status |= WL_ECORRUPT;
+    }
+    st->S_prev = S;
+    st->have_prev = 1;
+    st->q_lo = lo;
+    st->q_hi = hi;
+    st->q = q;
+    st->S = S;
+    st->c = c;
+    st->drift = drift;
+    st->bad = (int32_t)bad;
+    st->status = status;
+    if (is_pass) {
+        st->last = st->next;
+        st->passes += 1;
+    }
+    st->next.c64 = c;
+    st->next.c32 = __double2float_rn(c);
+    uint64_t s = st->lcg;
+    wl_draw_params(n, N, s, st->next.alpha, st->next.gamma);
+    st->lcg = s;
+    st->acc_lo = 0;
+    st->acc_hi = 0;
+    st->acc_bad = 0;
+    __threadfence();
+    st->ticket = 0;
+}
+
+// Last-CTA detection: every thread fences its global writes, then one thread
+// takes a ticket; the CTA that draws the last ticket runs the finaliser.
+__device__ __forceinline__ bool wl_last_cta(WlDevState *st)
+{
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(&st->ticket, 1u);
+        s_last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
+    }
+    __syncthreads();
+    if (s_last)
+        __threadfence();
+    return s_last;
+}
+
+// physical offset of logical pool index q (sub-vector-major, row pitch Np)
+__device__ __forceinline__ int64_t wl_phys(int64_t q, int64_t N, int64_t Np)
+{
+    int64_t i = q / N;
+    return i * Np + (q - i * N);
+}

@@ -1,0 +1,167 @@
+// Many passes of Wallace's generator in one launch for a pool that fits in
+// shared memory (Brent's RANN4 paper, Section 2: a pass is a few vector
+// operations over the pool; here the pool never leaves the SM between
+// passes, only the returned values go to global memory).
+//
+// One CTA owns the generator.  Per pass: thread 0 already holds the pass's
+// strides, offsets and scale in the state (drawn by the previous
+// finaliser); all threads gather from one shared buffer into the other
+// (Eq. 1), accumulate the exact sum of squares, and write the returned prefix;
+// thread 0 then runs the chi-squared rescale (Eq. 3) and drift check and draws
+// the next parameters.  At the end the pool is written back to global memory.
+#include "wl_common.cuh"
+#include "wl_launch.h"
+
+#define FU_THREADS 512
+#define FU_SMEM_MAX (220 * 1024)
+
+namespace {
+
+template <int NSUB, typename T>
+__global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout, int64_t N,
+                                                          int64_t Np, WlDevState *st,
+                                                          int64_t passes, int64_t R,
+                                                          int64_t last_take, T *__restrict__ out,
+                                                          double mu_d, double sigma_d)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    __shared__ uint64_t red[3 * (FU_THREADS / 32)];
+    __shared__ int32_t s_alpha[NSUB];
+    __shared__ int32_t s_gamma[NSUB];
+    __shared__ T s_c;
+    const int tid = threadIdx.x;
+    const int nu = NSUB * (int)N;
+    T *buf0 = (T *)fsm;
+    T *buf1 = buf0 + nu;
+    for (int q = tid; q < nu; q += FU_THREADS) {
+        int i = q / (int)N;
+        buf0[q] = gin[(int64_t)i * Np + (q - i * (int)N)];
+    }
+    const T mu = (T)mu_d, sigma = (T)sigma_d;
+    T *src = buf0, *dst = buf1;
+    for (int64_t pass = 0; pass < passes; pass++) {
+        if (tid == 0) {
+            for (int i = 0; i < NSUB; i++) {
+                s_alpha[i] = st->next.alpha[i];
+                s_gamma[i] = (int32_t)st->next.gamma[i];
+            }
+            if constexpr (sizeof(T) == 8)
+                s_c = st->next.c64;
+            else
+                s_c = st->next.c32;
+        }
+        __syncthreads();
+        const T c = s_c;
+        const int take = (int)(pass + 1 < passes ? R : last_take);
+        T *o = out + pass * R;
+        int idx[NSUB], stp[NSUB];
+#pragma unroll
+        for (int i = 0; i < NSUB; i++) {
+            idx[i] = (int)(((int64_t)s_alpha[i] * (tid < N ? tid : 0) + s_gamma[i]) % N);
+            stp[i] = (int)(((int64_t)s_alpha[i] * FU_THREADS) % N);
+        }
+        uint64_t lo = 0, hi = 0;
+        uint32_t bad = 0;
+        for (int j = tid; j < (int)N; j += FU_THREADS) {
+            T g[NSUB], y[NSUB];
+#pragma unroll
+            for (int i = 0; i < NSUB; i++) {
+                g[i] = src[i * (int)N + idx[i]];
+                idx[i] += stp[i];
+                if (idx[i] >= (int)N)
+                    idx[i] -= (int)N;
+            }
+            if constexpr (sizeof(T) == 8) {
+                if constexpr (NSUB == 4)
+                    wl_xform4d(g, c, y);
+                else
+                    wl_xform8d(g, c, y);
+            } else {
+                if constexpr (NSUB == 4)
+                    wl_xform4(g, c, y);
+                else
+                    wl_xform8(g, c, y);
+            }
+#pragma unroll
+            for (int k = 0; k < NSUB; k++) {
+                int q = k * (int)N + j;
+                dst[q] = y[k];
+                if constexpr (sizeof(T) == 8) {
+                    uint64_t tl, th;
+                    wl_term64(y[k], tl, th, bad);
+                    wl_add128(lo, hi, tl, th);
+                    if (q < take)
+                        o[q] = __dadd_rn(mu, __dmul_rn(sigma, y[k]));
+                } else {
+                    wl_add128(lo, hi, wl_term32(y[k], bad), 0);
+                    if (q < take)
+                        o[q] = __fadd_rn(mu, __fmul_rn(sigma, y[k]));
+                }
+            }
+        }
+        wl_cta_reduce_to_state(lo, hi, bad, st, red);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence_block();
+            wl_finalise(st, NSUB, N, (int64_t)nu, (double)dst[nu - 1], sizeof(T) == 8, true);
+        }
+        __syncthreads();
+        T *t = src;
+        src = dst;
+        dst = t;
+    }
+    for (int q = tid; q < nu; q += FU_THREADS) {
+        int i = q / (int)N;
+        gout[(int64_t)i * Np + (q - i * (int)N)] = src[q];
+    }
+}
+
+template <int NSUB, typename T>
+cudaError_t launch_one(void *pin, void *pout, int64_t N, int64_t Np, WlDevState *st, int64_t passes,
+                       int64_t R, int64_t last_take, void *out, double mu, double sigma,
+                       cudaStream_t stream)
+{
+    static bool configured = false;
+    const size_t smem = 2 * sizeof(T) * (size_t)NSUB * (size_t)N;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(fused_kernel<NSUB, T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             FU_SMEM_MAX);
+        if (e != cudaSuccess)
+            return e;
+        configured = true;
+    }
+    fused_kernel<NSUB, T><<<1, FU_THREADS, smem, stream>>>((const T *)pin, (T *)pout, N, Np, st,
+                                                          passes, R, last_take, (T *)out, mu,
+                                                          sigma);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+bool wl_fused_supported(int n, int64_t N, int fp64, int64_t *smem_bytes)
+{
+    int64_t bytes = 2 * (fp64 ? 8 : 4) * (int64_t)n * N;
+    if (smem_bytes)
+        *smem_bytes = bytes;
+    return (n == 4 || n == 8) && N >= 4 && bytes <= FU_SMEM_MAX;
+}
+
+cudaError_t wl_launch_fused(void *pool_cur, void *pool_other, int fp64, int n, int64_t N,
+                            int64_t Np, WlDevState *st, int64_t passes, int64_t R,
+                            int64_t last_take, void *out, double mu, double sigma,
+                            cudaStream_t stream)
+{
+    (void)pool_other;
+    if (passes <= 0)
+        return cudaSuccess;
+    if (n == 4)
+        return fp64 ? launch_one<4, double>(pool_cur, pool_cur, N, Np, st, passes, R, last_take,
+                                            out, mu, sigma, stream)
+                    : launch_one<4, float>(pool_cur, pool_cur, N, Np, st, passes, R, last_take,
+                                           out, mu, sigma, stream);
+    return fp64 ? launch_one<8, double>(pool_cur, pool_cur, N, Np, st, passes, R, last_take, out,
+                                        mu, sigma, stream)
+                : launch_one<8, float>(pool_cur, pool_cur, N, Np, st, passes, R, last_take, out,
+                                       mu, sigma, stream);
+}

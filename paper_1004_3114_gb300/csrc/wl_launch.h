@@ -1,0 +1,46 @@
+// Host-side launchers of the Wallace generator kernels (internal to the
+// library; the public interface is include/wallace.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+struct WlDevState;
+
+// Arguments of one pass.  Pools hold n sub-vectors of length N at row pitch
+// Np elements.  Pool values with logical index q in [w0, w1) are also written,
+// mapped to mu + sigma*y, to out[q - w0] (the returned prefix of the pass).
+struct WlPassArgs {
+    const void *src;
+    void *dst;
+    int n;
+    int64_t N, Np, nu;
+    WlDevState *st;
+    void *out;
+    int64_t w0, w1;
+    double mu, sigma;
+};
+
+cudaError_t wl_launch_init(void *pool, int fp64, int n, int64_t N, int64_t Np, uint32_t seed,
+                           uint32_t stream_id, WlDevState *st, int sm_count, cudaStream_t stream);
+
+// direct strided gather from global memory, any n, N, either precision
+cudaError_t wl_launch_gather(const WlPassArgs &a, int fp64, int sm_count, cudaStream_t stream);
+
+// out[k] = mu + sigma * pool[pos + k], k < count (values already produced)
+cudaError_t wl_launch_drain(const void *pool, int fp64, int64_t N, int64_t Np, int64_t pos,
+                            int64_t count, void *out, double mu, double sigma, int sm_count,
+                            cudaStream_t stream);
+
+// lane-tiled gather staged through shared memory (binary32, n = 4)
+bool wl_tiled_supported(int n, int64_t N, int fp64);
+cudaError_t wl_launch_tiled(const WlPassArgs &a, int sm_count, cudaStream_t stream);
+
+// whole pool resident in shared memory for `passes` passes in one launch.
+// Pass k (0-based) writes its values [0, take_k) to out + out_off_k where
+// take_k = R for k < passes-1 and last_take for the final pass.
+bool wl_fused_supported(int n, int64_t N, int fp64, int64_t *smem_bytes);
+cudaError_t wl_launch_fused(void *pool_cur, void *pool_other, int fp64, int n, int64_t N,
+                            int64_t Np, WlDevState *st, int64_t passes, int64_t R,
+                            int64_t last_take, void *out, double mu, double sigma,
+                            cudaStream_t stream);

@@ -1,0 +1,193 @@
+"""Python binding of libwallace.so (include/wallace.h), names as in the C ABI.
+
+Argument marshalling only: every step of the generator runs in the library's
+CUDA kernels.  Device buffers are torch tensors (their data_ptr is passed),
+and the handle runs on the caller's current torch CUDA stream unless another
+stream is given.  Importing this module raises if the library is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libwallace.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "wallace.h")
+
+OK, EINVAL, ENOMEM, ECORRUPT, ECUDA, ETIMEOUT, ESTATE = 0, 1, 2, 4, 8, 16, 32
+FP32, FP64POOL = 0, 1
+VARIANT_AUTO, VARIANT_GATHER, VARIANT_TILED, VARIANT_FUSED = 0, 1, 2, 3
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("q_lo", C.c_uint64), ("q_hi", C.c_uint64), ("q", C.c_double), ("S", C.c_double),
+        ("c", C.c_double), ("c32", C.c_float), ("drift", C.c_double), ("passes", C.c_int64),
+        ("status", C.c_int32), ("bad", C.c_int32), ("lcg", C.c_uint64),
+        ("alpha", C.c_int32 * 8), ("gamma", C.c_int64 * 8), ("R", C.c_int64),
+        ("cursor", C.c_int64), ("kernel_ms", C.c_double), ("kernel_launches", C.c_int64),
+    ]
+
+    @property
+    def Q(self) -> int:
+        return (int(self.q_hi) << 64) | int(self.q_lo)
+
+
+_lib = C.CDLL(LIB_PATH)
+_h = C.c_void_p
+_SIGS = {
+    "wallace_create": (C.c_int, [C.c_int, C.c_int64, C.c_uint32, C.c_double, C.POINTER(_h)]),
+    "wallace_create_ex": (C.c_int, [C.c_int, C.c_int64, C.c_uint32, C.c_uint32, C.c_double,
+                                    C.c_int, C.c_void_p, C.POINTER(_h)]),
+    "wallace_destroy": (None, [_h]),
+    "wallace_pass": (C.c_int, [_h]),
+    "wallace_fill": (C.c_int, [_h, C.c_void_p, C.c_int64, C.c_float, C.c_float]),
+    "wallace_fill64": (C.c_int, [_h, C.c_void_p, C.c_int64, C.c_double, C.c_double]),
+    "wallace_fill_host": (C.c_int, [_h, C.c_void_p, C.c_int64, C.c_float, C.c_float]),
+    "wallace_set_stream": (C.c_int, [_h, C.c_void_p]),
+    "wallace_set_variant": (C.c_int, [_h, C.c_int]),
+    "wallace_set_timing": (C.c_int, [_h, C.c_int]),
+    "wallace_sync": (C.c_int, [_h]),
+    "wallace_stats": (C.c_int, [_h, C.POINTER(Stats)]),
+    "wallace_get_pool": (C.c_int, [_h, C.c_void_p]),
+    "wallace_get_pool64": (C.c_int, [_h, C.c_void_p]),
+    "wallace_set_pool": (C.c_int, [_h, C.c_void_p]),
+    "wallace_clear_error": (C.c_int, [_h]),
+    "wallace_returned_per_pass": (C.c_int64, [_h]),
+    "wallace_strerror": (C.c_char_p, [C.c_int]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def lib() -> C.CDLL:
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/wallace.h declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(wallace_\w+)\s*\(", text, re.M)))
+
+
+class WallaceError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {_lib.wallace_strerror(code).decode()} (status {code})")
+
+
+def _check(rc: int, where: str, allow: int = 0) -> int:
+    if rc & ~allow:
+        raise WallaceError(rc, where)
+    return rc
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Wallace:
+    """One generator handle (wallace_create_ex ... wallace_destroy)."""
+
+    def __init__(self, n: int, N: int, seed: int, frac: float = 1.0, *, stream_id: int = 0,
+                 mode: int = FP32, stream=None):
+        self.n, self.N, self.mode = n, N, mode
+        self.nu = n * N
+        h = _h()
+        rc = _lib.wallace_create_ex(n, N, seed, stream_id, frac, mode, _stream_ptr(stream),
+                                    C.byref(h))
+        _check(rc, "wallace_create_ex")
+        self._h = h
+        self.R = int(_lib.wallace_returned_per_pass(h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.wallace_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def pass_(self) -> int:
+        return _check(_lib.wallace_pass(self._h), "wallace_pass", allow=ECORRUPT)
+
+    def fill(self, out, mu: float = 0.0, sigma: float = 1.0, count: int | None = None) -> int:
+        """Fill a float32 (FP32 mode) or float64 (FP64POOL) CUDA tensor `out`."""
+        count = out.numel() if count is None else count
+        if self.mode == FP32:
+            rc = _lib.wallace_fill(self._h, C.c_void_p(out.data_ptr()), count, mu, sigma)
+        else:
+            rc = _lib.wallace_fill64(self._h, C.c_void_p(out.data_ptr()), count, mu, sigma)
+        return _check(rc, "wallace_fill", allow=ECORRUPT)
+
+    def fill_host(self, out: np.ndarray, mu: float = 0.0, sigma: float = 1.0) -> int:
+        """Fill a host float32 numpy array (or pinned torch CPU tensor)."""
+        if isinstance(out, np.ndarray):
+            assert out.dtype == np.float32 and out.flags.c_contiguous
+            ptr, count = out.ctypes.data, out.size
+        else:
+            ptr, count = out.data_ptr(), out.numel()
+        rc = _lib.wallace_fill_host(self._h, C.c_void_p(ptr), count, mu, sigma)
+        return _check(rc, "wallace_fill_host", allow=ECORRUPT)
+
+    def set_stream(self, stream) -> None:
+        _check(_lib.wallace_set_stream(self._h, _stream_ptr(stream)), "wallace_set_stream")
+
+    def set_variant(self, variant: int) -> None:
+        _check(_lib.wallace_set_variant(self._h, variant), "wallace_set_variant")
+
+    def set_timing(self, on: bool) -> None:
+        _check(_lib.wallace_set_timing(self._h, int(on)), "wallace_set_timing")
+
+    def sync(self) -> int:
+        return _check(_lib.wallace_sync(self._h), "wallace_sync", allow=ECORRUPT)
+
+    def stats(self) -> Stats:
+        st = Stats()
+        _check(_lib.wallace_stats(self._h, C.byref(st)), "wallace_stats", allow=ECORRUPT)
+        return st
+
+    def pool(self) -> np.ndarray:
+        out = np.empty(self.nu, dtype=np.float32)
+        _check(_lib.wallace_get_pool(self._h, out.ctypes.data), "wallace_get_pool", allow=ECORRUPT)
+        return out
+
+    def pool64(self) -> np.ndarray:
+        out = np.empty(self.nu, dtype=np.float64)
+        _check(_lib.wallace_get_pool64(self._h, out.ctypes.data), "wallace_get_pool64",
+               allow=ECORRUPT)
+        return out
+
+    def set_pool(self, pool: np.ndarray) -> None:
+        pool = np.ascontiguousarray(pool, dtype=np.float32)
+        assert pool.size == self.nu
+        _check(_lib.wallace_set_pool(self._h, pool.ctypes.data), "wallace_set_pool")
+
+    def clear_error(self) -> None:
+        _check(_lib.wallace_clear_error(self._h), "wallace_clear_error")

@@ -1,0 +1,235 @@
+"""Parity of the CUDA library (through its C ABI) with the oracle.
+
+Binary32 mode must match the oracle bit for bit: the initial pool, every pass
+(pool, exact Q, chi-squared target S, scale c), every returned value, and the
+integer parameters.  Binary64-pool mode must match the binary64 oracle bit for
+bit as well (same operations, exact order-free sum of squares).
+
+Cases span several tiles and ragged tails: N = 2^8 (whole pool in shared
+memory), N not a multiple of 4, N with small odd factors (stride fallback;
+in-kernel plain gather), n = 8, and the full 2^24 x 4 pool.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU machines, skipped there
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1004_3114_gb300 import wallace as W  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def bits(a):
+    return np.ascontiguousarray(a).view(np.uint32 if a.dtype == np.float32 else np.uint64)
+
+
+def assert_same(got, ref, what=""):
+    if not np.array_equal(bits(got), bits(ref)):
+        bad = np.nonzero(bits(got) != bits(ref))[0]
+        raise AssertionError(f"{what}: {len(bad)} mismatches, first at {bad[:5]}: "
+                             f"got {got[bad[:5]]} ref {ref[bad[:5]]}")
+
+
+def assert_stats_equal(g, o, what=""):
+    gs, os_ = g.stats(), o.stats()
+    assert gs.Q == os_.Q, what
+    assert gs.S == os_.S and gs.c == os_.c and gs.c32 == os_.c32, what
+    assert gs.passes == os_.passes, what
+    assert list(gs.alpha[:g.n]) == list(os_.alpha[:g.n]), what
+    assert list(gs.gamma[:g.n]) == list(os_.gamma[:g.n]), what
+    assert gs.status == os_.status, what
+
+
+def fill_dev(g, count, mu=0.0, sigma=1.0):
+    dt = torch.float32 if g.mode == W.FP32 else torch.float64
+    out = torch.empty(count, dtype=dt, device="cuda")
+    g.fill(out, mu, sigma)
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,N,seed,mode", [
+    (4, 256, 1, 0), (4, 1001, 2, 0), (8, 128, 3, 0), (4, 1 << 16, 4, 0), (4, 4, 5, 0),
+    (4, 4097, 6, 1), (8, 130, 7, 1),
+])
+def test_initial_pool_bit_exact(orc, n, N, seed, mode):
+    g = W.Wallace(n, N, seed, 1.0, mode=mode)
+    o = orc.Generator(n, N, seed, 1.0, mode=mode)
+    if mode == 0:
+        assert_same(g.pool(), o.pool32(), "pool0")
+    else:
+        assert_same(g.pool64(), o.pool64(), "pool0")
+    assert_stats_equal(g, o, "init")
+
+
+@pytest.mark.parametrize("variant", [W.VARIANT_AUTO, W.VARIANT_GATHER])
+def test_small_config_1000_passes(orc, variant):
+    """n=4, N=256, seed 1, frac=1: 1000 passes, every returnable value."""
+    g = W.Wallace(4, 256, 1, 1.0)
+    g.set_variant(variant)
+    o = orc.Generator(4, 256, 1, 1.0)
+    got = fill_dev(g, 1023 * 1000)
+    ref = o.fill(1023 * 1000)
+    assert_same(got, ref, "returned stream")
+    assert_same(g.pool(), o.pool32(), "pool after 1000 passes")
+    assert_stats_equal(g, o, "after 1000 passes")
+    # and the stored oracle snapshot
+    with open(os.path.join(GOLDEN, "n4_N256_seed1_frac1.json")) as f:
+        snap = json.load(f)["snapshots"][-1]
+    assert snap["passes"] == 1000
+    assert [int(v) for v in g.pool()[:16].view(np.uint32)] == snap["pool_head"]
+    assert str(g.stats().Q) == snap["Q"]
+
+
+def test_small_config_fp64_deviation(orc):
+    """Binary32 stream vs the binary64 oracle after 1000 passes (<= 1e-5)."""
+    g = W.Wallace(4, 256, 1, 1.0)
+    got = fill_dev(g, 1023 * 1000).astype(np.float64)
+    o64 = orc.Generator(4, 256, 1, 1.0, mode=orc.FP64)
+    ref = o64.fill(1023 * 1000)
+    dev = np.abs(got - ref)
+    assert dev.max() <= 1e-5, dev.max()
+
+
+@pytest.mark.parametrize("n,N,frac,variant", [
+    (4, 16384, 1.0, W.VARIANT_TILED),
+    (4, 16387, 0.5, W.VARIANT_TILED),
+    (4, 20000, 1 / 3, W.VARIANT_TILED),
+    (4, 45045, 0.5, W.VARIANT_TILED),      # 3^2 5 7 11 13: fallback strides, in-kernel gather
+    (4, 1 << 17, 0.5, W.VARIANT_AUTO),
+    (4, 1 << 17, 0.5, W.VARIANT_GATHER),
+    (8, 5000, 0.5, W.VARIANT_GATHER),
+    (8, 3001, 1.0, W.VARIANT_FUSED),
+    (4, 6000, 0.25, W.VARIANT_FUSED),
+    (4, 6000, 0.25, W.VARIANT_GATHER),
+])
+def test_passes_bit_exact(orc, n, N, frac, variant):
+    g = W.Wallace(n, N, 11, frac)
+    g.set_variant(variant)
+    o = orc.Generator(n, N, 11, frac)
+    R = g.R
+    for k in range(6):
+        got = fill_dev(g, R)
+        ref = o.fill(R)
+        assert_same(got, ref, f"pass {k + 1} output")
+        assert_same(g.pool(), o.pool32(), f"pass {k + 1} pool")
+        assert_stats_equal(g, o, f"pass {k + 1}")
+
+
+def test_fill_split_and_affine_map(orc):
+    g = W.Wallace(4, 16384, 3, 0.5)
+    o = orc.Generator(4, 16384, 3, 0.5)
+    sizes = [1, 0, 5, 16383, 16384, 40000, 7, 100001]
+    mu, sigma = -3.5, 2.25
+    for s in sizes:
+        got = fill_dev(g, s, mu, sigma)
+        ref = o.fill(s, mu, sigma)
+        assert_same(got, ref, f"fill {s}")
+    assert_stats_equal(g, o)
+
+
+def test_explicit_passes_skip_unread_values(orc):
+    g = W.Wallace(4, 2048, 8, 1.0)
+    o = orc.Generator(4, 2048, 8, 1.0)
+    fill_dev(g, 100)
+    o.fill(100)
+    g.pass_()
+    o.pass_()
+    assert_same(fill_dev(g, 5000), o.fill(5000), "after explicit pass")
+
+
+def test_stream_id_and_seeds(orc):
+    a = W.Wallace(4, 1024, 9, 1.0, stream_id=0)
+    b = W.Wallace(4, 1024, 9, 1.0, stream_id=3)
+    ob = orc.Generator(4, 1024, 9, 1.0, stream=3)
+    xa, xb = fill_dev(a, 10000), fill_dev(b, 10000)
+    assert not np.array_equal(xa, xb)
+    assert_same(xb, ob.fill(10000), "stream 3")
+
+
+@pytest.mark.parametrize("n,N", [(4, 1024), (4, 20000), (8, 2048)])
+def test_fp64_pool_mode_bit_exact(orc, n, N):
+    g = W.Wallace(n, N, 3, 0.5, mode=W.FP64POOL)
+    o = orc.Generator(n, N, 3, 0.5, mode=orc.FP64)
+    for k in range(5):
+        assert_same(fill_dev(g, g.R, 1.0, 2.0), o.fill(g.R, 1.0, 2.0), f"fp64 pass {k}")
+        assert_same(g.pool64(), o.pool64(), f"fp64 pool {k}")
+        assert_stats_equal(g, o, f"fp64 pass {k}")
+
+
+def test_corruption_detected(orc):
+    g = W.Wallace(4, 16384, 1, 0.5)
+    fill_dev(g, 3 * g.R)
+    assert g.stats().status == 0
+    pool = g.pool()
+    pool[12345] = np.float32(60.0)     # caller wrote over the work area
+    g.set_pool(pool)
+    g.pass_()
+    assert g.sync() & W.ECORRUPT
+    assert g.stats().status & W.ECORRUPT
+    g.clear_error()
+    assert g.sync() == 0
+    h = W.Wallace(4, 256, 1, 1.0)
+    pool = h.pool()
+    pool[0] = np.nan
+    h.set_pool(pool)
+    h.pass_()
+    assert h.sync() & W.ECORRUPT
+
+
+def test_fill_host_matches_device(orc):
+    g = W.Wallace(4, 16384, 21, 0.5)
+    o = orc.Generator(4, 16384, 21, 0.5)
+    host = np.empty(3 * g.R + 123, dtype=np.float32)
+    g.fill_host(host, 0.5, 1.5)
+    assert_same(host, o.fill(host.size, 0.5, 1.5), "fill_host")
+    pinned = torch.empty(g.R * 2, dtype=torch.float32).pin_memory()
+    g.fill_host(pinned)
+    assert_same(pinned.numpy(), o.fill(pinned.numel()), "fill_host pinned")
+
+
+def test_streams_and_timing(orc):
+    s = torch.cuda.Stream()
+    g = W.Wallace(4, 1 << 16, 2, 0.5, stream=s)
+    g.set_timing(True)
+    o = orc.Generator(4, 1 << 16, 2, 0.5)
+    with torch.cuda.stream(s):
+        out = torch.empty(g.R * 3, device="cuda")
+        g.fill(out)
+    s.synchronize()
+    assert_same(out.cpu().numpy(), o.fill(g.R * 3))
+    st = g.stats()
+    assert st.kernel_launches == 3 and st.kernel_ms > 0
+
+
+def test_full_size_pool_parity(orc):
+    """n=4, N=2^24 (256 MB pool), frac=1/2: the first passes element by element,
+    then pass 200 recomputed by the oracle from the device pool and parameters."""
+    n, N, seed = 4, 1 << 24, 7
+    g = W.Wallace(n, N, seed, 0.5)
+    o = orc.Generator(n, N, seed, 0.5)
+    assert_same(g.pool(), o.pool32(), "pool0")
+    assert_stats_equal(g, o, "init")
+    for k in range(2):
+        assert_same(fill_dev(g, g.R), o.fill(g.R), f"pass {k + 1} output")
+        assert_same(g.pool(), o.pool32(), f"pass {k + 1} pool")
+        assert_stats_equal(g, o, f"pass {k + 1}")
+    out = torch.empty(g.R, device="cuda")
+    for _ in range(197):
+        g.fill(out)
+    before = g.pool()
+    c32 = g.stats().c32
+    g.fill(out)
+    st = g.stats()
+    assert st.passes == 200 and st.status == 0
+    after = orc.pass_explicit32(n, N, before, st.alpha[:n], st.gamma[:n], c32)
+    assert_same(g.pool(), after, "pass 200 pool")
+    Q, bad = orc.sumsq32(after)
+    assert Q == st.Q and bad == 0
+    assert_same(out.cpu().numpy(), (np.float32(0) + np.float32(1) * after[:g.R]).astype(np.float32))
