@@ -184,6 +184,59 @@ int wallace_clear_error(wallace_t *h);
 /* wallace_returned_per_pass -- R for the handle (host value, no sync). */
 int64_t wallace_returned_per_pass(const wallace_t *h);
 
+/*
+ * wallace_pass_static -- one pass that allocates nothing.  The paper has no
+ * counterpart: this is a deployment entry point.
+ *
+ * For callers that cannot allocate device memory -- for example a plug-in
+ * whose host application hands it fixed buffers and a fixed memory budget
+ * and does not allow cudaMalloc, or a path where cudaMalloc's implicit
+ * device-wide synchronisation is not acceptable.  Such a caller cannot
+ * create a handle (wallace_create allocates the double buffer and state), so
+ * here the caller keeps the pool and the per-pass parameters itself, and the
+ * pass's scratch (the second pool buffer and the reduction/finaliser block)
+ * lives in one fixed array of 4 * WALLACE_STATIC_MAX_VALUES + 512 bytes
+ * inside the library, present on every device that loads the library until
+ * the process exits.  Neither this call nor anything it calls allocates.
+ *
+ *   n, N        sub-vectors and their length as in wallace_create;
+ *               n*N <= WALLACE_STATIC_MAX_VALUES, else WALLACE_EINVAL
+ *   pool        device, n*N floats, sub-vector-major, rows of exactly N
+ *               values (no padding); read, then overwritten with the new pool
+ *   alpha, gamma  host arrays of n strides and offsets for this pass
+ *               (0 <= gamma < N); results match wallace_pass only when they
+ *               are coprime to N as Eq. 2 requires
+ *   c32         scale of this pass (the c32 a previous pass reported)
+ *   out         device, receives mu + sigma*y for the first out_count values
+ *               of the new pool (0 <= out_count <= n*N; NULL if 0)
+ *   result      host; receives Q, q, S and the next pass's c and c32
+ *   cuda_stream stream to run on (NULL: legacy default stream)
+ * Synchronous: returns after the pass, the copy back into `pool` and the
+ * result copy have finished.  Returns WALLACE_OK, WALLACE_EINVAL,
+ * WALLACE_ECUDA, or WALLACE_ECORRUPT (bad value, Q = 0 or Q >= 2^64).
+ *
+ * The scratch array is shared by every call: calls that overlap on the GPU
+ * (in flight at the same time on any streams) race and give wrong results.
+ * The block that must start at zero is cleared at the start of each call.
+ * The first call on a device looks up the array's device address with that
+ * device current; make it before any stream capture begins.
+ */
+#define WALLACE_STATIC_MAX_VALUES (1 << 20)
+
+typedef struct {
+    uint64_t q_lo, q_hi;  /* exact sum of squares of the new pool (128-bit)   */
+    double q;             /* Q * 2^-32                                         */
+    double S;             /* chi-squared target from the new pool's last value */
+    double c;             /* scale for the next pass, sqrt(S/q)                */
+    float c32;            /* c rounded to binary32                             */
+    int32_t bad;          /* a value was non-finite or |y| >= 256              */
+    int32_t status;       /* WALLACE_* bits found by the pass                  */
+} wallace_pass_result_t;
+
+int wallace_pass_static(int n, int64_t N, float *pool, const int32_t *alpha, const int64_t *gamma,
+                        float c32, float *out, int64_t out_count, float mu, float sigma,
+                        wallace_pass_result_t *result, void *cuda_stream);
+
 /* wallace_strerror -- static text for a status code (lowest set bit). */
 const char *wallace_strerror(int code);
 

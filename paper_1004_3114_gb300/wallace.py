@@ -41,6 +41,19 @@ class Stats(C.Structure):
         return (int(self.q_hi) << 64) | int(self.q_lo)
 
 
+class PassResult(C.Structure):
+    _fields_ = [
+        ("q_lo", C.c_uint64), ("q_hi", C.c_uint64), ("q", C.c_double), ("S", C.c_double),
+        ("c", C.c_double), ("c32", C.c_float), ("bad", C.c_int32), ("status", C.c_int32),
+    ]
+
+    @property
+    def Q(self) -> int:
+        return (int(self.q_hi) << 64) | int(self.q_lo)
+
+
+STATIC_MAX_VALUES = 1 << 20
+
 _lib = C.CDLL(LIB_PATH)
 _h = C.c_void_p
 _SIGS = {
@@ -63,6 +76,9 @@ _SIGS = {
     "wallace_clear_error": (C.c_int, [_h]),
     "wallace_returned_per_pass": (C.c_int64, [_h]),
     "wallace_strerror": (C.c_char_p, [C.c_int]),
+    "wallace_pass_static": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_float, C.c_void_p, C.c_int64, C.c_float, C.c_float,
+                                      C.POINTER(PassResult), C.c_void_p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -78,6 +94,20 @@ def header_functions() -> list[str]:
     """Names of the functions include/wallace.h declares."""
     text = open(HEADER).read()
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(wallace_\w+)\s*\(", text, re.M)))
+
+
+def pass_static(n: int, N: int, pool, alpha, gamma, c32: float, out=None, out_count: int = 0,
+                mu: float = 0.0, sigma: float = 1.0, stream=None) -> tuple[int, PassResult]:
+    """wallace_pass_static: one pass on a caller-held pool (CUDA float32 tensor of
+    n*N values, rows of N), using the library's fixed scratch array; returns
+    (status, result)."""
+    a = (C.c_int32 * 8)(*[int(v) for v in alpha])
+    g = (C.c_int64 * 8)(*[int(v) for v in gamma])
+    res = PassResult()
+    rc = _lib.wallace_pass_static(n, N, C.c_void_p(pool.data_ptr()), a, g, c32,
+                                  C.c_void_p(out.data_ptr() if out is not None else 0), out_count,
+                                  mu, sigma, C.byref(res), _stream_ptr(stream))
+    return int(rc), res
 
 
 class WallaceError(RuntimeError):
