@@ -269,7 +269,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs larger than L2: 2 x 256 MiB pools + 128 MiB output"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": profiled_traffic(), "kernel": "wl_tiled pass",
+                         "traffic": profiled_traffic(), "kernel": "tiled_kernel (lane-tiled pass, 16-byte async copies)",
                          "kernel_ms": kernel_ms, "algorithmic_bytes_per_launch": BYTES_PER_PASS},
             "e2e": {"value": world * e2e_steps * R / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * R},

@@ -61,6 +61,10 @@ typedef struct wallace wallace_t;
 #define WALLACE_VARIANT_GATHER  1  /* direct strided gather from HBM, one pass/launch   */
 #define WALLACE_VARIANT_TILED   2  /* lane-tiled gather staged in shared memory         */
 #define WALLACE_VARIANT_FUSED   3  /* whole pool in shared memory, many passes/launch   */
+#define WALLACE_VARIANT_TILED_ASYNC 4 /* lane-tiled, per-thread 16-byte async copies      */
+#define WALLACE_VARIANT_TILED_TMA   5 /* lane-tiled, warp-specialised bulk (TMA) copies
+                                         into a stage ring; needs N % 4 == 0 (else the
+                                         per-thread-copy kernel runs)                   */
 
 /* Scalars of the most recent pass (or of the initial pool after create). */
 typedef struct {

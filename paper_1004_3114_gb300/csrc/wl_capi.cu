@@ -140,7 +140,10 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
     a.sigma = sigma;
     {
         KernelTimer t(h);
-        if (v == WALLACE_VARIANT_TILED && wl_tiled_supported(h->n, h->N, fp64))
+        if (v == WALLACE_VARIANT_TILED_TMA && wl_tma_supported(h->n, h->N, fp64, h->sm_count))
+            e = wl_launch_tma(a, h->sm_count, h->stream);
+        else if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_ASYNC) &&
+                 wl_tiled_supported(h->n, h->N, fp64))
             e = wl_launch_tiled(a, h->sm_count, h->stream);
         else
             e = wl_launch_gather(a, fp64, h->sm_count, h->stream);
@@ -432,6 +435,8 @@ int wallace_set_variant(wallace_t *h, int variant)
     case WALLACE_VARIANT_GATHER:
         break;
     case WALLACE_VARIANT_TILED:
+    case WALLACE_VARIANT_TILED_ASYNC:
+    case WALLACE_VARIANT_TILED_TMA:
         if (!wl_tiled_supported(h->n, h->N, fp64))
             return WALLACE_EINVAL;
         break;

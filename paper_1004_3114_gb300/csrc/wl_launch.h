@@ -36,6 +36,11 @@ cudaError_t wl_launch_drain(const void *pool, int fp64, int64_t N, int64_t Np, i
 bool wl_tiled_supported(int n, int64_t N, int fp64);
 cudaError_t wl_launch_tiled(const WlPassArgs &a, int sm_count, cudaStream_t stream);
 
+// warp-specialised lane-tiled gather with bulk (TMA) copies into a stage ring
+// (binary32, n = 4, N a multiple of 4)
+bool wl_tma_supported(int n, int64_t N, int fp64, int sm_count);
+cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, cudaStream_t stream);
+
 // whole pool resident in shared memory for `passes` passes in one launch.
 // Pass k (0-based) writes its values [0, take_k) to out + out_off_k where
 // take_k = R for k < passes-1 and last_take for the final pass.

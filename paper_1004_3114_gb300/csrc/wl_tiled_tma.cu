@@ -1,0 +1,398 @@
+// One pass of Wallace's generator (Eq. 1 of Brent's RANN4 paper; n = 4,
+// binary32 pool, N a multiple of 4) as a warp-specialised lane-tiled gather.
+//
+// Lane geometry as in wl_tiled.cu: L = lcm(alpha_i) lanes, lane l starting at
+// J_l = ceil(l N / L); a tile of T lane times reads, per sub-vector i,
+// m_i = L / alpha_i contiguous spans of alpha_i T values (span p starts at
+// ceil(p N / m_i) + alpha_i t0 + gamma_i mod N) and uses every value.
+//
+// Pipeline (one CTA per SM, persistent over tiles):
+//   producer warp  -- computes the tile's span addresses, posts the expected
+//                     byte count on the stage's "full" mbarrier, and issues
+//                     one bulk copy (cp.async.bulk, the TMA engine) per span
+//                     (two for a span that wraps past the end of its row)
+//                     into a ring of TM_STAGES shared-memory stages;
+//   consumer warps -- wait for the stage, gather the n-tuples from shared
+//                     memory (odd strides: no bank conflicts), transform,
+//                     store the new pool and the returned values, accumulate
+//                     the exact sum of squares, and release the stage on its
+//                     "empty" mbarrier.
+// Every wait is bounded by a cycle budget; on expiry the CTA records
+// WALLACE_ETIMEOUT in the state, stops issuing work, waits (bounded) for its
+// copies still in flight, and leaves.
+#include "wl_common.cuh"
+#include "wl_launch.h"
+
+#define TM_CONS_WARPS 12
+#define TM_CONS_THREADS (TM_CONS_WARPS * 32)
+#define TM_THREADS (TM_CONS_THREADS + 32)
+#define TM_STAGES 4
+#define TM_ETARGET 2048          /* lane-times per tile: L * T <= this */
+#define TM_LMAX 315
+#define TM_MAXSPANS 256          /* sum_i L / alpha_i for the stride tables is <= 248 */
+#define TM_MIN_N 16384
+#define TM_WAIT_CYCLES 2000000000ll   /* about one second */
+
+namespace {
+
+__host__ __device__ constexpr int tm_stage_data_words() { return 4 * TM_ETARGET + 12 * TM_MAXSPANS; }
+__host__ __device__ constexpr int tm_stage_words() { return tm_stage_data_words() + 4 * TM_LMAX; }
+__host__ __device__ constexpr int tm_common_words() { return (TM_LMAX + 1) + 4 * TM_LMAX + 2 * TM_MAXSPANS; }
+__host__ __device__ constexpr size_t tm_smem_bytes()
+{
+    return sizeof(float) * (size_t)(TM_STAGES * tm_stage_words() + tm_common_words());
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar)
+                 : "memory");
+}
+
+// true when the phase with the given parity has completed; false after the
+// cycle budget runs out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const long long start = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done)
+            return true;
+        if (clock64() - start > TM_WAIT_CYCLES)
+            return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t magic_div(uint32_t d)
+{
+    return d > 1 ? (uint32_t)((0x100000000ull + d - 1) / d) : 0u;
+}
+__device__ __forceinline__ uint32_t fast_div(uint32_t f, uint32_t d, uint32_t m)
+{
+    return d > 1 ? __umulhi(f, m) : f;
+}
+
+// sum of squares term of one binary32 value: floor(y^2 2^32), exact.  With
+// y = m 2^(e-150) (m including the hidden bit), y^2 2^32 = m^2 2^-(268-2e);
+// values below 2^-16 give 0 (shift >= 63 on a 48-bit square), and
+// |y| >= 256 or Inf/NaN (e >= 135) contributes 0 and sets `bad`.
+__device__ __forceinline__ uint64_t term32_fast(float y, uint32_t &bad)
+{
+    const uint32_t u = __float_as_uint(y);
+    const int e = (int)((u >> 23) & 0xffu);
+    const uint32_t m = (u & 0x7fffffu) | 0x800000u;
+    const int rs = min(268 - 2 * e, 63);
+    const uint64_t t = ((uint64_t)m * (uint64_t)m) >> max(rs, 0);
+    const bool big = e >= 135;
+    bad |= big ? 1u : 0u;
+    return big ? 0ull : t;
+}
+
+__global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
+{
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar_full[TM_STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[TM_STAGES];
+    __shared__ uint64_t red[3 * (TM_THREADS / 32 + 1)];
+    __shared__ volatile int s_abort;
+
+    WlDevState *st = a.st;
+    const float *__restrict__ src = (const float *)a.src;
+    float *__restrict__ dst = (float *)a.dst;
+    const int64_t N = a.N, Np = a.Np;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int alpha[4];
+    int64_t gam[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        alpha[i] = st->next.alpha[i];
+        gam[i] = st->next.gamma[i];
+    }
+    const float c = st->next.c32;
+    float *out = (float *)a.out;
+    const float mu = (float)a.mu, sigma = (float)a.sigma;
+    const int64_t w0 = a.w0, w1 = a.w1;
+
+    int L = alpha[0];
+#pragma unroll
+    for (int i = 1; i < 4; i++)
+        L = L / (int)wl_gcd(L, alpha[i]) * alpha[i];
+    int m[4], sb[5];
+    sb[0] = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        m[i] = L <= TM_LMAX ? L / alpha[i] : 0;
+        sb[i + 1] = sb[i] + m[i];
+    }
+    const int nspans = sb[4];
+
+    uint64_t lo = 0, hi = 0;
+    uint32_t bad = 0;
+
+    if (L > TM_LMAX || nspans > TM_MAXSPANS || N < TM_MIN_N || (N & 3)) {
+        // plain strided gather for this pass (strides with a large lcm)
+        const int64_t G = (int64_t)gridDim.x * blockDim.x;
+        int64_t j = (int64_t)blockIdx.x * blockDim.x + tid;
+        int64_t idx[4], stp[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            idx[i] = (int64_t)(((uint64_t)alpha[i] * (uint64_t)(j < N ? j : 0) + (uint64_t)gam[i]) % (uint64_t)N);
+            stp[i] = (int64_t)(((uint64_t)alpha[i] * (uint64_t)G) % (uint64_t)N);
+        }
+        for (; j < N; j += G) {
+            float g[4], y[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                g[i] = src[i * Np + idx[i]];
+                idx[i] += stp[i];
+                if (idx[i] >= N)
+                    idx[i] -= N;
+            }
+            wl_xform4(g, c, y);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                dst[k * Np + j] = y[k];
+                wl_add128(lo, hi, wl_term32(y[k], bad), 0);
+                int64_t q = k * N + j;
+                if (q >= w0 && q < w1)
+                    out[q - w0] = __fadd_rn(mu, __fmul_rn(sigma, y[k]));
+            }
+        }
+    } else {
+        const int T = TM_ETARGET / L;
+        int SL[4], slot0[4];
+        slot0[0] = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            SL[i] = (alpha[i] * T + 8 + 3) & ~3;   // 16-byte aligned slots; wrap copies need +6
+            if (i < 3)
+                slot0[i + 1] = slot0[i] + m[i] * SL[i];
+        }
+        float *stage0 = smem;
+        int *common = (int *)(smem + TM_STAGES * tm_stage_words());
+        int *J = common;
+        int *lanebase = J + (TM_LMAX + 1);
+        int *spanC = lanebase + 4 * TM_LMAX;
+        int *spanLead = spanC + TM_MAXSPANS;
+
+        for (int l = tid; l <= L; l += TM_THREADS)
+            J[l] = (int)(((int64_t)l * N + L - 1) / L);
+        for (int s = tid; s < nspans; s += TM_THREADS) {
+            int i = (s >= sb[1]) + (s >= sb[2]) + (s >= sb[3]);
+            int p = s - sb[i];
+            spanC[s] = (int)(((int64_t)p * N + m[i] - 1) / m[i]);
+        }
+        if (tid == 0) {
+            for (int s = 0; s < TM_STAGES; s++) {
+                mbar_init(smem_u32(&bar_full[s]), 32);
+                mbar_init(smem_u32(&bar_empty[s]), TM_CONS_WARPS);
+            }
+            s_abort = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        }
+        __syncthreads();
+        for (int e = tid; e < 4 * L; e += TM_THREADS) {
+            int i = e / L, l = e - i * L;
+            int w = l / m[i], p = l - w * m[i];
+            int64_t r = (int64_t)alpha[i] * J[l] - (int64_t)w * N - spanC[sb[i] + p];
+            lanebase[i * TM_LMAX + l] = slot0[i] + p * SL[i] + (int)r;
+        }
+        __syncthreads();
+        const int maxlen = (int)((N + L - 1) / L);
+        const int ntiles = (maxlen + T - 1) / T;
+
+        if (warp == TM_CONS_WARPS) {
+            // ---------------- producer warp ----------------
+            int issued[TM_STAGES];
+#pragma unroll
+            for (int s = 0; s < TM_STAGES; s++)
+                issued[s] = 0;
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+                const int s = it % TM_STAGES;
+                const int k = it / TM_STAGES;
+                if (s_abort)
+                    break;
+                if (k > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (uint32_t)((k - 1) & 1))) {
+                    s_abort = 1;
+                    atomicOr(&st->status, WL_ETIMEOUT);
+                    break;
+                }
+                const int t0 = tile * T;
+                const int Tt = min(T, maxlen - t0);
+                float *sdata = stage0 + s * tm_stage_words();
+                int *laneoff = (int *)(sdata + tm_stage_data_words());
+                const uint32_t full = smem_u32(&bar_full[s]);
+                // byte count of this lane's spans
+                uint32_t bytes = 0;
+                for (int sp = lane; sp < nspans; sp += 32) {
+                    int i = (sp >= sb[1]) + (sp >= sb[2]) + (sp >= sb[3]);
+                    int64_t addr = (int64_t)spanC[sp] + (int64_t)alpha[i] * t0 + gam[i];
+                    while (addr >= N)
+                        addr -= N;
+                    int len = alpha[i] * Tt;
+                    int as = (int)addr & ~3;
+                    spanLead[sp] = (int)addr - as;
+                    if (addr + len <= N) {
+                        bytes += 16u * (uint32_t)(((int)addr - as + len + 3) >> 2);
+                    } else {
+                        int e2 = ((int)(addr + len - N) + 3) & ~3;
+                        bytes += 4u * (uint32_t)((int)N - as) + 4u * (uint32_t)e2;
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    bytes += __shfl_xor_sync(0xffffffffu, bytes, off);
+                if (lane == 0)
+                    mbar_expect_tx(full, bytes);
+                __syncwarp();
+                for (int e = lane; e < 4 * L; e += 32) {
+                    int i = e / L, l = e - i * L;
+                    laneoff[i * TM_LMAX + l] = lanebase[i * TM_LMAX + l] + spanLead[sb[i] + l % m[i]];
+                }
+                const uint32_t sbase = smem_u32(sdata);
+                for (int sp = lane; sp < nspans; sp += 32) {
+                    int i = (sp >= sb[1]) + (sp >= sb[2]) + (sp >= sb[3]);
+                    int p = sp - sb[i];
+                    int64_t addr = (int64_t)spanC[sp] + (int64_t)alpha[i] * t0 + gam[i];
+                    while (addr >= N)
+                        addr -= N;
+                    int len = alpha[i] * Tt;
+                    int as = (int)addr & ~3;
+                    const float *row = src + (int64_t)i * Np;
+                    uint32_t d = sbase + 4u * (uint32_t)(slot0[i] + p * SL[i]);
+                    if (addr + len <= N) {
+                        bulk_g2s(d, row + as, 16u * (uint32_t)(((int)addr - as + len + 3) >> 2), full);
+                    } else {
+                        int e2 = ((int)(addr + len - N) + 3) & ~3;
+                        bulk_g2s(d, row + as, 4u * (uint32_t)((int)N - as), full);
+                        bulk_g2s(d + 4u * (uint32_t)((int)N - as), row, 4u * (uint32_t)e2, full);
+                    }
+                }
+                mbar_arrive(full);
+                issued[s] = k + 1;
+            }
+            // copies still in flight must land before the CTA leaves
+            for (int s = 0; s < TM_STAGES; s++)
+                if (issued[s] > 0 && !mbar_wait(smem_u32(&bar_full[s]), (uint32_t)((issued[s] - 1) & 1)))
+                    atomicOr(&st->status, WL_ETIMEOUT);
+        } else {
+            // ---------------- consumer warps ----------------
+            int mode[4];   // 0: none of sub-vector k is returned, 1: all, 2: check each value
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                int64_t q0 = k * N, q1 = q0 + N;
+                mode[k] = (q1 <= w0 || q0 >= w1) ? 0 : ((q0 >= w0 && q1 <= w1) ? 1 : 2);
+            }
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+                const int s = it % TM_STAGES;
+                const int k = it / TM_STAGES;
+                if (s_abort)
+                    break;
+                if (!mbar_wait(smem_u32(&bar_full[s]), (uint32_t)(k & 1))) {
+                    s_abort = 1;
+                    atomicOr(&st->status, WL_ETIMEOUT);
+                    break;
+                }
+                const int t0 = tile * T;
+                const int Tt = min(T, maxlen - t0);
+                const float *sdata = stage0 + s * tm_stage_words();
+                const int *laneoff = (const int *)(sdata + tm_stage_data_words());
+                const uint32_t mT = magic_div((uint32_t)Tt);
+                const int npairs = L * Tt;
+                for (int f = tid; f < npairs; f += TM_CONS_THREADS) {
+                    const int l = (int)fast_div((uint32_t)f, (uint32_t)Tt, mT);
+                    const int t = f - l * Tt;
+                    const int jl = J[l];
+                    const int tt = t0 + t;
+                    if (tt >= J[l + 1] - jl)
+                        continue;
+                    float g[4], y[4];
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+                        g[i] = sdata[laneoff[i * TM_LMAX + l] + alpha[i] * t];
+                    wl_xform4(g, c, y);
+                    const int64_t j = (int64_t)jl + tt;
+#pragma unroll
+                    for (int kk = 0; kk < 4; kk++) {
+                        dst[kk * Np + j] = y[kk];
+                        lo += term32_fast(y[kk], bad);
+                        if (mode[kk]) {
+                            const int64_t q = kk * N + j;
+                            if (mode[kk] == 1 || (q >= w0 && q < w1))
+                                out[q - w0] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(smem_u32(&bar_empty[s]));
+            }
+        }
+    }
+
+    wl_cta_reduce_to_state(lo, hi, bad, st, red);
+    if (wl_last_cta(st) && tid == 0) {
+        double x = (double)__ldcg(&dst[wl_phys(a.nu - 1, N, Np)]);
+        wl_finalise(st, 4, N, a.nu, x, false, true);
+    }
+}
+
+bool g_tma_configured = false;
+
+} // namespace
+
+bool wl_tma_supported(int n, int64_t N, int fp64, int sm_count)
+{
+    // each consumer thread sums at most ceil(nu / (SMs * consumer threads))
+    // terms below 2^48 in 64 bits: keep that count below 2^16
+    const int64_t nu = (int64_t)n * N;
+    const int64_t per_thread = nu / ((int64_t)(sm_count > 0 ? sm_count : 1) * TM_CONS_THREADS) + 1;
+    return n == 4 && !fp64 && N >= TM_MIN_N && (N & 3) == 0 && N <= ((int64_t)1 << 28) &&
+           per_thread < 65536;
+}
+
+cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, cudaStream_t stream)
+{
+    const size_t smem = tm_smem_bytes();
+    if (!g_tma_configured) {
+        cudaError_t e = cudaFuncSetAttribute(tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        g_tma_configured = true;
+    }
+    tma_kernel<<<sm_count, TM_THREADS, smem, stream>>>(a);
+    return cudaGetLastError();
+}

@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "wallace.h")
 OK, EINVAL, ENOMEM, ECORRUPT, ECUDA, ETIMEOUT, ESTATE = 0, 1, 2, 4, 8, 16, 32
 FP32, FP64POOL = 0, 1
 VARIANT_AUTO, VARIANT_GATHER, VARIANT_TILED, VARIANT_FUSED = 0, 1, 2, 3
+VARIANT_TILED_ASYNC, VARIANT_TILED_TMA = 4, 5
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with "

@@ -99,6 +99,11 @@ def test_small_config_fp64_deviation(orc):
 
 @pytest.mark.parametrize("n,N,frac,variant", [
     (4, 16384, 1.0, W.VARIANT_TILED),
+    (4, 16384, 1.0, W.VARIANT_TILED_ASYNC),
+    (4, 1 << 17, 0.5, W.VARIANT_TILED_ASYNC),
+    (4, 100004, 1 / 3, W.VARIANT_TILED_TMA),
+    (4, 1 << 17, 0.5, W.VARIANT_TILED_TMA),
+    (4, 16387, 0.5, W.VARIANT_TILED_TMA),
     (4, 16387, 0.5, W.VARIANT_TILED),
     (4, 20000, 1 / 3, W.VARIANT_TILED),
     (4, 45045, 0.5, W.VARIANT_TILED),      # 3^2 5 7 11 13: fallback strides, in-kernel gather
