@@ -158,15 +158,18 @@ void orc_box_muller(uint32_t u1, uint32_t u2, float *a, float *b)
  * for strides that are distinct, greater than one, odd, and coprime to N, and
  * offsets uniform on {0..N-1}, all redrawn every pass; RANN4 picks its two
  * strides from {3,5} and {7,11}.  Reading for n = 4 and n = 8 (the paper
- * gives only n = 2): sub-vector i draws one uniform whose top bit picks one of
- * two strides from row i of the table below, then one uniform U giving the
- * offset floor(U*N/2^32).  All table entries are distinct odd divisors of
- * 315 (rows 0-3) or 3465 (rows 4-7).  If the picked stride shares a factor
- * with N, or is already in use, the other entry of the row is taken; if that
- * fails too, the smallest odd number > 1 coprime to N and not in use.
+ * gives only n = 2): the candidate strides are the odd divisors > 1 of 45
+ * (n = 4: 3, 5, 9, 15, 45) or of 315 (n = 8: eleven values), so the lcm of
+ * any pass's strides divides 45 or 315.  Sub-vector i draws one uniform U and
+ * takes entry floor(U * k / 2^32) of the k candidates still available --
+ * coprime to N and not yet used this pass, in table order -- so for N coprime
+ * to the table every ordered choice of distinct strides is equally likely
+ * (120 for n = 4).  If none is available, it takes the smallest odd number
+ * > 1 coprime to N and not in use.  Then one uniform U gives the offset
+ * floor(U * N / 2^32).
  * ------------------------------------------------------------------------ */
-static const int32_t ORC_STRIDES[8][2] = {
-    {3, 5}, {7, 9}, {15, 21}, {35, 45}, {11, 33}, {55, 77}, {99, 165}, {231, 385}};
+static const int32_t ORC_CAND4[5] = {3, 5, 9, 15, 45};
+static const int32_t ORC_CAND8[11] = {3, 5, 7, 9, 15, 21, 35, 45, 63, 105, 315};
 
 static int64_t orc_gcd(int64_t a, int64_t b)
 {
@@ -190,17 +193,22 @@ static int orc_stride_ok(int32_t a, int64_t N, const int32_t *used, int nused)
 
 void orc_draw_params(int n, int64_t N, uint64_t *state, int32_t *alpha, int64_t *gamma)
 {
+    const int32_t *cand = n == 4 ? ORC_CAND4 : ORC_CAND8;
+    const int ncand = n == 4 ? 5 : 11;
     for (int i = 0; i < n; i++) {
-        uint32_t ub = orc_lcg_next(state);
-        int bit = (int)(ub >> 31);
-        int32_t a = ORC_STRIDES[i][bit];
-        if (!orc_stride_ok(a, N, alpha, i)) {
-            a = ORC_STRIDES[i][1 - bit];
-            if (!orc_stride_ok(a, N, alpha, i)) {
-                a = 3;
-                while (!orc_stride_ok(a, N, alpha, i))
-                    a += 2;
-            }
+        uint32_t us = orc_lcg_next(state);
+        int32_t avail[11];
+        int na = 0;
+        for (int k = 0; k < ncand; k++)
+            if (orc_stride_ok(cand[k], N, alpha, i))
+                avail[na++] = cand[k];
+        int32_t a;
+        if (na > 0) {
+            a = avail[((uint64_t)us * (uint64_t)na) >> 32];
+        } else {
+            a = 3;
+            while (!orc_stride_ok(a, N, alpha, i))
+                a += 2;
         }
         alpha[i] = a;
         uint32_t uo = orc_lcg_next(state);

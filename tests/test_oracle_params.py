@@ -10,7 +10,8 @@ import math
 import numpy as np
 import pytest
 
-TABLE4 = [(3, 5), (7, 9), (15, 21), (35, 45)]
+CAND4 = (3, 5, 9, 15, 45)          # odd divisors > 1 of 45
+CAND8 = (3, 5, 7, 9, 15, 21, 35, 45, 63, 105, 315)   # odd divisors > 1 of 315
 
 
 def _check(n, N, alpha, gamma):
@@ -36,19 +37,46 @@ def test_params_satisfy_paper_constraints(orc, n, N):
         s = s2
 
 
-def test_power_of_two_strides_come_from_lcm_bounded_table(orc):
+def test_power_of_two_strides_are_ordered_choices_from_divisors_of_45(orc):
+    """For N coprime to 45 every ordered choice of 4 distinct strides from
+    {3,5,9,15,45} is equally likely (120 outcomes), and lcm(strides) = 45."""
+    import itertools
     s = orc.seed_state(1)
-    seen = [set() for _ in range(4)]
-    for _ in range(400):
+    counts = {}
+    draws = 24000
+    for _ in range(draws):
         alpha, gamma, s = orc.draw_params(4, 1 << 20, s)
-        for i, a in enumerate(alpha):
-            assert int(a) in TABLE4[i]
-            seen[i].add(int(a))
+        key = tuple(int(a) for a in alpha)
+        assert all(a in CAND4 for a in key)
         lcm = 1
-        for a in alpha:
-            lcm = lcm * int(a) // math.gcd(lcm, int(a))
-        assert 315 % lcm == 0
-    assert all(len(x) == 2 for x in seen)   # both choices occur
+        for a in key:
+            lcm = lcm * a // math.gcd(lcm, a)
+        assert lcm == 45
+        counts[key] = counts.get(key, 0) + 1
+    outcomes = list(itertools.permutations(CAND4, 4))
+    assert set(counts) == set(outcomes)
+    exp = draws / len(outcomes)
+    chi2 = sum((counts[o] - exp) ** 2 / exp for o in outcomes)
+    assert chi2 < 119 + 6 * math.sqrt(2 * 119)     # 119 dof
+
+
+def test_n8_strides_divide_315(orc):
+    s = orc.seed_state(2)
+    for _ in range(500):
+        alpha, _, s = orc.draw_params(8, 1 << 16, s)
+        assert all(int(a) in CAND8 for a in alpha)
+        assert len(set(int(a) for a in alpha)) == 8
+
+
+def test_fallback_when_table_exhausted(orc):
+    # N divisible by 3 and 5: every candidate shares a factor with N, so the
+    # rule takes the smallest free odd numbers coprime to N
+    N = 3 * 5 * 7 * 11 * 1000
+    alpha, _, _ = orc.draw_params(4, N, orc.seed_state(3))
+    assert sorted(int(a) for a in alpha) == [13, 17, 19, 23]
+    # N divisible by 3 only: candidate 5, then the fallbacks 7, 11, 13
+    alpha, _, _ = orc.draw_params(4, 3 * 4096, orc.seed_state(4))
+    assert sorted(int(a) for a in alpha) == [5, 7, 11, 13]
 
 
 def test_offsets_are_uniform(orc):
