@@ -59,7 +59,9 @@ typedef struct wallace wallace_t;
 /* pass kernel selection (wallace_set_variant) */
 #define WALLACE_VARIANT_AUTO    0  /* pick by pool size                                 */
 #define WALLACE_VARIANT_GATHER  1  /* direct strided gather from HBM, one pass/launch   */
-#define WALLACE_VARIANT_TILED   2  /* lane-tiled gather staged in shared memory         */
+#define WALLACE_VARIANT_TILED   2  /* lane-tiled gather staged in shared memory: the
+                                      bulk-copy (TMA) pipeline when N % 4 == 0, else
+                                      per-thread 16-byte async copies                 */
 #define WALLACE_VARIANT_FUSED   3  /* whole pool in shared memory, many passes/launch   */
 #define WALLACE_VARIANT_TILED_ASYNC 4 /* lane-tiled, per-thread 16-byte async copies      */
 #define WALLACE_VARIANT_TILED_TMA   5 /* lane-tiled, warp-specialised bulk (TMA) copies

@@ -140,9 +140,11 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
     a.sigma = sigma;
     {
         KernelTimer t(h);
-        if (v == WALLACE_VARIANT_TILED_TMA && wl_tma_supported(h->n, h->N, fp64, h->sm_count))
+        if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_TMA) &&
+            wl_tma_supported(h->n, h->N, fp64, h->sm_count))
             e = wl_launch_tma(a, h->sm_count, h->stream);
-        else if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_ASYNC) &&
+        else if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_ASYNC ||
+                  v == WALLACE_VARIANT_TILED_TMA) &&
                  wl_tiled_supported(h->n, h->N, fp64))
             e = wl_launch_tiled(a, h->sm_count, h->stream);
         else

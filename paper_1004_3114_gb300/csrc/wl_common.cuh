@@ -84,12 +84,13 @@ __device__ __forceinline__ uint64_t wl_lcg_jump(uint64_t s, uint64_t m)
 }
 
 // ---- per-pass parameters ---------------------------------------------------
-// Strides are distinct, odd, > 1 and coprime to N (Eq. 2, Sections 3 and 7);
-// row i of the table offers two choices picked by the top bit of one uniform
-// (RANN4 picks from {3,5} and {7,11}, Section 8).  Rows 0-3 divide 315 and
-// rows 4-7 divide 3465, which bounds the lane count of the tiled kernel.
-// Fallbacks: the row's other entry, then the smallest free odd number > 1
-// coprime to N.  The offset is floor(U N / 2^32), uniform on {0..N-1}.
+// Strides are distinct, odd, > 1 and coprime to N (Eq. 2, Sections 3 and 7).
+// Candidates: the odd divisors > 1 of 45 (n = 4) or of 315 (n = 8), so one
+// pass's strides have lcm dividing 45 (315): the lane count of the tiled
+// kernels.  One uniform per sub-vector picks, by multiply-shift, among the
+// candidates still free (coprime to N, not yet used) in table order; with
+// none free, the smallest free odd number > 1 coprime to N.  The offset is
+// floor(U N / 2^32), uniform on {0..N-1}.
 __device__ __forceinline__ int64_t wl_gcd(int64_t a, int64_t b)
 {
     while (b) {
@@ -112,22 +113,28 @@ __device__ __forceinline__ bool wl_stride_free(int32_t a, int64_t N, const int32
 
 __device__ inline void wl_draw_params(int n, int64_t N, uint64_t &s, int32_t *alpha, int64_t *gamma)
 {
-    const int32_t tab[8][2] = {{3, 5}, {7, 9}, {15, 21}, {35, 45},
-                               {11, 33}, {55, 77}, {99, 165}, {231, 385}};
+    const int32_t div45[5] = {3, 5, 9, 15, 45};
+    const int32_t div315[11] = {3, 5, 7, 9, 15, 21, 35, 45, 63, 105, 315};
+    const int32_t *cand = n == 4 ? div45 : div315;
+    const int ncand = n == 4 ? 5 : 11;
     for (int i = 0; i < n; i++) {
-        uint32_t pick = wl_lcg_step(s) >> 31;
-        int32_t a = tab[i][pick];
-        if (!wl_stride_free(a, N, alpha, i)) {
-            a = tab[i][1 - pick];
-            if (!wl_stride_free(a, N, alpha, i)) {
-                a = 3;
-                while (!wl_stride_free(a, N, alpha, i))
-                    a += 2;
-            }
+        const uint32_t u = wl_lcg_step(s);
+        int32_t freec[11];
+        int nf = 0;
+        for (int k = 0; k < ncand; k++)
+            if (wl_stride_free(cand[k], N, alpha, i))
+                freec[nf++] = cand[k];
+        int32_t a;
+        if (nf > 0) {
+            a = freec[((uint64_t)u * (uint64_t)nf) >> 32];
+        } else {
+            a = 3;
+            while (!wl_stride_free(a, N, alpha, i))
+                a += 2;
         }
         alpha[i] = a;
-        uint32_t u = wl_lcg_step(s);
-        gamma[i] = (int64_t)(((uint64_t)u * (uint64_t)N) >> 32);
+        const uint32_t v = wl_lcg_step(s);
+        gamma[i] = (int64_t)(((uint64_t)v * (uint64_t)N) >> 32);
     }
 }
 

@@ -4,40 +4,49 @@
 // Lane geometry as in wl_tiled.cu: L = lcm(alpha_i) lanes, lane l starting at
 // J_l = ceil(l N / L); a tile of T lane times reads, per sub-vector i,
 // m_i = L / alpha_i contiguous spans of alpha_i T values (span p starts at
-// ceil(p N / m_i) + alpha_i t0 + gamma_i mod N) and uses every value.
+// ceil(p N / m_i) + alpha_i t0 + gamma_i mod N) and uses every value.  With
+// strides drawn from the odd divisors of 45, L = 45 and a tile is 45 lanes by
+// T = 64 lane times: at most 32 spans of 0.75 to 11.5 KB.
 //
 // Pipeline (one CTA per SM, persistent over tiles):
-//   producer warp  -- computes the tile's span addresses, posts the expected
-//                     byte count on the stage's "full" mbarrier, and issues
-//                     one bulk copy (cp.async.bulk, the TMA engine) per span
-//                     (two for a span that wraps past the end of its row)
-//                     into a ring of TM_STAGES shared-memory stages;
-//   consumer warps -- wait for the stage, gather the n-tuples from shared
-//                     memory (odd strides: no bank conflicts), transform,
-//                     store the new pool and the returned values, accumulate
-//                     the exact sum of squares, and release the stage on its
-//                     "empty" mbarrier.
+//   producer warps -- for each span of the tile: its address, its 16-byte
+//                     alignment lead (stored for the consumers), its byte
+//                     count, and one bulk copy (cp.async.bulk, the TMA engine;
+//                     two for a span that wraps past the end of its row) into
+//                     a ring of TM_STAGES shared-memory stages, completing on
+//                     the stage's "full" mbarrier.  Span sp belongs to lane
+//                     sp / 4 of producer warp sp % 4: a single warp issues
+//                     bulk copies too slowly for spans of about 1 KB;
+//   consumer warps -- wait for the stage; each warp task is one lane and 32
+//                     consecutive lane times, so lane-table reads are
+//                     broadcasts, shared-memory gathers have odd stride
+//                     alpha_i (no bank conflicts) and every store instruction
+//                     writes 128 contiguous bytes; transform, store the new
+//                     pool and the returned values, accumulate the exact sum
+//                     of squares, then release the stage on its "empty"
+//                     mbarrier.
 // Every wait is bounded by a cycle budget; on expiry the CTA records
 // WALLACE_ETIMEOUT in the state, stops issuing work, waits (bounded) for its
 // copies still in flight, and leaves.
 #include "wl_common.cuh"
 #include "wl_launch.h"
 
-#define TM_CONS_WARPS 12
+#define TM_CONS_WARPS 16
 #define TM_CONS_THREADS (TM_CONS_WARPS * 32)
-#define TM_THREADS (TM_CONS_THREADS + 32)
+#define TM_PROD_WARPS 4          /* one warp issues a bulk copy only every ~80 cycles */
+#define TM_THREADS (TM_CONS_THREADS + 32 * TM_PROD_WARPS)
 #define TM_STAGES 4
-#define TM_ETARGET 2048          /* lane-times per tile: L * T <= this */
-#define TM_LMAX 315
-#define TM_MAXSPANS 256          /* sum_i L / alpha_i for the stride tables is <= 248 */
+#define TM_ETARGET 2880          /* lane-times per tile: L * T <= this (T = 64 at L = 45) */
+#define TM_LMAX 45
+#define TM_MAXSPANS 32           /* sum_i 45 / alpha_i <= 15 + 9 + 5 + 3 */
 #define TM_MIN_N 16384
 #define TM_WAIT_CYCLES 2000000000ll   /* about one second */
 
 namespace {
 
 __host__ __device__ constexpr int tm_stage_data_words() { return 4 * TM_ETARGET + 12 * TM_MAXSPANS; }
-__host__ __device__ constexpr int tm_stage_words() { return tm_stage_data_words() + 4 * TM_LMAX; }
-__host__ __device__ constexpr int tm_common_words() { return (TM_LMAX + 1) + 4 * TM_LMAX + 2 * TM_MAXSPANS; }
+__host__ __device__ constexpr int tm_stage_words() { return tm_stage_data_words() + TM_MAXSPANS; }
+__host__ __device__ constexpr int tm_common_words() { return (TM_LMAX + 1) + 4 * TM_LMAX + TM_MAXSPANS; }
 __host__ __device__ constexpr size_t tm_smem_bytes()
 {
     return sizeof(float) * (size_t)(TM_STAGES * tm_stage_words() + tm_common_words());
@@ -92,29 +101,19 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
-__device__ __forceinline__ uint32_t magic_div(uint32_t d)
-{
-    return d > 1 ? (uint32_t)((0x100000000ull + d - 1) / d) : 0u;
-}
-__device__ __forceinline__ uint32_t fast_div(uint32_t f, uint32_t d, uint32_t m)
-{
-    return d > 1 ? __umulhi(f, m) : f;
-}
-
-// sum of squares term of one binary32 value: floor(y^2 2^32), exact.  With
-// y = m 2^(e-150) (m including the hidden bit), y^2 2^32 = m^2 2^-(268-2e);
-// values below 2^-16 give 0 (shift >= 63 on a 48-bit square), and
-// |y| >= 256 or Inf/NaN (e >= 135) contributes 0 and sets `bad`.
-__device__ __forceinline__ uint64_t term32_fast(float y, uint32_t &bad)
+// floor(y^2 2^32) of one binary32 value, exact.  y = m 2^(e-150) with the
+// hidden bit in m, so y^2 2^32 = m^2 / 2^(268-2e).  The shift is clamped to
+// 63 as an unsigned value: e <= 110 (|y| < 2^-16) gives 0, and e >= 135
+// (|y| >= 256, Inf, NaN: a corrupt pool) wraps to a huge shift and also
+// gives 0; such exponents are caught through the running maximum `emax`.
+__device__ __forceinline__ uint64_t term32(float y, uint32_t &emax)
 {
     const uint32_t u = __float_as_uint(y);
-    const int e = (int)((u >> 23) & 0xffu);
+    const uint32_t e = (u >> 23) & 0xffu;
     const uint32_t m = (u & 0x7fffffu) | 0x800000u;
-    const int rs = min(268 - 2 * e, 63);
-    const uint64_t t = ((uint64_t)m * (uint64_t)m) >> max(rs, 0);
-    const bool big = e >= 135;
-    bad |= big ? 1u : 0u;
-    return big ? 0ull : t;
+    const uint32_t rs = min(268u - 2u * e, 63u);
+    emax = max(emax, e);
+    return ((uint64_t)m * (uint64_t)m) >> rs;
 }
 
 __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
@@ -159,7 +158,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
     uint32_t bad = 0;
 
     if (L > TM_LMAX || nspans > TM_MAXSPANS || N < TM_MIN_N || (N & 3)) {
-        // plain strided gather for this pass (strides with a large lcm)
+        // plain strided gather for this pass (strides with a larger lcm)
         const int64_t G = (int64_t)gridDim.x * blockDim.x;
         int64_t j = (int64_t)blockIdx.x * blockDim.x + tid;
         int64_t idx[4], stp[4];
@@ -202,7 +201,6 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
         int *J = common;
         int *lanebase = J + (TM_LMAX + 1);
         int *spanC = lanebase + 4 * TM_LMAX;
-        int *spanLead = spanC + TM_MAXSPANS;
 
         for (int l = tid; l <= L; l += TM_THREADS)
             J[l] = (int)(((int64_t)l * N + L - 1) / L);
@@ -213,7 +211,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
         }
         if (tid == 0) {
             for (int s = 0; s < TM_STAGES; s++) {
-                mbar_init(smem_u32(&bar_full[s]), 32);
+                mbar_init(smem_u32(&bar_full[s]), 32 * TM_PROD_WARPS);
                 mbar_init(smem_u32(&bar_empty[s]), TM_CONS_WARPS);
             }
             s_abort = 0;
@@ -221,18 +219,37 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         }
         __syncthreads();
+        // per lane and sub-vector: slot offset of the lane's first value,
+        // packed with the index of the span that holds it (span < 32)
         for (int e = tid; e < 4 * L; e += TM_THREADS) {
             int i = e / L, l = e - i * L;
             int w = l / m[i], p = l - w * m[i];
             int64_t r = (int64_t)alpha[i] * J[l] - (int64_t)w * N - spanC[sb[i] + p];
-            lanebase[i * TM_LMAX + l] = slot0[i] + p * SL[i] + (int)r;
+            lanebase[i * TM_LMAX + l] = ((slot0[i] + p * SL[i] + (int)r) << 5) | (sb[i] + p);
         }
         __syncthreads();
         const int maxlen = (int)((N + L - 1) / L);
         const int ntiles = (maxlen + T - 1) / T;
 
-        if (warp == TM_CONS_WARPS) {
-            // ---------------- producer warp ----------------
+        if (warp >= TM_CONS_WARPS) {
+            // ---------------- producer warps ----------------
+            // span sp belongs to this lane for the whole kernel
+            const int sp = (warp - TM_CONS_WARPS) + TM_PROD_WARPS * lane;
+            const bool owner = sp < nspans;
+            int sp_i = 0, sp_alpha = 0;
+            int64_t sp_gam = 0, sp_C = 0;
+            uint32_t sp_doff = 0;
+            const float *sp_row = src;
+            if (owner) {
+                sp_i = (sp >= sb[1]) + (sp >= sb[2]) + (sp >= sb[3]);
+                const int sp_p = sp - sb[sp_i];
+                sp_alpha = alpha[sp_i];
+                sp_gam = gam[sp_i];
+                sp_C = spanC[sp];
+                sp_doff = 4u * (uint32_t)(slot0[sp_i] + sp_p * SL[sp_i]);
+                sp_row = src + (int64_t)sp_i * Np;
+            }
+            const uint32_t stage_base = smem_u32(stage0);
             int issued[TM_STAGES];
 #pragma unroll
             for (int s = 0; s < TM_STAGES; s++)
@@ -250,53 +267,41 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
                 }
                 const int t0 = tile * T;
                 const int Tt = min(T, maxlen - t0);
-                float *sdata = stage0 + s * tm_stage_words();
-                int *laneoff = (int *)(sdata + tm_stage_data_words());
+                int *lead = (int *)(stage0 + s * tm_stage_words() + tm_stage_data_words());
                 const uint32_t full = smem_u32(&bar_full[s]);
-                // byte count of this lane's spans
+                const uint32_t d = stage_base + 4u * (uint32_t)(s * tm_stage_words()) + sp_doff;
+                int64_t addr = 0;
+                int len = 0, as = 0;
                 uint32_t bytes = 0;
-                for (int sp = lane; sp < nspans; sp += 32) {
-                    int i = (sp >= sb[1]) + (sp >= sb[2]) + (sp >= sb[3]);
-                    int64_t addr = (int64_t)spanC[sp] + (int64_t)alpha[i] * t0 + gam[i];
-                    while (addr >= N)
+                bool wrap = false;
+                if (owner) {
+                    addr = sp_C + (int64_t)sp_alpha * t0 + sp_gam;   // < 3N
+                    if (addr >= N)
                         addr -= N;
-                    int len = alpha[i] * Tt;
-                    int as = (int)addr & ~3;
-                    spanLead[sp] = (int)addr - as;
-                    if (addr + len <= N) {
-                        bytes += 16u * (uint32_t)(((int)addr - as + len + 3) >> 2);
-                    } else {
-                        int e2 = ((int)(addr + len - N) + 3) & ~3;
-                        bytes += 4u * (uint32_t)((int)N - as) + 4u * (uint32_t)e2;
-                    }
+                    if (addr >= N)
+                        addr -= N;
+                    len = sp_alpha * Tt;
+                    as = (int)addr & ~3;
+                    lead[sp] = (int)addr - as;
+                    wrap = addr + len > N;
+                    bytes = wrap ? 4u * (uint32_t)((int)N - as) +
+                                       4u * (uint32_t)(((int)(addr + len - N) + 3) & ~3)
+                                 : 16u * (uint32_t)(((int)addr - as + len + 3) >> 2);
                 }
+                uint32_t total = bytes;
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1)
-                    bytes += __shfl_xor_sync(0xffffffffu, bytes, off);
+                    total += __shfl_xor_sync(0xffffffffu, total, off);
                 if (lane == 0)
-                    mbar_expect_tx(full, bytes);
+                    mbar_expect_tx(full, total);
                 __syncwarp();
-                for (int e = lane; e < 4 * L; e += 32) {
-                    int i = e / L, l = e - i * L;
-                    laneoff[i * TM_LMAX + l] = lanebase[i * TM_LMAX + l] + spanLead[sb[i] + l % m[i]];
-                }
-                const uint32_t sbase = smem_u32(sdata);
-                for (int sp = lane; sp < nspans; sp += 32) {
-                    int i = (sp >= sb[1]) + (sp >= sb[2]) + (sp >= sb[3]);
-                    int p = sp - sb[i];
-                    int64_t addr = (int64_t)spanC[sp] + (int64_t)alpha[i] * t0 + gam[i];
-                    while (addr >= N)
-                        addr -= N;
-                    int len = alpha[i] * Tt;
-                    int as = (int)addr & ~3;
-                    const float *row = src + (int64_t)i * Np;
-                    uint32_t d = sbase + 4u * (uint32_t)(slot0[i] + p * SL[i]);
-                    if (addr + len <= N) {
-                        bulk_g2s(d, row + as, 16u * (uint32_t)(((int)addr - as + len + 3) >> 2), full);
+                if (owner) {
+                    if (!wrap) {
+                        bulk_g2s(d, sp_row + as, bytes, full);
                     } else {
-                        int e2 = ((int)(addr + len - N) + 3) & ~3;
-                        bulk_g2s(d, row + as, 4u * (uint32_t)((int)N - as), full);
-                        bulk_g2s(d + 4u * (uint32_t)((int)N - as), row, 4u * (uint32_t)e2, full);
+                        const int e2 = ((int)(addr + len - N) + 3) & ~3;
+                        bulk_g2s(d, sp_row + as, 4u * (uint32_t)((int)N - as), full);
+                        bulk_g2s(d + 4u * (uint32_t)((int)N - as), sp_row, 4u * (uint32_t)e2, full);
                     }
                 }
                 mbar_arrive(full);
@@ -308,12 +313,16 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
                     atomicOr(&st->status, WL_ETIMEOUT);
         } else {
             // ---------------- consumer warps ----------------
+            float *dstk[4], *outk[4];
             int mode[4];   // 0: none of sub-vector k is returned, 1: all, 2: check each value
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                int64_t q0 = k * N, q1 = q0 + N;
+                const int64_t q0 = k * N, q1 = q0 + N;
                 mode[k] = (q1 <= w0 || q0 >= w1) ? 0 : ((q0 >= w0 && q1 <= w1) ? 1 : 2);
+                dstk[k] = dst + k * Np;
+                outk[k] = mode[k] == 1 ? out + (q0 - w0) : out;
             }
+            uint32_t emax = 0;
             int it = 0;
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
                 const int s = it % TM_STAGES;
@@ -328,29 +337,33 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
                 const int t0 = tile * T;
                 const int Tt = min(T, maxlen - t0);
                 const float *sdata = stage0 + s * tm_stage_words();
-                const int *laneoff = (const int *)(sdata + tm_stage_data_words());
-                const uint32_t mT = magic_div((uint32_t)Tt);
-                const int npairs = L * Tt;
-                for (int f = tid; f < npairs; f += TM_CONS_THREADS) {
-                    const int l = (int)fast_div((uint32_t)f, (uint32_t)Tt, mT);
-                    const int t = f - l * Tt;
+                const int *lead = (const int *)(sdata + tm_stage_data_words());
+                const int chunks = (Tt + 31) >> 5;
+                const int ntasks = L * chunks;
+                for (int task = warp; task < ntasks; task += TM_CONS_WARPS) {
+                    const int l = chunks == 2 ? task >> 1 : task / chunks;
+                    const int t = (task - l * chunks) * 32 + lane;
                     const int jl = J[l];
                     const int tt = t0 + t;
-                    if (tt >= J[l + 1] - jl)
+                    if (t >= Tt || tt >= J[l + 1] - jl)
                         continue;
                     float g[4], y[4];
 #pragma unroll
-                    for (int i = 0; i < 4; i++)
-                        g[i] = sdata[laneoff[i * TM_LMAX + l] + alpha[i] * t];
+                    for (int i = 0; i < 4; i++) {
+                        const int lb = lanebase[i * TM_LMAX + l];
+                        g[i] = sdata[(lb >> 5) + lead[lb & 31] + alpha[i] * t];
+                    }
                     wl_xform4(g, c, y);
                     const int64_t j = (int64_t)jl + tt;
 #pragma unroll
                     for (int kk = 0; kk < 4; kk++) {
-                        dst[kk * Np + j] = y[kk];
-                        lo += term32_fast(y[kk], bad);
-                        if (mode[kk]) {
+                        dstk[kk][j] = y[kk];
+                        lo += term32(y[kk], emax);
+                        if (mode[kk] == 1) {
+                            outk[kk][j] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
+                        } else if (mode[kk] == 2) {
                             const int64_t q = kk * N + j;
-                            if (mode[kk] == 1 || (q >= w0 && q < w1))
+                            if (q >= w0 && q < w1)
                                 out[q - w0] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
                         }
                     }
@@ -359,6 +372,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
                 if (lane == 0)
                     mbar_arrive(smem_u32(&bar_empty[s]));
             }
+            bad = emax >= 135u ? 1u : 0u;
         }
     }
 
