@@ -17,21 +17,22 @@
 //                     the stage's "full" mbarrier.  Span sp belongs to lane
 //                     sp / 4 of producer warp sp % 4: a single warp issues
 //                     bulk copies too slowly for spans of about 1 KB;
-//   consumer warps -- wait for the stage; each warp task is one lane and 32
-//                     consecutive lane times, so lane-table reads are
-//                     broadcasts, shared-memory gathers have odd stride
-//                     alpha_i (no bank conflicts) and every store instruction
-//                     writes 128 contiguous bytes; transform, store the new
-//                     pool and the returned values, accumulate the exact sum
-//                     of squares, then release the stage on its "empty"
-//                     mbarrier.
+//   consumer warps -- wait for the stage; each warp owns whole lanes (three
+//                     of the 45) and walks their lane times 64 at a time (two
+//                     independent values per thread), so lane-table reads are
+//                     broadcasts done once per lane,
+//                     shared-memory gathers have odd stride alpha_i (no bank
+//                     conflicts) and every store instruction writes 128
+//                     contiguous bytes; transform, store the new pool and the
+//                     returned values, accumulate the exact sum of squares,
+//                     then release the stage on its "empty" mbarrier.
 // Every wait is bounded by a cycle budget; on expiry the CTA records
 // WALLACE_ETIMEOUT in the state, stops issuing work, waits (bounded) for its
 // copies still in flight, and leaves.
 #include "wl_common.cuh"
 #include "wl_launch.h"
 
-#define TM_CONS_WARPS 16
+#define TM_CONS_WARPS 15          /* 45 lanes = 3 per consumer warp */
 #define TM_CONS_THREADS (TM_CONS_WARPS * 32)
 #define TM_PROD_WARPS 4          /* one warp issues a bulk copy only every ~80 cycles */
 #define TM_THREADS (TM_CONS_THREADS + 32 * TM_PROD_WARPS)
@@ -338,33 +339,44 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
                 const int Tt = min(T, maxlen - t0);
                 const float *sdata = stage0 + s * tm_stage_words();
                 const int *lead = (const int *)(sdata + tm_stage_data_words());
-                const int chunks = (Tt + 31) >> 5;
-                const int ntasks = L * chunks;
-                for (int task = warp; task < ntasks; task += TM_CONS_WARPS) {
-                    const int l = chunks == 2 ? task >> 1 : task / chunks;
-                    const int t = (task - l * chunks) * 32 + lane;
+                for (int l = warp; l < L; l += TM_CONS_WARPS) {
                     const int jl = J[l];
-                    const int tt = t0 + t;
-                    if (t >= Tt || tt >= J[l + 1] - jl)
-                        continue;
-                    float g[4], y[4];
+                    const int tmax = min(Tt, J[l + 1] - jl - t0);   // lane times of lane l in this tile
+                    const float *gp[4];
 #pragma unroll
                     for (int i = 0; i < 4; i++) {
                         const int lb = lanebase[i * TM_LMAX + l];
-                        g[i] = sdata[(lb >> 5) + lead[lb & 31] + alpha[i] * t];
+                        gp[i] = sdata + (lb >> 5) + lead[lb & 31];
                     }
-                    wl_xform4(g, c, y);
-                    const int64_t j = (int64_t)jl + tt;
+                    const int64_t jb = (int64_t)jl + t0;
+                    for (int t = lane; t < tmax; t += 64) {
+                        const bool v2 = t + 32 < tmax;
+                        float g[4], h[4], y[4], z[4];
 #pragma unroll
-                    for (int kk = 0; kk < 4; kk++) {
-                        dstk[kk][j] = y[kk];
-                        lo += term32(y[kk], emax);
-                        if (mode[kk] == 1) {
-                            outk[kk][j] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
-                        } else if (mode[kk] == 2) {
-                            const int64_t q = kk * N + j;
-                            if (q >= w0 && q < w1)
-                                out[q - w0] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
+                        for (int i = 0; i < 4; i++) {
+                            g[i] = gp[i][alpha[i] * t];
+                            h[i] = v2 ? gp[i][alpha[i] * (t + 32)] : 0.f;
+                        }
+                        wl_xform4(g, c, y);
+                        wl_xform4(h, c, z);
+                        const int64_t j = jb + t;
+#pragma unroll
+                        for (int kk = 0; kk < 4; kk++) {
+                            dstk[kk][j] = y[kk];
+                            if (v2) dstk[kk][j + 32] = z[kk];
+                            lo += term32(y[kk], emax);
+                            if (v2) lo += term32(z[kk], emax);
+                            if (mode[kk] == 1) {
+                                outk[kk][j] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
+                                if (v2) outk[kk][j + 32] = __fadd_rn(mu, __fmul_rn(sigma, z[kk]));
+                            } else if (mode[kk] == 2) {
+                                int64_t q = kk * N + j;
+                                if (q >= w0 && q < w1)
+                                    out[q - w0] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
+                                q += 32;
+                                if (v2 && q >= w0 && q < w1)
+                                    out[q - w0] = __fadd_rn(mu, __fmul_rn(sigma, z[kk]));
+                            }
                         }
                     }
                 }
