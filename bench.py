@@ -291,6 +291,37 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def precision_study(passes: int = 1000, N: int = 1 << 22, seed: int = 3):
+    """Binary32 pool (exact integer sum of squares, binary64 scale) against the
+    binary64-pool reference mode on the same GPU, same seed and parameters:
+    max and RMS deviation after `passes` passes and the per-pass drift
+    q_k / S_{k-1} - 1 of each mode."""
+    import numpy as np
+    import torch  # noqa: F401  (CUDA context)
+    from paper_1004_3114_gb300 import wallace as W
+    res = {"metric": "precision study", "passes": passes, "N": N, "seed": seed, "cases": []}
+    for n in (4, 8):
+        g32 = W.Wallace(n, N, seed, 1.0, mode=W.FP32)
+        g64 = W.Wallace(n, N, seed, 1.0, mode=W.FP64POOL)
+        d32, d64 = [], []
+        for _ in range(passes):
+            g32.pass_()
+            g64.pass_()
+            d32.append(g32.stats().drift)
+            d64.append(g64.stats().drift)
+        p32, p64 = g32.pool64(), g64.pool64()
+        dev = np.abs(p32 - p64)
+        res["cases"].append({
+            "n": n, "max_abs_dev": float(dev.max()), "rms_dev": float(np.sqrt((dev ** 2).mean())),
+            "max_abs_value": float(np.abs(p64).max()),
+            "fp32_drift_max": float(np.max(np.abs(d32))), "fp32_drift_rms": float(np.sqrt(np.mean(np.square(d32)))),
+            "fp64_drift_max": float(np.max(np.abs(d64))),
+            "status": [int(g32.sync()), int(g64.sync())]})
+        g32.close()
+        g64.close()
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,7 +331,12 @@ def main():
     ap.add_argument("--cpu-passes", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="binary32 vs binary64 pool study (N=2^22, n=4 and 8, 1000 passes) instead of the benchmark")
     args = ap.parse_args()
+    if args.precision_study:
+        precision_study()
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))

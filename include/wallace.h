@@ -190,6 +190,81 @@ int wallace_clear_error(wallace_t *h);
 /* wallace_returned_per_pass -- R for the handle (host value, no sync). */
 int64_t wallace_returned_per_pass(const wallace_t *h);
 
+/* ---- many generators in one launch ------------------------------------ */
+/*
+ * A batch holds `count` independent generators (Section 9: independent
+ * streams need no communication after initialisation) with their own pool
+ * sizes and seeds, in one device arena.  wallace_batch_run advances every
+ * generator by the same number of passes in ONE persistent kernel launch
+ * (a CUDA graph: work-counter reset + kernel).  CTAs take whole generators,
+ * largest pool first; small pools stay in shared memory across all passes.
+ * Each generator produces exactly the values a handle made by
+ * wallace_create_ex(n, N[s], seed[s], 0, frac, WALLACE_FP32, ...) would:
+ * run(P1) then run(P2) equals run(P1 + P2), and both equal P passes of
+ * wallace_fill with count R_s per pass.
+ */
+typedef struct wallace_batch wallace_batch_t;
+
+/*
+ * wallace_batch_create -- `count` >= 1 generators; N and seed are host
+ * arrays of `count` values (4 <= N[s], n*N[s] <= 2^30); n in {4, 8} and
+ * frac as in wallace_create.  Initial pools are made here (synchronous).
+ * Errors: WALLACE_EINVAL, WALLACE_ENOMEM, WALLACE_ECUDA.
+ */
+int wallace_batch_create(int count, int n, const int64_t *N, const uint32_t *seed, double frac,
+                         void *cuda_stream, wallace_batch_t **out);
+
+/* wallace_batch_destroy -- synchronise and free everything.  NULL-safe. */
+void wallace_batch_destroy(wallace_batch_t *b);
+
+/*
+ * wallace_batch_run -- `passes` passes of every generator, one launch.
+ *   out   device buffer, or NULL to discard the returned values.  Generator s
+ *         writes its passes*R_s returned values (mu + sigma*y, pass-major) to
+ *         out + wallace_batch_out_offset(b, s, passes); the total size is
+ *         wallace_batch_out_offset(b, count, passes).
+ * Asynchronous on the batch's stream.
+ */
+int wallace_batch_run(wallace_batch_t *b, int64_t passes, float *out, float mu, float sigma);
+
+/* wallace_batch_out_offset -- passes * (sum of R over generators before s);
+ * s == count gives the total.  -1 on bad arguments. */
+int64_t wallace_batch_out_offset(const wallace_batch_t *b, int s, int64_t passes);
+
+/* wallace_batch_returned_per_pass -- R_s; -1 on bad arguments. */
+int64_t wallace_batch_returned_per_pass(const wallace_batch_t *b, int s);
+
+/* wallace_batch_sync -- wait; returns the OR of every generator's status. */
+int wallace_batch_sync(wallace_batch_t *b);
+
+/* wallace_batch_stats -- synchronise and copy generator s's scalars. */
+int wallace_batch_stats(wallace_batch_t *b, int s, wallace_stats_t *out);
+
+/* wallace_batch_get_pool -- synchronise and copy generator s's pool to HOST
+ * memory (n*N[s] floats, sub-vector-major). */
+int wallace_batch_get_pool(wallace_batch_t *b, int s, float *host_out);
+
+/*
+ * wallace_batch_set_tuning / wallace_batch_get_tuning -- launch shape: CTAs
+ * per SM (capped by occupancy), lane-times per tile of the tiled gather
+ * (4 <= etarget <= 2560), and the largest pool (n*N values) kept in shared
+ * memory across passes (at most ~8400 values fit).
+ */
+int wallace_batch_set_tuning(wallace_batch_t *b, int ctas_per_sm, int etarget, int64_t fused_max);
+int wallace_batch_get_tuning(const wallace_batch_t *b, int *ctas_per_sm, int *etarget,
+                             int64_t *fused_max);
+
+/*
+ * wallace_batch_autotune -- pick the launch shape.  If `cache_path` (may be
+ * NULL) holds an entry for this device and batch shape (count, n, frac and
+ * the histogram of pool sizes), use it.  Otherwise time `trial_passes`
+ * passes for each candidate (CTAs/SM in {1,2,3}, tile in {1280,1920,2560},
+ * shared-memory pool limit in {2048,4096,8192}) on a snapshot of the
+ * generators -- the generators themselves do not advance -- keep the fastest
+ * and append it to `cache_path` as one JSON object per line.  Synchronous.
+ */
+int wallace_batch_autotune(wallace_batch_t *b, const char *cache_path, int trial_passes);
+
 /*
  * wallace_pass_static -- one pass that allocates nothing.  The paper has no
  * counterpart: this is a deployment entry point.

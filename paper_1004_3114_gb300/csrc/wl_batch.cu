@@ -1,0 +1,770 @@
+// Many independent Wallace generators (Brent's RANN4 paper: independent
+// streams need no communication after initialisation, Section 9) advanced
+// together in one persistent launch.
+//
+// The CTAs take whole generators from a work counter, largest pool first.  A
+// CTA runs every pass of its generator itself, so the end-of-pass sum of
+// squares and chi-squared rescale (Eq. 3) are CTA-local and no CTA ever waits
+// for another:
+//   * a pool that fits in shared memory is loaded once and regenerated there
+//     for all passes (only the returned values go to global memory);
+//   * a larger n = 4 pool whose pass has strides with lcm <= 315 runs the
+//     lane-tiled gather (wl_tiled_body.cuh) over all of its tiles;
+//   * anything else runs the plain strided gather.
+// The launch is a CUDA graph (work-counter reset + kernel) whose kernel
+// arguments are updated per run.  An autotuner times candidate settings
+// (CTAs per SM, tile size, shared-memory pool limit) on a snapshot of the
+// generators and caches the best in a JSON-lines file.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "wallace.h"
+#include "wl_launch.h"
+#include "wl_tiled_body.cuh"
+
+#define BT_THREADS 256
+
+namespace {
+
+struct BatchStream {
+    float *pool[2];
+    WlDevState *st;
+    int64_t N, Np, R;
+    int64_t out_pref;   // sum of R over the streams before this one (stream order)
+    int32_t cur;
+    int32_t n;
+};
+
+struct BatchArgs {
+    BatchStream *streams;
+    const int *order;
+    int *queue;
+    int count;
+    int etarget;
+    int64_t passes;
+    int64_t fused_max;   // pools with n*N <= this stay in shared memory
+    float *out;
+    float mu, sigma;
+};
+
+template <int NSUB>
+__device__ void gather_range_n(const float *src, float *dst, int64_t N, int64_t Np, const int32_t *alpha,
+                               const int64_t *gam, float c, float *out, int64_t w1, float mu,
+                               float sigma, uint64_t &lo, uint64_t &hi, uint32_t &bad)
+{
+    const int64_t G = blockDim.x;
+    int64_t j = threadIdx.x;
+    int64_t idx[NSUB], stp[NSUB];
+#pragma unroll
+    for (int i = 0; i < NSUB; i++) {
+        idx[i] = (int64_t)(((uint64_t)alpha[i] * (uint64_t)(j < N ? j : 0) + (uint64_t)gam[i]) % (uint64_t)N);
+        stp[i] = (int64_t)(((uint64_t)alpha[i] * (uint64_t)G) % (uint64_t)N);
+    }
+    for (; j < N; j += G) {
+        float g[NSUB], y[NSUB];
+#pragma unroll
+        for (int i = 0; i < NSUB; i++) {
+            g[i] = src[i * Np + idx[i]];
+            idx[i] += stp[i];
+            if (idx[i] >= N)
+                idx[i] -= N;
+        }
+        if constexpr (NSUB == 4)
+            wl_xform4(g, c, y);
+        else
+            wl_xform8(g, c, y);
+#pragma unroll
+        for (int k = 0; k < NSUB; k++) {
+            dst[k * Np + j] = y[k];
+            wl_add128(lo, hi, wl_term32(y[k], bad), 0);
+            const int64_t q = k * N + j;
+            if (q < w1)
+                out[q] = __fadd_rn(mu, __fmul_rn(sigma, y[k]));
+        }
+    }
+}
+
+// All passes of one generator whose pool fits in shared memory.
+template <int NSUB>
+__device__ void run_fused(const BatchStream &d, const BatchArgs &a, float *sm, uint64_t *red,
+                          int32_t *s_prm)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int N = (int)d.N, nu = NSUB * N;
+    float *src = sm, *dst = sm + nu;
+    const float *g0 = d.pool[d.cur];
+    for (int q = tid; q < nu; q += nth) {
+        int i = q / N;
+        src[q] = g0[(int64_t)i * d.Np + (q - i * N)];
+    }
+    float *obase = a.out ? a.out + a.passes * d.out_pref : nullptr;
+    for (int64_t p = 0; p < a.passes; p++) {
+        __syncthreads();
+        if (tid == 0) {
+            for (int i = 0; i < NSUB; i++) {
+                s_prm[i] = d.st->next.alpha[i];
+                s_prm[8 + i] = (int32_t)d.st->next.gamma[i];
+            }
+            s_prm[16] = __float_as_int(d.st->next.c32);
+        }
+        __syncthreads();
+        const float c = __int_as_float(s_prm[16]);
+        int idx[NSUB], stp[NSUB];
+#pragma unroll
+        for (int i = 0; i < NSUB; i++) {
+            idx[i] = (int)(((int64_t)s_prm[i] * (tid < N ? tid : 0) + s_prm[8 + i]) % N);
+            stp[i] = (int)(((int64_t)s_prm[i] * nth) % N);
+        }
+        float *o = obase ? obase + p * d.R : nullptr;
+        const int w1 = o ? (int)d.R : 0;
+        uint64_t lo = 0, hi = 0;
+        uint32_t bad = 0;
+        for (int j = tid; j < N; j += nth) {
+            float g[NSUB], y[NSUB];
+#pragma unroll
+            for (int i = 0; i < NSUB; i++) {
+                g[i] = src[i * N + idx[i]];
+                idx[i] += stp[i];
+                if (idx[i] >= N)
+                    idx[i] -= N;
+            }
+            if constexpr (NSUB == 4)
+                wl_xform4(g, c, y);
+            else
+                wl_xform8(g, c, y);
+#pragma unroll
+            for (int k = 0; k < NSUB; k++) {
+                const int q = k * N + j;
+                dst[q] = y[k];
+                wl_add128(lo, hi, wl_term32(y[k], bad), 0);
+                if (q < w1)
+                    o[q] = __fadd_rn(a.mu, __fmul_rn(a.sigma, y[k]));
+            }
+        }
+        wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
+        __syncthreads();
+        if (tid == 0)
+            wl_finalise(d.st, NSUB, N, nu, (double)dst[nu - 1], false, true);
+        float *t = src;
+        src = dst;
+        dst = t;
+    }
+    __syncthreads();
+    float *g1 = d.pool[d.cur];
+    for (int q = tid; q < nu; q += nth) {
+        int i = q / N;
+        g1[(int64_t)i * d.Np + (q - i * N)] = src[q];
+    }
+}
+
+// All passes of one generator from global memory; returns the final buffer index.
+template <int NSUB>
+__device__ int run_global(const BatchStream &d, const BatchArgs &a, float *sm, uint64_t *red)
+{
+    const int tid = threadIdx.x;
+    const int64_t N = d.N, nu = NSUB * N;
+    int cur = d.cur;
+    float *obase = a.out ? a.out + a.passes * d.out_pref : nullptr;
+    for (int64_t p = 0; p < a.passes; p++) {
+        __syncthreads();   // the previous pass's parameters are written
+        int32_t alpha[NSUB];
+        int64_t gam[NSUB];
+#pragma unroll
+        for (int i = 0; i < NSUB; i++) {
+            alpha[i] = d.st->next.alpha[i];
+            gam[i] = d.st->next.gamma[i];
+        }
+        const float c = d.st->next.c32;
+        const float *src = d.pool[cur];
+        float *dst = d.pool[1 - cur];
+        float *o = obase ? obase + p * d.R : nullptr;
+        uint64_t lo = 0, hi = 0;
+        uint32_t bad = 0;
+        if constexpr (NSUB == 4) {
+            WlTileJob job;
+            job.src = src;
+            job.dst = dst;
+            job.N = N;
+            job.Np = d.Np;
+            for (int i = 0; i < 4; i++) {
+                job.alpha[i] = alpha[i];
+                job.gam[i] = gam[i];
+            }
+            job.c = c;
+            job.out = o;
+            job.w0 = 0;
+            job.w1 = o ? d.R : 0;
+            job.mu = a.mu;
+            job.sigma = a.sigma;
+            const int L = wl_lcm4(job.alpha);
+            if (wl_tiled_ok(L, N))
+                wl_tiled4_tiles(job, L, 0, 1, a.etarget, sm, lo, hi, bad);
+            else
+                wl_gather4_range(job, tid, blockDim.x, lo, hi, bad);
+        } else {
+            gather_range_n<NSUB>(src, dst, N, d.Np, alpha, gam, c, o, o ? d.R : 0, a.mu, a.sigma,
+                                 lo, hi, bad);
+        }
+        wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
+        __syncthreads();
+        if (tid == 0)
+            wl_finalise(d.st, NSUB, N, nu, (double)__ldcg(&dst[wl_phys(nu - 1, N, d.Np)]), false, true);
+        cur = 1 - cur;
+    }
+    return cur;
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
+{
+    extern __shared__ __align__(16) float smem[];
+    __shared__ uint64_t red[3 * (BT_THREADS / 32)];
+    __shared__ int32_t s_prm[20];
+    __shared__ int s_k;
+    const int tid = threadIdx.x;
+    const int64_t smem_values = (int64_t)(tl_smem_bytes() / sizeof(float));
+    while (true) {
+        __syncthreads();
+        if (tid == 0)
+            s_k = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int k = s_k;
+        if (k >= a.count)
+            break;
+        const BatchStream d = a.streams[a.order[k]];
+        const int64_t nu = (int64_t)d.n * d.N;
+        if (nu <= a.fused_max && 2 * nu <= smem_values) {
+            if (d.n == 4)
+                run_fused<4>(d, a, smem, red, s_prm);
+            else
+                run_fused<8>(d, a, smem, red, s_prm);
+        } else {
+            const int cur = d.n == 4 ? run_global<4>(d, a, smem, red) : run_global<8>(d, a, smem, red);
+            if (tid == 0)
+                a.streams[a.order[k]].cur = cur;
+        }
+    }
+}
+
+struct Tuning {
+    int ctas_per_sm = 2;
+    int etarget = TL_EMAX;
+    int64_t fused_max = 4096;
+};
+
+} // namespace
+
+struct wallace_batch {
+    int count = 0, n = 4;
+    double frac = 1.0;
+    std::vector<int64_t> N, Np, R, pref;
+    std::vector<int> order;
+    std::vector<size_t> pool_off;   // float offset of each stream's first buffer in the arena
+    size_t arena_floats = 0;
+    float *arena = nullptr;
+    WlDevState *states = nullptr;
+    BatchStream *d_streams = nullptr;
+    int *d_order = nullptr;
+    int *d_queue = nullptr;
+    cudaStream_t stream = nullptr;
+    int sm_count = 1, device = 0, max_ctas_per_sm = 1;
+    Tuning tune;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t knode = nullptr;
+    int graph_ctas = 0;
+    int status = 0;
+    double last_run_ms = 0.0;
+};
+
+namespace {
+
+int bfail(wallace_batch_t *b, cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return WALLACE_OK;
+    if (b)
+        b->status |= WALLACE_ECUDA;
+    return WALLACE_ECUDA;
+}
+
+BatchArgs make_args(wallace_batch_t *b, int64_t passes, float *out, float mu, float sigma)
+{
+    BatchArgs a;
+    a.streams = b->d_streams;
+    a.order = b->d_order;
+    a.queue = b->d_queue;
+    a.count = b->count;
+    a.etarget = b->tune.etarget;
+    a.passes = passes;
+    a.fused_max = b->tune.fused_max;
+    a.out = out;
+    a.mu = mu;
+    a.sigma = sigma;
+    return a;
+}
+
+cudaError_t ensure_configured()
+{
+    static bool done = false;
+    if (done)
+        return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tl_smem_bytes());
+    if (e == cudaSuccess)
+        done = true;
+    return e;
+}
+
+// Graph: reset the work counter, then the persistent kernel.  Rebuilt when the
+// CTA count changes; otherwise only the kernel's arguments are updated.
+cudaError_t launch_graph(wallace_batch_t *b, const BatchArgs &args)
+{
+    cudaError_t e = ensure_configured();
+    if (e != cudaSuccess)
+        return e;
+    const int ctas = b->sm_count * std::min(b->tune.ctas_per_sm, b->max_ctas_per_sm);
+    BatchArgs a = args;
+    void *params[] = {&a};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.func = (void *)batch_kernel;
+    kp.gridDim = dim3(ctas);
+    kp.blockDim = dim3(BT_THREADS);
+    kp.sharedMemBytes = (unsigned)tl_smem_bytes();
+    kp.kernelParams = params;
+    if (!b->exec || b->graph_ctas != ctas) {
+        if (b->exec)
+            cudaGraphExecDestroy(b->exec);
+        if (b->graph)
+            cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        e = cudaGraphCreate(&b->graph, 0);
+        if (e != cudaSuccess)
+            return e;
+        cudaMemsetParams mp;
+        memset(&mp, 0, sizeof(mp));
+        mp.dst = b->d_queue;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = 1;
+        mp.height = 1;
+        cudaGraphNode_t mnode;
+        e = cudaGraphAddMemsetNode(&mnode, b->graph, nullptr, 0, &mp);
+        if (e == cudaSuccess)
+            e = cudaGraphAddKernelNode(&b->knode, b->graph, &mnode, 1, &kp);
+        if (e == cudaSuccess)
+            e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess)
+            return e;
+        b->graph_ctas = ctas;
+    } else {
+        e = cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaGraphLaunch(b->exec, b->stream);
+}
+
+std::string tune_key(const wallace_batch_t *b)
+{
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, b->device);
+    // pool-size histogram on powers of two, plus count, n and frac
+    std::vector<int> hist(40, 0);
+    for (int s = 0; s < b->count; s++) {
+        int lg = 0;
+        while (((int64_t)1 << (lg + 1)) <= b->N[s] && lg < 39)
+            lg++;
+        hist[lg]++;
+    }
+    std::string k = std::string(prop.name) + "|sm" + std::to_string(b->sm_count) + "|n" +
+                    std::to_string(b->n) + "|count" + std::to_string(b->count) + "|frac" +
+                    std::to_string(b->frac) + "|h";
+    for (int v : hist)
+        k += std::to_string(v) + ",";
+    for (char &ch : k)
+        if (ch == '"' || ch == '\n')
+            ch = '_';
+    return k;
+}
+
+bool read_cached(const char *path, const std::string &key, Tuning *t)
+{
+    if (!path)
+        return false;
+    FILE *f = fopen(path, "r");
+    if (!f)
+        return false;
+    char line[8192];
+    bool found = false;
+    const std::string needle = "\"key\": \"" + key + "\"";
+    while (fgets(line, sizeof line, f)) {
+        if (!strstr(line, needle.c_str()))
+            continue;
+        int ctas = 0, et = 0;
+        long long fm = 0;
+        const char *pc = strstr(line, "\"ctas_per_sm\": ");
+        const char *pe = strstr(line, "\"etarget\": ");
+        const char *pf = strstr(line, "\"fused_max\": ");
+        if (pc && pe && pf && sscanf(pc, "\"ctas_per_sm\": %d", &ctas) == 1 &&
+            sscanf(pe, "\"etarget\": %d", &et) == 1 && sscanf(pf, "\"fused_max\": %lld", &fm) == 1) {
+            t->ctas_per_sm = ctas;
+            t->etarget = et;
+            t->fused_max = fm;
+            found = true;   // the last matching line wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+} // namespace
+
+extern "C" {
+
+int wallace_batch_create(int count, int n, const int64_t *N, const uint32_t *seed, double frac,
+                         void *cuda_stream, wallace_batch_t **out)
+{
+    if (!out || count < 1 || !N || !seed || (n != 4 && n != 8) || !(frac > 0.0 && frac <= 1.0))
+        return WALLACE_EINVAL;
+    *out = nullptr;
+    wallace_batch_t *b = new (std::nothrow) wallace_batch;
+    if (!b)
+        return WALLACE_ENOMEM;
+    b->count = count;
+    b->n = n;
+    b->frac = frac;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->N.resize(count);
+    b->Np.resize(count);
+    b->R.resize(count);
+    b->pref.resize(count);
+    b->pool_off.resize(count);
+    int64_t pr = 0;
+    for (int s = 0; s < count; s++) {
+        const int64_t Ns = N[s];
+        if (Ns < 4 || (int64_t)n * Ns > ((int64_t)1 << 30)) {
+            delete b;
+            return WALLACE_EINVAL;
+        }
+        const int64_t nu = (int64_t)n * Ns;
+        int64_t R = (int64_t)(frac * (double)nu);
+        if (R > nu - 1)
+            R = nu - 1;
+        if (R < 1) {
+            delete b;
+            return WALLACE_EINVAL;
+        }
+        b->N[s] = Ns;
+        b->Np[s] = ((Ns + 8 + 63) / 64) * 64;
+        b->R[s] = R;
+        b->pref[s] = pr;
+        pr += R;
+        b->pool_off[s] = b->arena_floats;
+        b->arena_floats += 2 * (size_t)n * (size_t)b->Np[s];
+    }
+    // largest pools first (longest-processing-time order)
+    b->order.resize(count);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [&](int x, int y) { return b->N[x] > b->N[y]; });
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess)
+        e = ensure_configured();
+    if (e == cudaSuccess) {
+        int per = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel, BT_THREADS, tl_smem_bytes());
+        b->max_ctas_per_sm = per > 0 ? per : 1;
+    }
+    if (e != cudaSuccess) {
+        delete b;
+        return WALLACE_ECUDA;
+    }
+    if (cudaMalloc(&b->arena, sizeof(float) * b->arena_floats) != cudaSuccess ||
+        cudaMalloc(&b->states, sizeof(WlDevState) * (size_t)count) != cudaSuccess ||
+        cudaMalloc(&b->d_streams, sizeof(BatchStream) * (size_t)count) != cudaSuccess ||
+        cudaMalloc(&b->d_order, sizeof(int) * (size_t)count) != cudaSuccess ||
+        cudaMalloc(&b->d_queue, sizeof(int)) != cudaSuccess) {
+        wallace_batch_destroy(b);
+        return WALLACE_ENOMEM;
+    }
+    std::vector<BatchStream> hs(count);
+    for (int s = 0; s < count; s++) {
+        float *p0 = b->arena + b->pool_off[s];
+        hs[s].pool[0] = p0;
+        hs[s].pool[1] = p0 + (size_t)n * (size_t)b->Np[s];
+        hs[s].st = b->states + s;
+        hs[s].N = b->N[s];
+        hs[s].Np = b->Np[s];
+        hs[s].R = b->R[s];
+        hs[s].out_pref = b->pref[s];
+        hs[s].cur = 0;
+        hs[s].n = n;
+    }
+    e = cudaMemsetAsync(b->arena, 0, sizeof(float) * b->arena_floats, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->states, 0, sizeof(WlDevState) * (size_t)count, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_streams, hs.data(), sizeof(BatchStream) * (size_t)count,
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_order, b->order.data(), sizeof(int) * (size_t)count,
+                            cudaMemcpyHostToDevice, b->stream);
+    for (int s = 0; s < count && e == cudaSuccess; s++)
+        e = wl_launch_init(hs[s].pool[0], 0, n, b->N[s], b->Np[s], seed[s], 0, b->states + s,
+                           b->sm_count, b->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        wallace_batch_destroy(b);
+        return WALLACE_ECUDA;
+    }
+    *out = b;
+    return WALLACE_OK;
+}
+
+void wallace_batch_destroy(wallace_batch_t *b)
+{
+    if (!b)
+        return;
+    cudaStreamSynchronize(b->stream);
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    if (b->graph)
+        cudaGraphDestroy(b->graph);
+    cudaFree(b->arena);
+    cudaFree(b->states);
+    cudaFree(b->d_streams);
+    cudaFree(b->d_order);
+    cudaFree(b->d_queue);
+    delete b;
+}
+
+int64_t wallace_batch_returned_per_pass(const wallace_batch_t *b, int s)
+{
+    if (!b || s < 0 || s >= b->count)
+        return -1;
+    return b->R[s];
+}
+
+int64_t wallace_batch_out_offset(const wallace_batch_t *b, int s, int64_t passes)
+{
+    if (!b || s < 0 || s > b->count || passes < 0)
+        return -1;
+    if (s == b->count)
+        return passes * (b->pref[b->count - 1] + b->R[b->count - 1]);
+    return passes * b->pref[s];
+}
+
+int wallace_batch_run(wallace_batch_t *b, int64_t passes, float *out, float mu, float sigma)
+{
+    if (!b || passes < 0)
+        return WALLACE_EINVAL;
+    if (passes == 0)
+        return b->status;
+    cudaError_t e = launch_graph(b, make_args(b, passes, out, mu, sigma));
+    if (e != cudaSuccess)
+        return bfail(b, e);
+    return b->status;
+}
+
+int wallace_batch_sync(wallace_batch_t *b)
+{
+    if (!b)
+        return WALLACE_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess)
+        return bfail(b, e);
+    std::vector<WlDevState> s(b->count);
+    e = cudaMemcpy(s.data(), b->states, sizeof(WlDevState) * (size_t)b->count, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return bfail(b, e);
+    int st = 0;
+    for (auto &x : s)
+        st |= x.status;
+    return b->status | st;
+}
+
+int wallace_batch_stats(wallace_batch_t *b, int s, wallace_stats_t *out)
+{
+    if (!b || s < 0 || s >= b->count || !out)
+        return WALLACE_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess)
+        return bfail(b, e);
+    WlDevState x;
+    e = cudaMemcpy(&x, b->states + s, sizeof(x), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return bfail(b, e);
+    memset(out, 0, sizeof(*out));
+    out->q_lo = x.q_lo;
+    out->q_hi = x.q_hi;
+    out->q = x.q;
+    out->S = x.S;
+    out->c = x.c;
+    out->c32 = x.next.c32;
+    out->drift = x.drift;
+    out->passes = x.passes;
+    out->status = b->status | x.status;
+    out->bad = x.bad;
+    out->lcg = x.lcg;
+    for (int i = 0; i < 8; i++) {
+        out->alpha[i] = x.last.alpha[i];
+        out->gamma[i] = x.last.gamma[i];
+    }
+    out->R = b->R[s];
+    out->cursor = b->R[s];
+    out->kernel_ms = b->last_run_ms;
+    return out->status;
+}
+
+int wallace_batch_get_pool(wallace_batch_t *b, int s, float *host_out)
+{
+    if (!b || s < 0 || s >= b->count || !host_out)
+        return WALLACE_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess)
+        return bfail(b, e);
+    BatchStream d;
+    e = cudaMemcpy(&d, b->d_streams + s, sizeof(d), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return bfail(b, e);
+    for (int i = 0; i < b->n && e == cudaSuccess; i++)
+        e = cudaMemcpy(host_out + (size_t)i * b->N[s], d.pool[d.cur] + (size_t)i * b->Np[s],
+                       sizeof(float) * (size_t)b->N[s], cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? b->status : bfail(b, e);
+}
+
+int wallace_batch_set_tuning(wallace_batch_t *b, int ctas_per_sm, int etarget, int64_t fused_max)
+{
+    if (!b || ctas_per_sm < 1 || etarget < 4 || etarget > TL_EMAX || fused_max < 0)
+        return WALLACE_EINVAL;
+    b->tune.ctas_per_sm = ctas_per_sm;
+    b->tune.etarget = etarget;
+    b->tune.fused_max = fused_max;
+    return WALLACE_OK;
+}
+
+int wallace_batch_get_tuning(const wallace_batch_t *b, int *ctas_per_sm, int *etarget, int64_t *fused_max)
+{
+    if (!b)
+        return WALLACE_EINVAL;
+    if (ctas_per_sm)
+        *ctas_per_sm = std::min(b->tune.ctas_per_sm, b->max_ctas_per_sm);
+    if (etarget)
+        *etarget = b->tune.etarget;
+    if (fused_max)
+        *fused_max = b->tune.fused_max;
+    return WALLACE_OK;
+}
+
+int wallace_batch_autotune(wallace_batch_t *b, const char *cache_path, int trial_passes)
+{
+    if (!b || trial_passes < 1)
+        return WALLACE_EINVAL;
+    const std::string key = tune_key(b);
+    Tuning cached;
+    if (read_cached(cache_path, key, &cached)) {
+        b->tune = cached;
+        return WALLACE_OK;
+    }
+    // snapshot of pools, states and buffer indices: trials must not advance the generators
+    float *bk_arena = nullptr;
+    WlDevState *bk_states = nullptr;
+    BatchStream *bk_streams = nullptr;
+    cudaError_t e = cudaMalloc(&bk_arena, sizeof(float) * b->arena_floats);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&bk_states, sizeof(WlDevState) * (size_t)b->count);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&bk_streams, sizeof(BatchStream) * (size_t)b->count);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bk_arena, b->arena, sizeof(float) * b->arena_floats,
+                            cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bk_states, b->states, sizeof(WlDevState) * (size_t)b->count,
+                            cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bk_streams, b->d_streams, sizeof(BatchStream) * (size_t)b->count,
+                            cudaMemcpyDeviceToDevice, b->stream);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&t0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&t1);
+    Tuning best = b->tune;
+    float best_ms = 1e30f;
+    const int ctas_list[] = {1, 2, 3};
+    const int et_list[] = {1280, 1920, TL_EMAX};
+    const int64_t fm_list[] = {2048, 4096, 8192};
+    for (int ci = 0; ci < 3 && e == cudaSuccess; ci++) {
+        if (ctas_list[ci] > b->max_ctas_per_sm)
+            continue;
+        for (int ei = 0; ei < 3 && e == cudaSuccess; ei++)
+            for (int fi = 0; fi < 3 && e == cudaSuccess; fi++) {
+                b->tune.ctas_per_sm = ctas_list[ci];
+                b->tune.etarget = et_list[ei];
+                b->tune.fused_max = fm_list[fi];
+                e = cudaEventRecord(t0, b->stream);
+                if (e == cudaSuccess)
+                    e = launch_graph(b, make_args(b, trial_passes, nullptr, 0.f, 1.f));
+                if (e == cudaSuccess)
+                    e = cudaEventRecord(t1, b->stream);
+                if (e == cudaSuccess)
+                    e = cudaEventSynchronize(t1);
+                float ms = 0.f;
+                if (e == cudaSuccess)
+                    e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e == cudaSuccess && ms < best_ms) {
+                    best_ms = ms;
+                    best = b->tune;
+                }
+                // back to the snapshot
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(b->arena, bk_arena, sizeof(float) * b->arena_floats,
+                                        cudaMemcpyDeviceToDevice, b->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(b->states, bk_states, sizeof(WlDevState) * (size_t)b->count,
+                                        cudaMemcpyDeviceToDevice, b->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(b->d_streams, bk_streams, sizeof(BatchStream) * (size_t)b->count,
+                                        cudaMemcpyDeviceToDevice, b->stream);
+            }
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(b->stream);
+    if (t0)
+        cudaEventDestroy(t0);
+    if (t1)
+        cudaEventDestroy(t1);
+    cudaFree(bk_arena);
+    cudaFree(bk_states);
+    cudaFree(bk_streams);
+    b->tune = best;
+    if (e != cudaSuccess)
+        return bfail(b, e);
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f,
+                    "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"etarget\": %d, \"fused_max\": %lld, "
+                    "\"trial_passes\": %d, \"ms\": %.4f}\n",
+                    key.c_str(), best.ctas_per_sm, best.etarget, (long long)best.fused_max,
+                    trial_passes, best_ms);
+            fclose(f);
+        }
+    }
+    return WALLACE_OK;
+}
+
+} // extern "C"

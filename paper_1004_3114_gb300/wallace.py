@@ -77,6 +77,19 @@ _SIGS = {
     "wallace_clear_error": (C.c_int, [_h]),
     "wallace_returned_per_pass": (C.c_int64, [_h]),
     "wallace_strerror": (C.c_char_p, [C.c_int]),
+    "wallace_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double,
+                                       C.c_void_p, C.POINTER(C.c_void_p)]),
+    "wallace_batch_destroy": (None, [C.c_void_p]),
+    "wallace_batch_run": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_float, C.c_float]),
+    "wallace_batch_out_offset": (C.c_int64, [C.c_void_p, C.c_int, C.c_int64]),
+    "wallace_batch_returned_per_pass": (C.c_int64, [C.c_void_p, C.c_int]),
+    "wallace_batch_sync": (C.c_int, [C.c_void_p]),
+    "wallace_batch_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Stats)]),
+    "wallace_batch_get_pool": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "wallace_batch_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int64]),
+    "wallace_batch_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                           C.POINTER(C.c_int64)]),
+    "wallace_batch_autotune": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
     "wallace_pass_static": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_float, C.c_void_p, C.c_int64, C.c_float, C.c_float,
                                       C.POINTER(PassResult), C.c_void_p]),
@@ -95,6 +108,75 @@ def header_functions() -> list[str]:
     """Names of the functions include/wallace.h declares."""
     text = open(HEADER).read()
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(wallace_\w+)\s*\(", text, re.M)))
+
+
+class Batch:
+    """Many generators advanced in one launch (wallace_batch_*)."""
+
+    def __init__(self, n: int, Ns, seeds, frac: float = 1.0, stream=None):
+        Ns = np.ascontiguousarray(Ns, dtype=np.int64)
+        seeds = np.ascontiguousarray(seeds, dtype=np.uint32)
+        assert Ns.size == seeds.size
+        self.n, self.count = n, int(Ns.size)
+        self.N = Ns.copy()
+        h = C.c_void_p()
+        rc = _lib.wallace_batch_create(self.count, n, Ns.ctypes.data, seeds.ctypes.data, frac,
+                                       _stream_ptr(stream), C.byref(h))
+        _check(rc, "wallace_batch_create")
+        self._h = h
+        self.R = np.array([_lib.wallace_batch_returned_per_pass(h, s) for s in range(self.count)],
+                          dtype=np.int64)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.wallace_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def out_offset(self, s: int, passes: int) -> int:
+        return int(_lib.wallace_batch_out_offset(self._h, s, passes))
+
+    def out_size(self, passes: int) -> int:
+        return self.out_offset(self.count, passes)
+
+    def run(self, passes: int, out=None, mu: float = 0.0, sigma: float = 1.0) -> int:
+        ptr = C.c_void_p(out.data_ptr()) if out is not None else None
+        return _check(_lib.wallace_batch_run(self._h, passes, ptr, mu, sigma), "wallace_batch_run",
+                      allow=ECORRUPT)
+
+    def sync(self) -> int:
+        return _check(_lib.wallace_batch_sync(self._h), "wallace_batch_sync", allow=ECORRUPT)
+
+    def stats(self, s: int) -> Stats:
+        st = Stats()
+        _check(_lib.wallace_batch_stats(self._h, s, C.byref(st)), "wallace_batch_stats",
+               allow=ECORRUPT)
+        return st
+
+    def pool(self, s: int) -> np.ndarray:
+        out = np.empty(self.n * int(self.N[s]), dtype=np.float32)
+        _check(_lib.wallace_batch_get_pool(self._h, s, out.ctypes.data), "wallace_batch_get_pool",
+               allow=ECORRUPT)
+        return out
+
+    def set_tuning(self, ctas_per_sm: int, etarget: int, fused_max: int) -> None:
+        _check(_lib.wallace_batch_set_tuning(self._h, ctas_per_sm, etarget, fused_max),
+               "wallace_batch_set_tuning")
+
+    def tuning(self) -> tuple[int, int, int]:
+        a, b, c = C.c_int(), C.c_int(), C.c_int64()
+        _lib.wallace_batch_get_tuning(self._h, C.byref(a), C.byref(b), C.byref(c))
+        return a.value, b.value, c.value
+
+    def autotune(self, cache_path: str | None = None, trial_passes: int = 2) -> tuple[int, int, int]:
+        p = cache_path.encode() if cache_path else None
+        _check(_lib.wallace_batch_autotune(self._h, p, trial_passes), "wallace_batch_autotune")
+        return self.tuning()
 
 
 def pass_static(n: int, N: int, pool, alpha, gamma, c32: float, out=None, out_count: int = 0,

@@ -1,0 +1,84 @@
+"""Batched generators (one persistent launch for many pools) against the oracle.
+
+Every generator in a batch must produce, bit for bit, what the oracle (and a
+single handle) produces for its own n, N, seed and frac: the returned values
+of every pass, the pool and the exact sum of squares.  Pool sizes are chosen
+to exercise all three per-generator paths: pools kept in shared memory for
+all passes, the CTA-local lane-tiled gather (strides with lcm 45), and the
+plain gather (N with factors 3 or 5, whose strides fall back).
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1004_3114_gb300 import wallace as W  # noqa: E402
+
+NS4 = [4, 16, 100, 256, 1001, 2000, 2100, 3000, 4096, 5000, 8192, 20000, 65536, 100003, 16388, 7]
+
+
+def _check_batch(orc, b, Ns, seeds, frac, n, runs, mu=0.0, sigma=1.0):
+    oracles = [orc.Generator(n, int(N), int(sd), frac) for N, sd in zip(Ns, seeds)]
+    for P in runs:
+        out = torch.empty(b.out_size(P), dtype=torch.float32, device="cuda")
+        b.run(P, out, mu, sigma)
+        got = out.cpu().numpy()
+        for s, o in enumerate(oracles):
+            off = b.out_offset(s, P)
+            ref = o.fill(P * int(b.R[s]), mu, sigma)
+            assert np.array_equal(got[off:off + ref.size].view(np.uint32), ref.view(np.uint32)), (s, Ns[s], P)
+    for s, o in enumerate(oracles):
+        assert np.array_equal(b.pool(s).view(np.uint32), o.pool32().view(np.uint32)), (s, Ns[s])
+        gs, os_ = b.stats(s), o.stats()
+        assert gs.Q == os_.Q and gs.c32 == os_.c32 and gs.passes == os_.passes, (s, Ns[s])
+    assert b.sync() == 0
+
+
+def test_batch_n4_mixed_sizes_matches_oracle(orc):
+    seeds = list(range(100, 100 + len(NS4)))
+    b = W.Batch(4, NS4, seeds, 1.0)
+    _check_batch(orc, b, NS4, seeds, 1.0, 4, runs=[3, 2, 1], mu=0.5, sigma=2.0)
+
+
+@pytest.mark.parametrize("tuning", [(1, 1280, 0), (3, 2560, 8192), (2, 640, 2048)])
+def test_batch_tunings_give_identical_streams(orc, tuning):
+    Ns = [300, 2000, 9000, 30000, 65536, 5001]
+    seeds = [5, 6, 7, 8, 9, 10]
+    b = W.Batch(4, Ns, seeds, 0.5)
+    b.set_tuning(*tuning)
+    _check_batch(orc, b, Ns, seeds, 0.5, 4, runs=[2, 3])
+
+
+def test_batch_n8(orc):
+    Ns = [128, 1000, 3000, 9000]
+    seeds = [1, 2, 3, 4]
+    b = W.Batch(8, Ns, seeds, 1 / 3)
+    _check_batch(orc, b, Ns, seeds, 1 / 3, 8, runs=[2, 2])
+
+
+def test_batch_without_output_and_autotune_does_not_advance(orc):
+    Ns = [512, 4096, 40000, 70000]
+    seeds = [11, 12, 13, 14]
+    b = W.Batch(4, Ns, seeds, 1.0)
+    before = [b.pool(s) for s in range(len(Ns))]
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "tune.jsonl")
+        t1 = b.autotune(path, 1)
+        assert os.path.exists(path)
+        t2 = b.autotune(path, 1)       # second call reads the cache
+        assert t1 == t2
+    for s in range(len(Ns)):
+        assert np.array_equal(b.pool(s), before[s])
+    b.run(2)                           # values discarded, generators advance
+    oracles = [orc.Generator(4, N, sd, 1.0) for N, sd in zip(Ns, seeds)]
+    for s, o in enumerate(oracles):
+        o.pass_()
+        o.pass_()
+        assert np.array_equal(b.pool(s).view(np.uint32), o.pool32().view(np.uint32))
