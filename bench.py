@@ -144,6 +144,19 @@ def cpu_baseline(passes: int):
     return passes * R / dt, dt
 
 
+def reduce_over_ranks(ms: float, units: int, dist, device) -> tuple[float, int]:
+    """Max of the per-rank times and sum of the per-rank units over the
+    process group (any backend): the job's time is its slowest rank."""
+    if dist is None:
+        return ms, units
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -218,10 +231,7 @@ def run_ours(args, rank, world, local_rank):
     launches = st1.kernel_launches - st0.kernel_launches
     kernel_ms = (st1.kernel_ms - st0.kernel_ms) / max(launches, 1)
     status = g.sync()
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, total_units = reduce_over_ranks(ms, args.steps * R, dist, dev)
 
     # end to end through the C ABI into pinned HOST memory (D2H inside the timed region)
     host = torch.empty(R, dtype=torch.float32).pin_memory()
@@ -233,10 +243,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         g.fill_host(host)
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s, e2e_units = reduce_over_ranks(e2e_s, e2e_steps * R, dist, dev)
 
     # the other pass kernels on the same pool, for comparison
     cmp = {}
@@ -259,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         peak, peak_kind = hbm_peak()
         achieved = BYTES_PER_PASS / (kernel_ms * 1e-3) / 1e9
-        value = world * args.steps * R / (ms * 1e-3)
+        value = total_units / (ms * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -273,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": profiled_traffic(), "kernel": "tma_kernel (lane-tiled pass, bulk copies into a stage ring)",
                          "kernel_ms": kernel_ms, "algorithmic_bytes_per_launch": BYTES_PER_PASS},
-            "e2e": {"value": world * e2e_steps * R / e2e_s, "unit": UNIT,
+            "e2e": {"value": e2e_units / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * R},
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
@@ -322,6 +329,76 @@ def precision_study(passes: int = 1000, N: int = 1 << 22, seed: int = 3):
     print(json.dumps(res), flush=True)
 
 
+def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
+                  power_of_two: bool = False):
+    """4096 generators, n = 4, N log-uniform on [2^8, 2^18], seeds 0..4095,
+    frac = 1: `runs` batched launches of `passes_per_run` passes (autotuned,
+    CUDA graph), against the same generators run one after another through
+    single-generator handles (`seq_passes` passes each)."""
+    import numpy as np
+    import torch
+    from paper_1004_3114_gb300 import wallace as W
+    from paper_1004_3114_gb300.workloads import batch_sizes
+    Ns = batch_sizes(power_of_two=power_of_two)
+    seeds = np.arange(len(Ns), dtype=np.uint32)
+    stream = torch.cuda.Stream()
+    b = W.Batch(4, Ns, seeds, 1.0, stream=stream)
+    nu_total = int(4 * Ns.sum())
+    R_total = int(b.R.sum())
+    bytes_per_pass = 8 * nu_total + 4 * R_total
+    cache = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                         "wallace_batch_tune.jsonl")
+    t0 = time.perf_counter()
+    tuning = b.autotune(cache, 1)
+    tune_s = time.perf_counter() - t0
+    out = torch.empty(b.out_size(passes_per_run), dtype=torch.float32, device="cuda")
+    b.run(1, None)   # warm-up (graph instantiation)
+    b.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(runs):
+            b.run(passes_per_run, out)
+        ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    status = b.sync()
+    passes = runs * passes_per_run
+    value = passes * R_total / (ms * 1e-3)
+    peak, kind = hbm_peak()
+    achieved = passes * bytes_per_pass / (ms * 1e-3) / 1e9
+    b.close()
+    del out
+    # the same generators, one handle each, one after another
+    handles = [W.Wallace(4, int(N), int(sd), 1.0, stream=stream) for N, sd in zip(Ns, seeds)]
+    outs = [torch.empty(seq_passes * h.R, dtype=torch.float32, device="cuda") for h in handles]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for h, o in zip(handles, outs):
+            h.fill(o)
+        e1.record(stream)
+    e1.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    seq_value = seq_passes * R_total / (seq_ms * 1e-3)
+    for h in handles:
+        h.close()
+    print(json.dumps({
+        "metric": "batched generators: N(0,1) variates/s", "value": value, "unit": UNIT,
+        "workload": f"4096 generators, n=4, N log-uniform on [2^8, 2^18]"
+                    f"{' (powers of two)' if power_of_two else ''}, seeds 0..4095, frac=1",
+        "sum_nu": nu_total, "passes": passes, "runs": runs, "ms": ms,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": kind,
+                     "algorithmic_bytes_per_pass": bytes_per_pass},
+        "tuning": {"ctas_per_sm": tuning[0], "etarget": tuning[1], "fused_max": tuning[2],
+                   "autotune_s": tune_s},
+        "sequential_handles": {"value": seq_value, "passes": seq_passes, "ms": seq_ms,
+                               "launches": "one fill per generator"},
+        "speedup_vs_sequential": value / seq_value, "status": int(status)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,11 +408,17 @@ def main():
     ap.add_argument("--cpu-passes", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="4096 uneven generators in one persistent launch vs one handle each")
+    ap.add_argument("--pow2", action="store_true", help="with --batched: power-of-two pool sizes")
     ap.add_argument("--precision-study", action="store_true",
                     help="binary32 vs binary64 pool study (N=2^22, n=4 and 8, 1000 passes) instead of the benchmark")
     args = ap.parse_args()
     if args.precision_study:
         precision_study()
+        return
+    if args.batched:
+        batched_bench(power_of_two=args.pow2)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
