@@ -265,6 +265,91 @@ int wallace_batch_get_tuning(const wallace_batch_t *b, int *ctas_per_sm, int *et
  */
 int wallace_batch_autotune(wallace_batch_t *b, const char *cache_path, int trial_passes);
 
+/* ---- serving many clients by continuous batching ---------------------- */
+/*
+ * A server holds one generator per client (pool resident in device memory)
+ * and answers fill requests (client, count, mu, sigma).  A request is
+ * admitted when its client has no request in flight (each client's stream
+ * stays in order) and its output buffer -- plus a second pool buffer for
+ * pools too large for shared memory -- fits in the device-memory budget
+ * given at creation, which also holds every client's pool.  Each scheduler
+ * tick launches one persistent kernel over all admitted requests (each gets
+ * the values left in its client's current pool, then up to
+ * passes_per_tick passes whose returned prefixes go straight into its
+ * output); requests that arrive meanwhile join at the next tick.  The values
+ * a client receives do not depend on what other clients ask for: they are
+ * exactly those of a handle with the same n, N, seed and frac.
+ */
+typedef struct wallace_server wallace_server_t;
+
+typedef struct {
+    int64_t submitted, admitted, completed, queued, active, ticks;
+    int64_t values_delivered;   /* sum of the counts of completed requests     */
+    int64_t hbm_budget, hbm_in_use, hbm_peak;   /* bytes                      */
+    double p50_ms, p99_ms, mean_ms;   /* request latency: submit to completion */
+    double elapsed_s;           /* first submit to last completion            */
+    int32_t status;
+    int32_t pad_;
+} wallace_server_stats_t;
+
+/*
+ * wallace_server_create -- n_clients generators (host arrays N, seed); n and
+ * frac as in wallace_create.  hbm_budget_bytes bounds all device memory the
+ * server uses (pools, states, request buffers); WALLACE_ENOMEM if the pools
+ * alone do not fit.  Initial pools are made here (synchronous).
+ */
+int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t *seed, double frac,
+                          int64_t hbm_budget_bytes, void *cuda_stream, wallace_server_t **out);
+
+/* wallace_server_destroy -- synchronise and free everything.  NULL-safe. */
+void wallace_server_destroy(wallace_server_t *s);
+
+/* wallace_server_set_tuning -- passes per request per tick (>= 1), the
+ * largest pool kept in shared memory across passes, CTAs per SM.  Only
+ * while idle. */
+int wallace_server_set_tuning(wallace_server_t *s, int passes_per_tick, int64_t fused_max,
+                              int ctas_per_sm);
+
+/* wallace_server_submit -- queue a request; returns its id (host, no GPU work). */
+int wallace_server_submit(wallace_server_t *s, int client, int64_t count, float mu, float sigma,
+                          int64_t *request_id);
+
+/* wallace_server_progress -- reap finished ticks, admit, enqueue one tick.
+ * Non-blocking unless every tick slot is busy. */
+int wallace_server_progress(wallace_server_t *s);
+
+/* wallace_server_drain -- progress until no request is queued or active, then
+ * synchronise. */
+int wallace_server_drain(wallace_server_t *s);
+
+/* wallace_server_poll -- ids (up to max_ids) of requests completed since the
+ * last poll. */
+int wallace_server_poll(wallace_server_t *s, int64_t *ids, int max_ids, int *n_out);
+
+/* wallace_server_result -- a completed request's DEVICE output (count floats,
+ * owned by the server until released), count and latency in ms;
+ * WALLACE_ESTATE if not completed. */
+int wallace_server_result(wallace_server_t *s, int64_t id, float **dev_out, int64_t *count,
+                          double *latency_ms);
+
+/* wallace_server_release -- return a completed request's output buffer to
+ * the budget. */
+int wallace_server_release(wallace_server_t *s, int64_t id);
+
+/*
+ * wallace_server_run_trace -- replay n requests in real time: request k is
+ * submitted at arrival_s[k] seconds after the call starts (ascending), and
+ * its output is released as soon as it completes.  latency_ms (may be NULL)
+ * receives each request's time from its scheduled arrival to completion.
+ * Returns when all are done.
+ */
+int wallace_server_run_trace(wallace_server_t *s, int64_t n, const double *arrival_s,
+                             const int32_t *client, const int64_t *count, const float *mu,
+                             const float *sigma, double *latency_ms);
+
+/* wallace_server_stats -- counters, memory and latency percentiles. */
+int wallace_server_stats(wallace_server_t *s, wallace_server_stats_t *out);
+
 /*
  * wallace_pass_static -- one pass that allocates nothing.  The paper has no
  * counterpart: this is a deployment entry point.

@@ -28,7 +28,7 @@
 
 #include "wallace.h"
 #include "wl_launch.h"
-#include "wl_tiled_body.cuh"
+#include "wl_run_body.cuh"
 
 #define BT_THREADS 256
 
@@ -55,173 +55,6 @@ struct BatchArgs {
     float mu, sigma;
 };
 
-template <int NSUB>
-__device__ void gather_range_n(const float *src, float *dst, int64_t N, int64_t Np, const int32_t *alpha,
-                               const int64_t *gam, float c, float *out, int64_t w1, float mu,
-                               float sigma, uint64_t &lo, uint64_t &hi, uint32_t &bad)
-{
-    const int64_t G = blockDim.x;
-    int64_t j = threadIdx.x;
-    int64_t idx[NSUB], stp[NSUB];
-#pragma unroll
-    for (int i = 0; i < NSUB; i++) {
-        idx[i] = (int64_t)(((uint64_t)alpha[i] * (uint64_t)(j < N ? j : 0) + (uint64_t)gam[i]) % (uint64_t)N);
-        stp[i] = (int64_t)(((uint64_t)alpha[i] * (uint64_t)G) % (uint64_t)N);
-    }
-    for (; j < N; j += G) {
-        float g[NSUB], y[NSUB];
-#pragma unroll
-        for (int i = 0; i < NSUB; i++) {
-            g[i] = src[i * Np + idx[i]];
-            idx[i] += stp[i];
-            if (idx[i] >= N)
-                idx[i] -= N;
-        }
-        if constexpr (NSUB == 4)
-            wl_xform4(g, c, y);
-        else
-            wl_xform8(g, c, y);
-#pragma unroll
-        for (int k = 0; k < NSUB; k++) {
-            dst[k * Np + j] = y[k];
-            wl_add128(lo, hi, wl_term32(y[k], bad), 0);
-            const int64_t q = k * N + j;
-            if (q < w1)
-                out[q] = __fadd_rn(mu, __fmul_rn(sigma, y[k]));
-        }
-    }
-}
-
-// All passes of one generator whose pool fits in shared memory.
-template <int NSUB>
-__device__ void run_fused(const BatchStream &d, const BatchArgs &a, float *sm, uint64_t *red,
-                          int32_t *s_prm)
-{
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int N = (int)d.N, nu = NSUB * N;
-    float *src = sm, *dst = sm + nu;
-    const float *g0 = d.pool[d.cur];
-    for (int q = tid; q < nu; q += nth) {
-        int i = q / N;
-        src[q] = g0[(int64_t)i * d.Np + (q - i * N)];
-    }
-    float *obase = a.out ? a.out + a.passes * d.out_pref : nullptr;
-    for (int64_t p = 0; p < a.passes; p++) {
-        __syncthreads();
-        if (tid == 0) {
-            for (int i = 0; i < NSUB; i++) {
-                s_prm[i] = d.st->next.alpha[i];
-                s_prm[8 + i] = (int32_t)d.st->next.gamma[i];
-            }
-            s_prm[16] = __float_as_int(d.st->next.c32);
-        }
-        __syncthreads();
-        const float c = __int_as_float(s_prm[16]);
-        int idx[NSUB], stp[NSUB];
-#pragma unroll
-        for (int i = 0; i < NSUB; i++) {
-            idx[i] = (int)(((int64_t)s_prm[i] * (tid < N ? tid : 0) + s_prm[8 + i]) % N);
-            stp[i] = (int)(((int64_t)s_prm[i] * nth) % N);
-        }
-        float *o = obase ? obase + p * d.R : nullptr;
-        const int w1 = o ? (int)d.R : 0;
-        uint64_t lo = 0, hi = 0;
-        uint32_t bad = 0;
-        for (int j = tid; j < N; j += nth) {
-            float g[NSUB], y[NSUB];
-#pragma unroll
-            for (int i = 0; i < NSUB; i++) {
-                g[i] = src[i * N + idx[i]];
-                idx[i] += stp[i];
-                if (idx[i] >= N)
-                    idx[i] -= N;
-            }
-            if constexpr (NSUB == 4)
-                wl_xform4(g, c, y);
-            else
-                wl_xform8(g, c, y);
-#pragma unroll
-            for (int k = 0; k < NSUB; k++) {
-                const int q = k * N + j;
-                dst[q] = y[k];
-                wl_add128(lo, hi, wl_term32(y[k], bad), 0);
-                if (q < w1)
-                    o[q] = __fadd_rn(a.mu, __fmul_rn(a.sigma, y[k]));
-            }
-        }
-        wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
-        __syncthreads();
-        if (tid == 0)
-            wl_finalise(d.st, NSUB, N, nu, (double)dst[nu - 1], false, true);
-        float *t = src;
-        src = dst;
-        dst = t;
-    }
-    __syncthreads();
-    float *g1 = d.pool[d.cur];
-    for (int q = tid; q < nu; q += nth) {
-        int i = q / N;
-        g1[(int64_t)i * d.Np + (q - i * N)] = src[q];
-    }
-}
-
-// All passes of one generator from global memory; returns the final buffer index.
-template <int NSUB>
-__device__ int run_global(const BatchStream &d, const BatchArgs &a, float *sm, uint64_t *red)
-{
-    const int tid = threadIdx.x;
-    const int64_t N = d.N, nu = NSUB * N;
-    int cur = d.cur;
-    float *obase = a.out ? a.out + a.passes * d.out_pref : nullptr;
-    for (int64_t p = 0; p < a.passes; p++) {
-        __syncthreads();   // the previous pass's parameters are written
-        int32_t alpha[NSUB];
-        int64_t gam[NSUB];
-#pragma unroll
-        for (int i = 0; i < NSUB; i++) {
-            alpha[i] = d.st->next.alpha[i];
-            gam[i] = d.st->next.gamma[i];
-        }
-        const float c = d.st->next.c32;
-        const float *src = d.pool[cur];
-        float *dst = d.pool[1 - cur];
-        float *o = obase ? obase + p * d.R : nullptr;
-        uint64_t lo = 0, hi = 0;
-        uint32_t bad = 0;
-        if constexpr (NSUB == 4) {
-            WlTileJob job;
-            job.src = src;
-            job.dst = dst;
-            job.N = N;
-            job.Np = d.Np;
-            for (int i = 0; i < 4; i++) {
-                job.alpha[i] = alpha[i];
-                job.gam[i] = gam[i];
-            }
-            job.c = c;
-            job.out = o;
-            job.w0 = 0;
-            job.w1 = o ? d.R : 0;
-            job.mu = a.mu;
-            job.sigma = a.sigma;
-            const int L = wl_lcm4(job.alpha);
-            if (wl_tiled_ok(L, N))
-                wl_tiled4_tiles(job, L, 0, 1, a.etarget, sm, lo, hi, bad);
-            else
-                wl_gather4_range(job, tid, blockDim.x, lo, hi, bad);
-        } else {
-            gather_range_n<NSUB>(src, dst, N, d.Np, alpha, gam, c, o, o ? d.R : 0, a.mu, a.sigma,
-                                 lo, hi, bad);
-        }
-        wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
-        __syncthreads();
-        if (tid == 0)
-            wl_finalise(d.st, NSUB, N, nu, (double)__ldcg(&dst[wl_phys(nu - 1, N, d.Np)]), false, true);
-        cur = 1 - cur;
-    }
-    return cur;
-}
-
 __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
 {
     extern __shared__ __align__(16) float smem[];
@@ -239,17 +72,24 @@ __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
         if (k >= a.count)
             break;
         const BatchStream d = a.streams[a.order[k]];
-        const int64_t nu = (int64_t)d.n * d.N;
-        if (nu <= a.fused_max && 2 * nu <= smem_values) {
-            if (d.n == 4)
-                run_fused<4>(d, a, smem, red, s_prm);
-            else
-                run_fused<8>(d, a, smem, red, s_prm);
-        } else {
-            const int cur = d.n == 4 ? run_global<4>(d, a, smem, red) : run_global<8>(d, a, smem, red);
-            if (tid == 0)
-                a.streams[a.order[k]].cur = cur;
-        }
+        WlRunSpec r;
+        r.buf[0] = d.pool[0];
+        r.buf[1] = d.pool[1];
+        r.cur = d.cur;
+        r.st = d.st;
+        r.N = d.N;
+        r.Np = d.Np;
+        r.R = d.R;
+        r.n = d.n;
+        r.passes = a.passes;
+        r.out = a.out ? a.out + a.passes * d.out_pref : nullptr;
+        r.last_take = d.R;
+        r.mu = a.mu;
+        r.sigma = a.sigma;
+        r.etarget = a.etarget;
+        const int cur = wl_run_spec(r, a.fused_max, smem_values, smem, red, s_prm);
+        if (tid == 0)
+            a.streams[a.order[k]].cur = cur;
     }
 }
 

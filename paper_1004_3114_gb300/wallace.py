@@ -42,6 +42,17 @@ class Stats(C.Structure):
         return (int(self.q_hi) << 64) | int(self.q_lo)
 
 
+class ServerStats(C.Structure):
+    _fields_ = [
+        ("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+        ("queued", C.c_int64), ("active", C.c_int64), ("ticks", C.c_int64),
+        ("values_delivered", C.c_int64), ("hbm_budget", C.c_int64), ("hbm_in_use", C.c_int64),
+        ("hbm_peak", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+        ("mean_ms", C.c_double), ("elapsed_s", C.c_double), ("status", C.c_int32),
+        ("pad_", C.c_int32),
+    ]
+
+
 class PassResult(C.Structure):
     _fields_ = [
         ("q_lo", C.c_uint64), ("q_hi", C.c_uint64), ("q", C.c_double), ("S", C.c_double),
@@ -90,6 +101,21 @@ _SIGS = {
     "wallace_batch_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                            C.POINTER(C.c_int64)]),
     "wallace_batch_autotune": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int]),
+    "wallace_server_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double,
+                                        C.c_int64, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "wallace_server_destroy": (None, [C.c_void_p]),
+    "wallace_server_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int]),
+    "wallace_server_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_float, C.c_float,
+                                        C.POINTER(C.c_int64)]),
+    "wallace_server_progress": (C.c_int, [C.c_void_p]),
+    "wallace_server_drain": (C.c_int, [C.c_void_p]),
+    "wallace_server_poll": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "wallace_server_result": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "wallace_server_release": (C.c_int, [C.c_void_p, C.c_int64]),
+    "wallace_server_run_trace": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "wallace_server_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
     "wallace_pass_static": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_float, C.c_void_p, C.c_int64, C.c_float, C.c_float,
                                       C.POINTER(PassResult), C.c_void_p]),
@@ -177,6 +203,101 @@ class Batch:
         p = cache_path.encode() if cache_path else None
         _check(_lib.wallace_batch_autotune(self._h, p, trial_passes), "wallace_batch_autotune")
         return self.tuning()
+
+
+class Server:
+    """Continuous-batching server over many client generators (wallace_server_*)."""
+
+    def __init__(self, n: int, Ns, seeds, frac: float, hbm_budget_bytes: int, stream=None):
+        Ns = np.ascontiguousarray(Ns, dtype=np.int64)
+        seeds = np.ascontiguousarray(seeds, dtype=np.uint32)
+        h = C.c_void_p()
+        rc = _lib.wallace_server_create(int(Ns.size), n, Ns.ctypes.data, seeds.ctypes.data, frac,
+                                        int(hbm_budget_bytes), _stream_ptr(stream), C.byref(h))
+        _check(rc, "wallace_server_create")
+        self._h = h
+        self.n, self.N = n, Ns.copy()
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.wallace_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, passes_per_tick: int, fused_max: int, ctas_per_sm: int) -> None:
+        _check(_lib.wallace_server_set_tuning(self._h, passes_per_tick, fused_max, ctas_per_sm),
+               "wallace_server_set_tuning")
+
+    def submit(self, client: int, count: int, mu: float = 0.0, sigma: float = 1.0) -> int:
+        rid = C.c_int64()
+        _check(_lib.wallace_server_submit(self._h, client, count, mu, sigma, C.byref(rid)),
+               "wallace_server_submit")
+        return rid.value
+
+    def progress(self) -> int:
+        return _check(_lib.wallace_server_progress(self._h), "wallace_server_progress", allow=ECORRUPT)
+
+    def drain(self) -> int:
+        return _check(_lib.wallace_server_drain(self._h), "wallace_server_drain", allow=ECORRUPT)
+
+    def poll(self, max_ids: int = 1 << 16) -> list[int]:
+        ids = np.empty(max_ids, dtype=np.int64)
+        n = C.c_int()
+        _check(_lib.wallace_server_poll(self._h, ids.ctypes.data, max_ids, C.byref(n)),
+               "wallace_server_poll", allow=ECORRUPT)
+        return [int(x) for x in ids[:n.value]]
+
+    def result(self, rid: int):
+        """(device pointer, count, latency ms) of a completed request."""
+        p, cnt, lat = C.c_void_p(), C.c_int64(), C.c_double()
+        _check(_lib.wallace_server_result(self._h, rid, C.byref(p), C.byref(cnt), C.byref(lat)),
+               "wallace_server_result")
+        return p.value, cnt.value, lat.value
+
+    def result_host(self, rid: int) -> np.ndarray:
+        """Copy a completed request's values (server-owned device buffer) to the host."""
+        import torch
+        p, cnt, _ = self.result(rid)
+        if cnt == 0:
+            return np.empty(0, dtype=np.float32)
+        torch.cuda.synchronize()
+        return _device_floats(p, cnt).cpu().numpy().copy()
+
+    def release(self, rid: int) -> None:
+        _check(_lib.wallace_server_release(self._h, rid), "wallace_server_release")
+
+    def run_trace(self, arrival_s, client, count, mu, sigma) -> np.ndarray:
+        arrival_s = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        client = np.ascontiguousarray(client, dtype=np.int32)
+        count = np.ascontiguousarray(count, dtype=np.int64)
+        mu = np.ascontiguousarray(mu, dtype=np.float32)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float32)
+        lat = np.empty(arrival_s.size, dtype=np.float64)
+        rc = _lib.wallace_server_run_trace(self._h, arrival_s.size, arrival_s.ctypes.data,
+                                           client.ctypes.data, count.ctypes.data, mu.ctypes.data,
+                                           sigma.ctypes.data, lat.ctypes.data)
+        _check(rc, "wallace_server_run_trace", allow=ECORRUPT)
+        return lat
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(_lib.wallace_server_stats(self._h, C.byref(st)), "wallace_server_stats")
+        return st
+
+
+def _device_floats(ptr: int, count: int):
+    """A torch view of `count` float32 values at device address `ptr`."""
+    import torch
+
+    class _View:
+        __cuda_array_interface__ = {"shape": (count,), "typestr": "<f4", "data": (ptr, False),
+                                    "version": 3}
+    return torch.as_tensor(_View(), device="cuda")
 
 
 def pass_static(n: int, N: int, pool, alpha, gamma, c32: float, out=None, out_count: int = 0,

@@ -1,8 +1,8 @@
 """Seeded synthetic workloads (sizes, seeds, request mixes).
 
 Holds none of the generator's arithmetic: it only draws the shapes of the
-benchmark and test workloads with numpy's own PCG64 generator, so the same
-inputs serve the CUDA library, the tests and the oracle.
+benchmark and test workloads (pool sizes, seeds, request mixes) with numpy's
+own PCG64 generator, so every consumer sees the same inputs.
 """
 from __future__ import annotations
 

@@ -1,0 +1,115 @@
+"""The continuous-batching server against the oracle.
+
+Each client's values must be exactly its own generator's stream, whatever
+the other clients ask for and however requests are interleaved: every
+request's output equals the oracle's fill of the same count, mu and sigma
+after that client's earlier requests, and the same client's requests served
+alone give the same bytes as in the mix.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1004_3114_gb300 import wallace as W  # noqa: E402
+
+
+def _mix(seed, n_clients, n_req, max_count):
+    rng = np.random.default_rng(seed)
+    Ns = np.floor(2.0 ** rng.uniform(6, 15, n_clients)).astype(np.int64)   # 64 .. 32768
+    seeds = rng.integers(0, 2**32, n_clients, dtype=np.uint64).astype(np.uint32)
+    reqs = [(int(rng.integers(0, n_clients)), int(np.floor(2.0 ** rng.uniform(0, np.log2(max_count)))),
+             float(rng.uniform(-3, 3)), float(rng.uniform(0.5, 2))) for _ in range(n_req)]
+    return Ns, seeds, reqs
+
+
+def _serve(Ns, seeds, reqs, frac, budget, tuning=None, interleave=True):
+    srv = W.Server(4, Ns, seeds, frac, budget)
+    if tuning:
+        srv.set_tuning(*tuning)
+    ids = []
+    for k, (c, cnt, mu, sg) in enumerate(reqs):
+        ids.append(srv.submit(c, cnt, mu, sg))
+        if interleave and k % 7 == 3:
+            srv.progress()          # new requests join while earlier ones run
+    srv.drain()
+    outs = [srv.result_host(i) for i in ids]
+    st = srv.stats()
+    assert st.completed == len(reqs) and st.queued == 0 and st.active == 0
+    return outs, st
+
+
+@pytest.mark.parametrize("frac,tuning", [(1 / 3, None), (1.0, (1, 2048, 2)), (0.5, (3, 0, 1))])
+def test_server_outputs_match_oracle(orc, frac, tuning):
+    Ns, seeds, reqs = _mix(7, 24, 160, 40000)
+    outs, st = _serve(Ns, seeds, reqs, frac, 256 << 20, tuning)
+    oracles = {c: orc.Generator(4, int(Ns[c]), int(seeds[c]), frac) for c in set(r[0] for r in reqs)}
+    for (c, cnt, mu, sg), got in zip(reqs, outs):
+        ref = oracles[c].fill(cnt, np.float32(mu), np.float32(sg))
+        assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (c, cnt)
+    assert st.hbm_peak <= 256 << 20
+
+
+def test_server_alone_equals_in_mix():
+    Ns, seeds, reqs = _mix(11, 16, 120, 30000)
+    outs_mix, _ = _serve(Ns, seeds, reqs, 1 / 3, 128 << 20)
+    target = reqs[0][0]
+    alone = [r for r in reqs if r[0] == target]
+    outs_alone, _ = _serve(Ns, seeds, alone, 1 / 3, 128 << 20, interleave=False)
+    mix_target = [o for r, o in zip(reqs, outs_mix) if r[0] == target]
+    assert len(mix_target) == len(outs_alone) > 1
+    for a, b in zip(mix_target, outs_alone):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_server_tight_budget_still_completes(orc):
+    """Budget barely above the pools: requests wait for memory, results are
+    read and released as they complete, and every value is still exact."""
+    Ns = np.array([20000, 30000, 5000, 40000], dtype=np.int64)
+    seeds = np.array([1, 2, 3, 4], dtype=np.uint32)
+    pools = int(sum(4 * ((N + 8 + 63) // 64 * 64) * 4 for N in Ns))
+    reqs = [(k % 4, 150000 + 1000 * k, 0.25, 2.0) for k in range(12)]
+    max_out = max(r[1] for r in reqs) * 4
+    max_scratch = 4 * ((40000 + 8 + 63) // 64 * 64) * 4
+    srv = W.Server(4, Ns, seeds, 0.5, pools + 2 * (max_out + max_scratch) + (1 << 16))
+    ids = [srv.submit(c, cnt, mu, sg) for c, cnt, mu, sg in reqs]
+    got = {}
+    while len(got) < len(ids):
+        srv.progress()
+        for rid in srv.poll():
+            got[rid] = srv.result_host(rid)
+            srv.release(rid)
+    oracles = [orc.Generator(4, int(N), int(sd), 0.5) for N, sd in zip(Ns, seeds)]
+    for rid, (c, cnt, mu, sg) in zip(ids, reqs):
+        ref = oracles[c].fill(cnt, np.float32(mu), np.float32(sg))
+        assert np.array_equal(got[rid].view(np.uint32), ref.view(np.uint32))
+    st = srv.stats()
+    assert st.hbm_peak <= st.hbm_budget
+
+
+def test_server_request_larger_than_budget_reports_enomem():
+    Ns = np.array([1024, 2048], dtype=np.int64)
+    srv = W.Server(4, Ns, np.array([1, 2], dtype=np.uint32), 1.0, 1 << 20)
+    srv.submit(0, 1 << 20)          # 4 MB of output cannot fit in a 1 MB budget
+    with pytest.raises(W.WallaceError) as e:
+        srv.drain()
+    assert e.value.code & W.ENOMEM
+
+
+def test_server_trace_replay_reports_latency():
+    Ns = np.floor(2.0 ** np.random.default_rng(3).uniform(10, 16, 64)).astype(np.int64)
+    seeds = np.arange(64, dtype=np.uint32)
+    srv = W.Server(4, Ns, seeds, 1 / 3, 512 << 20)
+    n = 2000
+    rng = np.random.default_rng(4)
+    arrival = np.cumsum(rng.exponential(1 / 20000.0, n))
+    client = rng.integers(0, 64, n).astype(np.int32)
+    count = np.floor(2.0 ** rng.uniform(10, 16, n)).astype(np.int64)
+    lat = srv.run_trace(arrival, client, count, rng.uniform(-1, 1, n), rng.uniform(0.5, 2, n))
+    st = srv.stats()
+    assert st.completed == n and np.all(lat > 0) and st.p99_ms >= st.p50_ms > 0
+    assert st.values_delivered == int(count.sum())
