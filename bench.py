@@ -399,6 +399,47 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
         "speedup_vs_sequential": value / seq_value, "status": int(status)}), flush=True)
 
 
+def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float = 50_000.0,
+                budget_gb: float = 40.0, passes_per_tick: int = 2):
+    """Serving loop: n_clients generators (n = 4, N log-uniform on
+    [2^10, 2^20], frac = 1/3), Poisson arrivals at `rate`, counts log-uniform
+    on [2^10, 2^24], mu ~ U[-10, 10], sigma ~ U[0.1, 10], admitted against a
+    device-memory budget; p50/p99 latency and sustained variates/s."""
+    import numpy as np
+    import torch
+    from paper_1004_3114_gb300 import wallace as W
+    from paper_1004_3114_gb300.workloads import serving_clients, serving_requests
+    Ns = serving_clients(n_clients)
+    seeds = np.arange(n_clients, dtype=np.uint32) + 20000
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    srv = W.Server(4, Ns, seeds, 1 / 3, int(budget_gb * (1 << 30)), stream=stream)
+    create_s = time.perf_counter() - t0
+    srv.set_tuning(passes_per_tick, 4096, 3)
+    tr = serving_requests(n_requests, n_clients, rate)
+    t0 = time.perf_counter()
+    lat = srv.run_trace(tr["arrival_s"], tr["client"], tr["count"], tr["mu"], tr["sigma"])
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    values = int(tr["count"].sum())
+    peak, kind = hbm_peak()
+    bytes_moved = 28 * values        # per returned value at f = 3: 3 x 8 B pool read+write + 4 B out
+    srv.close()
+    print(json.dumps({
+        "metric": "served N(mu, sigma^2) variates/s", "value": values / st.elapsed_s, "unit": UNIT,
+        "workload": f"{n_clients} clients, n=4, N log-uniform on [2^10, 2^20], frac=1/3; "
+                    f"{n_requests} requests, Poisson {rate:.0f}/s, count log-uniform on [2^10, 2^24], "
+                    f"mu~U[-10,10], sigma~U[0.1,10]; budget {budget_gb} GB",
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "values": values, "elapsed_s": st.elapsed_s, "wall_s": wall,
+        "offered_values_per_s": values / float(tr["arrival_s"][-1]),
+        "ticks": int(st.ticks), "hbm_peak_gb": st.hbm_peak / 2**30, "hbm_budget_gb": st.hbm_budget / 2**30,
+        "roofline": {"bound": "hbm", "achieved": bytes_moved / st.elapsed_s / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": bytes_moved / st.elapsed_s / 1e9 / peak, "peak_kind": kind,
+                     "bytes_per_value": 28},
+        "passes_per_tick": passes_per_tick, "create_s": create_s, "status": int(st.status)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,6 +452,11 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="4096 uneven generators in one persistent launch vs one handle each")
     ap.add_argument("--pow2", action="store_true", help="with --batched: power-of-two pool sizes")
+    ap.add_argument("--serve", action="store_true",
+                    help="continuous-batching serving loop (10^4 clients, Poisson arrivals)")
+    ap.add_argument("--serve-requests", type=int, default=20_000)
+    ap.add_argument("--serve-rate", type=float, default=50_000.0)
+    ap.add_argument("--serve-ppt", type=int, default=2)
     ap.add_argument("--precision-study", action="store_true",
                     help="binary32 vs binary64 pool study (N=2^22, n=4 and 8, 1000 passes) instead of the benchmark")
     args = ap.parse_args()
@@ -419,6 +465,10 @@ def main():
         return
     if args.batched:
         batched_bench(power_of_two=args.pow2)
+        return
+    if args.serve:
+        serve_bench(n_requests=args.serve_requests, rate=args.serve_rate,
+                    passes_per_tick=args.serve_ppt)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

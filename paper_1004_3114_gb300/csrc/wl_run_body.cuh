@@ -20,21 +20,24 @@ struct WlRunSpec {
     int etarget;         // lane-times per tile of the tiled gather
 };
 
+// plain strided gather of j in [j0, j_end) (j_end < 0: N), thread t taking
+// j0 + t, j0 + t + blockDim, ...
 template <int NSUB>
 __device__ void wl_gather_range_n(const float *src, float *dst, int64_t N, int64_t Np,
                                   const int32_t *alpha, const int64_t *gam, float c, float *out,
                                   int64_t w1, float mu, float sigma, uint64_t &lo, uint64_t &hi,
-                                  uint32_t &bad)
+                                  uint32_t &bad, int64_t j0 = 0, int64_t j_end = -1)
 {
     const int64_t G = blockDim.x;
-    int64_t j = threadIdx.x;
+    int64_t j = j0 + threadIdx.x;
+    const int64_t jmax = j_end < 0 ? N : j_end;
     int64_t idx[NSUB], stp[NSUB];
 #pragma unroll
     for (int i = 0; i < NSUB; i++) {
         idx[i] = (int64_t)(((uint64_t)alpha[i] * (uint64_t)(j < N ? j : 0) + (uint64_t)gam[i]) % (uint64_t)N);
         stp[i] = (int64_t)(((uint64_t)alpha[i] * (uint64_t)G) % (uint64_t)N);
     }
-    for (; j < N; j += G) {
+    for (; j < jmax; j += G) {
         float g[NSUB], y[NSUB];
 #pragma unroll
         for (int i = 0; i < NSUB; i++) {

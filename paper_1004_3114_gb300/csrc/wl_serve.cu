@@ -7,12 +7,17 @@
 // its output buffer -- and, for pools too large for shared memory, a second
 // pool buffer -- fit in the device-memory budget.  A scheduler tick turns
 // every active request into one work item (first the values left in the
-// client's current pool, then up to `passes_per_tick` passes whose returned
-// prefixes go straight into the request's output) and launches ONE
-// persistent kernel over all items; CTAs take items largest first and run
-// them with the per-generator runners of wl_run_body.cuh.  Requests arriving
-// while ticks run are admitted at the next tick as slots and memory free up,
-// so their work shares launches with requests already in flight.
+// client's current pool, then passes whose returned prefixes go straight into
+// the request's output).  Pools of up to 2^18 values run in one persistent
+// kernel, a CTA per request doing many passes in a row (in shared memory when
+// the pool fits, else from global memory that the L2 cache mostly holds), up
+// to a per-tick budget of pool values.  Larger pools run pass-major: each of up to
+// `passes_per_tick` launches does one pass of every large request, split
+// into units of about 2^17 pool values spread over all CTAs; the last unit
+// of a request (by ticket) runs its chi-squared rescale (Eq. 3), so no CTA
+// waits for another.  Requests arriving while ticks run are admitted at the
+// next tick as slots and memory free up, so their work shares launches with
+// requests already in flight.
 //
 // Ticks are enqueued back to back on the server's stream: the host's view of
 // every client (cursor, which buffer holds the pool) is updated when a tick
@@ -35,6 +40,8 @@
 #include "wl_run_body.cuh"
 
 #define SV_THREADS 256
+#define SV_MAX_PPT 14                /* passes per tick of a large pool (queue counters per slot - 1) */
+#define SV_QUEUES_PER_SLOT (SV_MAX_PPT + 2)
 
 namespace {
 
@@ -70,6 +77,105 @@ __global__ void __launch_bounds__(SV_THREADS, 3) serve_kernel(const ServeItem *i
         }
         if (it.spec.passes > 0)
             wl_run_spec(it.spec, fused_max, smem_values, smem, red, s_prm);
+    }
+}
+
+// One pass of one large request.
+struct PassItem {
+    const float *src;
+    float *dst;
+    WlDevState *st;
+    int64_t N, Np, nu;
+    int32_t n, nunits;
+    float *out;        // the pass's returned prefix (may be null)
+    int64_t w1;        // values of the prefix to write
+    float mu, sigma;
+    const float *drain_src;   // values of the current pool still to hand out (first pass only)
+    int64_t drain_pos, drain_take;
+    float *drain_out;
+};
+
+struct PassUnit {
+    int32_t item;
+    int32_t part;      // this unit's share of the pass: part of nunits
+};
+
+__device__ __forceinline__ bool last_unit(WlDevState *st, int nunits)
+{
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = atomicAdd(&st->ticket, 1u) == (unsigned)(nunits - 1);
+    __syncthreads();
+    if (s_last)
+        __threadfence();
+    return s_last;
+}
+
+__global__ void __launch_bounds__(SV_THREADS, 3) pass_units_kernel(const PassItem *items,
+                                                                  const PassUnit *units, int nunits,
+                                                                  int *queue)
+{
+    extern __shared__ __align__(16) float smem[];
+    __shared__ uint64_t red[3 * (SV_THREADS / 32)];
+    __shared__ int s_k;
+    const int tid = threadIdx.x;
+    while (true) {
+        __syncthreads();
+        if (tid == 0)
+            s_k = atomicAdd(queue, 1);
+        __syncthreads();
+        const int k = s_k;
+        if (k >= nunits)
+            break;
+        const PassUnit u = units[k];
+        const PassItem it = items[u.item];
+        const int64_t N = it.N;
+        if (u.part == 0)
+            for (int64_t q = tid; q < it.drain_take; q += blockDim.x) {
+                const float y = it.drain_src[wl_phys(it.drain_pos + q, N, it.Np)];
+                it.drain_out[q] = __fadd_rn(it.mu, __fmul_rn(it.sigma, y));
+            }
+        uint64_t lo = 0, hi = 0;
+        uint32_t bad = 0;
+        int32_t alpha[8];
+        int64_t gam[8];
+        for (int i = 0; i < it.n; i++) {
+            alpha[i] = it.st->next.alpha[i];
+            gam[i] = it.st->next.gamma[i];
+        }
+        const float c = it.st->next.c32;
+        const int64_t jb = N * u.part / it.nunits, je = N * (u.part + 1) / it.nunits;
+        if (it.n == 4) {
+            WlTileJob job;
+            job.src = it.src;
+            job.dst = it.dst;
+            job.N = N;
+            job.Np = it.Np;
+            for (int i = 0; i < 4; i++) {
+                job.alpha[i] = alpha[i];
+                job.gam[i] = gam[i];
+            }
+            job.c = c;
+            job.out = it.out;
+            job.w0 = 0;
+            job.w1 = it.out ? it.w1 : 0;
+            job.mu = it.mu;
+            job.sigma = it.sigma;
+            const int L = wl_lcm4(job.alpha);
+            if (wl_tiled_ok(L, N))
+                wl_tiled4_tiles(job, L, 0, 1, TL_EMAX, smem, lo, hi, bad, u.part, it.nunits);
+            else
+                wl_gather4_range(job, jb + tid, blockDim.x, lo, hi, bad, je);
+        } else {
+            wl_gather_range_n<8>(it.src, it.dst, N, it.Np, alpha, gam, c, it.out, it.out ? it.w1 : 0,
+                                 it.mu, it.sigma, lo, hi, bad, jb, je);
+        }
+        wl_cta_reduce_to_state(lo, hi, bad, it.st, red);
+        if (last_unit(it.st, it.nunits) && tid == 0)
+            wl_finalise(it.st, it.n, N, it.nu, (double)__ldcg(&it.dst[wl_phys(it.nu - 1, N, it.Np)]),
+                        false, true);
     }
 }
 
@@ -208,14 +314,17 @@ struct wallace_server {
     std::vector<int64_t> active;
     std::deque<Tick> inflight;
     std::vector<int64_t> completed_unpolled;
-    // tick slots: device item arrays and counters
+    // tick slots: device work arrays and work counters
     int nslots = 4;
-    std::vector<ServeItem *> d_items;
-    std::vector<int> items_cap;
-    int *d_queues = nullptr;
+    std::vector<char *> d_work;
+    std::vector<size_t> work_cap;
+    int *d_queues = nullptr;   // kQueuesPerSlot counters per slot
     std::vector<bool> slot_busy;
     // tuning
-    int passes_per_tick = 4;
+    int passes_per_tick = 2;          // large pools: passes per request per tick
+    int64_t small_values_per_tick = 1 << 20;   // one-CTA pools: pool values per request per tick
+    int64_t onchip_max_values = 1 << 18;       // pools up to this run one CTA per request
+    int64_t unit_values = 1 << 17;    // large pools: pool values per CTA work unit
     int64_t fused_max = 4096;
     int ctas_per_sm = 3;
     // statistics
@@ -325,7 +434,9 @@ void reap(wallace_server_t *s, bool block)
     }
 }
 
-// Build and enqueue one tick over every active request.
+// Build and enqueue one tick over every active request: one on-chip kernel
+// for the shared-memory pools, then one pass-major launch per pass for the
+// large pools.
 int enqueue_tick(wallace_server_t *s)
 {
     if (s->active.empty())
@@ -337,54 +448,94 @@ int enqueue_tick(wallace_server_t *s)
         if (slot < 0)
             return WALLACE_OK;
     }
-    std::vector<ServeItem> items;
-    items.reserve(s->active.size());
+    std::vector<ServeItem> small;
+    std::vector<std::vector<PassItem>> pitems(s->passes_per_tick);
+    std::vector<std::vector<PassUnit>> punits(s->passes_per_tick);
     Tick t;
     t.slot = slot;
     std::vector<int64_t> still;
     for (int64_t id : s->active) {
         Request &r = s->reqs[id];
         Client &c = s->clients[r.client];
-        ServeItem it;
-        memset(&it, 0, sizeof(it));
         float *bufs[2] = {c.buf, r.scratch ? r.scratch : c.buf};
+        const int64_t nu = (int64_t)s->n * c.N;
+        const bool fused = uses_fused(s, c);
+        const bool one_cta = nu <= s->onchip_max_values;   // whole request on one CTA per tick
         const int64_t remaining = r.count - r.done;
-        int64_t drain = std::min(remaining, c.R - c.cursor);
-        if (drain < 0)
-            drain = 0;
-        it.drain_src = bufs[r.loc];
-        it.drain_pos = c.cursor;
-        it.drain_take = drain;
-        it.drain_out = r.out + r.done;
+        int64_t drain = std::max<int64_t>(0, std::min(remaining, c.R - c.cursor));
+        const float *drain_src = bufs[r.loc];
+        const int64_t drain_pos = c.cursor;
+        float *drain_out = r.out + r.done;
         c.cursor += drain;
         r.done += drain;
-        int64_t left = r.count - r.done;
+        const int64_t left = r.count - r.done;
         int64_t P = (left + c.R - 1) / c.R;
-        if (P > s->passes_per_tick)
-            P = s->passes_per_tick;
-        int64_t last = P > 0 ? std::min(c.R, left - (P - 1) * c.R) : 0;
-        WlRunSpec &sp = it.spec;
-        sp.buf[0] = bufs[0];
-        sp.buf[1] = bufs[1];
-        sp.cur = r.loc;
-        sp.st = c.st;
-        sp.N = c.N;
-        sp.Np = c.Np;
-        sp.R = c.R;
-        sp.n = s->n;
-        sp.passes = P;
-        sp.out = r.out + r.done;
-        sp.last_take = last;
-        sp.mu = r.mu;
-        sp.sigma = r.sigma;
-        sp.etarget = TL_EMAX;
-        if (P > 0) {
-            r.done += (P - 1) * c.R + last;
+        const int64_t cap = one_cta ? std::max<int64_t>(1, s->small_values_per_tick / nu) : s->passes_per_tick;
+        if (P > cap)
+            P = cap;
+        const int64_t last = P > 0 ? std::min(c.R, left - (P - 1) * c.R) : 0;
+        if (one_cta || P == 0) {
+            ServeItem it;
+            memset(&it, 0, sizeof(it));
+            it.drain_src = drain_src;
+            it.drain_pos = drain_pos;
+            it.drain_take = drain;
+            it.drain_out = drain_out;
+            WlRunSpec &sp = it.spec;
+            sp.buf[0] = bufs[0];
+            sp.buf[1] = bufs[1];
+            sp.cur = r.loc;
+            sp.st = c.st;
+            sp.N = c.N;
+            sp.Np = c.Np;
+            sp.R = c.R;
+            sp.n = s->n;
+            sp.passes = P;
+            sp.out = r.out + r.done;
+            sp.last_take = last;
+            sp.mu = r.mu;
+            sp.sigma = r.sigma;
+            sp.etarget = TL_EMAX;
+            small.push_back(it);
+            if (P > 0) {
+                r.done += (P - 1) * c.R + last;
+                c.cursor = last;
+                if (!fused)
+                    r.loc ^= (int)(P & 1);   // global-memory passes alternate the two buffers
+            }
+        } else {
+            const int units = (int)std::max<int64_t>(1, (nu + s->unit_values - 1) / s->unit_values);
+            for (int64_t p = 0; p < P; p++) {
+                PassItem pi;
+                memset(&pi, 0, sizeof(pi));
+                pi.src = bufs[r.loc ^ (int)(p & 1)];
+                pi.dst = bufs[r.loc ^ (int)((p + 1) & 1)];
+                pi.st = c.st;
+                pi.N = c.N;
+                pi.Np = c.Np;
+                pi.nu = nu;
+                pi.n = s->n;
+                pi.nunits = units;
+                const int64_t take = p + 1 < P ? c.R : last;
+                pi.out = r.out + r.done;
+                pi.w1 = take;
+                pi.mu = r.mu;
+                pi.sigma = r.sigma;
+                if (p == 0) {
+                    pi.drain_src = drain_src;
+                    pi.drain_pos = drain_pos;
+                    pi.drain_take = drain;
+                    pi.drain_out = drain_out;
+                }
+                r.done += take;
+                const int idx = (int)pitems[p].size();
+                pitems[p].push_back(pi);
+                for (int u = 0; u < units; u++)
+                    punits[p].push_back(PassUnit{idx, u});
+            }
             c.cursor = last;
-            if (!uses_fused(s, c))
-                r.loc ^= (int)(P & 1);
+            r.loc ^= (int)(P & 1);
         }
-        items.push_back(it);
         if (r.done >= r.count) {
             r.finished = true;
             t.finishing.push_back(id);
@@ -405,28 +556,60 @@ int enqueue_tick(wallace_server_t *s)
         }
     }
     s->active.swap(still);
-    // largest pools first
-    std::sort(items.begin(), items.end(), [](const ServeItem &a, const ServeItem &b) {
+    // largest work first
+    std::sort(small.begin(), small.end(), [](const ServeItem &a, const ServeItem &b) {
         return a.spec.N * (a.spec.passes + 1) > b.spec.N * (b.spec.passes + 1);
     });
-    cudaError_t e = cudaSuccess;
-    if ((int)items.size() > s->items_cap[slot]) {
-        cudaFree(s->d_items[slot]);
-        s->d_items[slot] = nullptr;
-        int cap = std::max((int)items.size(), 2 * s->items_cap[slot]);
-        e = cudaMalloc(&s->d_items[slot], sizeof(ServeItem) * (size_t)cap);
-        s->items_cap[slot] = e == cudaSuccess ? cap : 0;
+    // one device buffer per slot: [small items][pass items...][pass units...]
+    size_t bytes = sizeof(ServeItem) * small.size();
+    std::vector<size_t> off_items(s->passes_per_tick), off_units(s->passes_per_tick);
+    for (int p = 0; p < s->passes_per_tick; p++) {
+        bytes = (bytes + 15) & ~(size_t)15;
+        off_items[p] = bytes;
+        bytes += sizeof(PassItem) * pitems[p].size();
     }
+    for (int p = 0; p < s->passes_per_tick; p++) {
+        bytes = (bytes + 15) & ~(size_t)15;
+        off_units[p] = bytes;
+        bytes += sizeof(PassUnit) * punits[p].size();
+    }
+    cudaError_t e = cudaSuccess;
+    if (bytes > s->work_cap[slot]) {
+        cudaFree(s->d_work[slot]);
+        s->d_work[slot] = nullptr;
+        size_t cap = std::max(bytes, 2 * s->work_cap[slot]);
+        e = cudaMalloc(&s->d_work[slot], cap);
+        s->work_cap[slot] = e == cudaSuccess ? cap : 0;
+    }
+    std::vector<char> host(bytes);
+    if (!small.empty())
+        memcpy(host.data(), small.data(), sizeof(ServeItem) * small.size());
+    for (int p = 0; p < s->passes_per_tick; p++) {
+        if (!pitems[p].empty())
+            memcpy(host.data() + off_items[p], pitems[p].data(), sizeof(PassItem) * pitems[p].size());
+        if (!punits[p].empty())
+            memcpy(host.data() + off_units[p], punits[p].data(), sizeof(PassUnit) * punits[p].size());
+    }
+    char *dw = s->d_work[slot];
+    int *dq = s->d_queues + slot * SV_QUEUES_PER_SLOT;
+    if (e == cudaSuccess && bytes)
+        e = cudaMemcpyAsync(dw, host.data(), bytes, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->d_items[slot], items.data(), sizeof(ServeItem) * items.size(),
-                            cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(s->d_queues + slot, 0, sizeof(int), s->stream);
-    if (e == cudaSuccess) {
-        const int ctas = s->sm_count * std::min(s->ctas_per_sm, s->max_ctas_per_sm);
-        const int grid = std::min(ctas, (int)items.size());
-        serve_kernel<<<grid, SV_THREADS, tl_smem_bytes(), s->stream>>>(s->d_items[slot], (int)items.size(),
-                                                                    s->d_queues + slot, s->fused_max);
+        e = cudaMemsetAsync(dq, 0, sizeof(int) * SV_QUEUES_PER_SLOT, s->stream);
+    const int ctas = s->sm_count * std::min(s->ctas_per_sm, s->max_ctas_per_sm);
+    if (e == cudaSuccess && !small.empty()) {
+        const int grid = std::min(ctas, (int)small.size());
+        serve_kernel<<<grid, SV_THREADS, tl_smem_bytes(), s->stream>>>((const ServeItem *)dw, (int)small.size(),
+                                                                    dq, s->fused_max);
+        e = cudaGetLastError();
+    }
+    for (int p = 0; p < s->passes_per_tick && e == cudaSuccess; p++) {
+        if (punits[p].empty())
+            continue;
+        const int grid = std::min(ctas, (int)punits[p].size());
+        pass_units_kernel<<<grid, SV_THREADS, tl_smem_bytes(), s->stream>>>(
+            (const PassItem *)(dw + off_items[p]), (const PassUnit *)(dw + off_units[p]),
+            (int)punits[p].size(), dq + 1 + p);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
@@ -510,6 +693,9 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tl_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pass_units_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tl_smem_bytes());
     if (e == cudaSuccess) {
         int per = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, serve_kernel, SV_THREADS, tl_smem_bytes());
@@ -519,15 +705,16 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
         e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess && cudaMalloc(&s->states, state_bytes) != cudaSuccess)
         e = cudaErrorMemoryAllocation;
-    if (e == cudaSuccess && cudaMalloc(&s->d_queues, sizeof(int) * (size_t)s->nslots) != cudaSuccess)
+    if (e == cudaSuccess &&
+        cudaMalloc(&s->d_queues, sizeof(int) * (size_t)(s->nslots * SV_QUEUES_PER_SLOT)) != cudaSuccess)
         e = cudaErrorMemoryAllocation;
     if (e != cudaSuccess) {
         wallace_server_destroy(s);
         return e == cudaErrorMemoryAllocation ? WALLACE_ENOMEM : WALLACE_ECUDA;
     }
     s->arena.init(s->pool_mem, s->budget - state_bytes);
-    s->d_items.assign(s->nslots, nullptr);
-    s->items_cap.assign(s->nslots, 0);
+    s->d_work.assign(s->nslots, nullptr);
+    s->work_cap.assign(s->nslots, 0);
     s->slot_busy.assign(s->nslots, false);
     e = cudaMemsetAsync(s->states, 0, state_bytes, s->stream);
     for (int c = 0; c < n_clients && e == cudaSuccess; c++) {
@@ -559,7 +746,7 @@ void wallace_server_destroy(wallace_server_t *s)
     cudaStreamSynchronize(s->stream);
     for (auto &t : s->inflight)
         cudaEventDestroy(t.ev);
-    for (auto *p : s->d_items)
+    for (auto *p : s->d_work)
         cudaFree(p);
     cudaFree(s->d_queues);
     cudaFree(s->states);
@@ -569,8 +756,8 @@ void wallace_server_destroy(wallace_server_t *s)
 
 int wallace_server_set_tuning(wallace_server_t *s, int passes_per_tick, int64_t fused_max, int ctas_per_sm)
 {
-    if (!s || passes_per_tick < 1 || fused_max < 0 || ctas_per_sm < 1 || !s->active.empty() ||
-        !s->inflight.empty())
+    if (!s || passes_per_tick < 1 || passes_per_tick > SV_MAX_PPT || fused_max < 0 || ctas_per_sm < 1 ||
+        !s->active.empty() || !s->inflight.empty())
         return WALLACE_EINVAL;
     s->passes_per_tick = passes_per_tick;
     s->fused_max = fused_max;

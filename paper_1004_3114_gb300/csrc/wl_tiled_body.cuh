@@ -85,10 +85,12 @@ __device__ __forceinline__ bool wl_tiled_ok(int L, int64_t N)
     return L <= TL_LMAX && N >= TL_MIN_N_CTA && N <= ((int64_t)1 << 28);
 }
 
+// j_end < 0 means N
 __device__ inline void wl_gather4_range(const WlTileJob &a, int64_t j, int64_t G, uint64_t &lo,
-                                        uint64_t &hi, uint32_t &bad)
+                                        uint64_t &hi, uint32_t &bad, int64_t j_end = -1)
 {
     const int64_t N = a.N, Np = a.Np;
+    const int64_t jmax = j_end < 0 ? N : j_end;
     int64_t idx[4], stp[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -96,7 +98,7 @@ __device__ inline void wl_gather4_range(const WlTileJob &a, int64_t j, int64_t G
                            (uint64_t)N);
         stp[i] = (int64_t)(((uint64_t)a.alpha[i] * (uint64_t)G) % (uint64_t)N);
     }
-    for (; j < N; j += G) {
+    for (; j < jmax; j += G) {
         float g[4], y[4];
 #pragma unroll
         for (int i = 0; i < 4; i++) {
@@ -119,9 +121,12 @@ __device__ inline void wl_gather4_range(const WlTileJob &a, int64_t j, int64_t G
 
 // Every thread of the CTA must call this (it synchronises the CTA).  `smem`
 // holds tl_smem_bytes() bytes, 16-byte aligned.  etarget <= TL_EMAX sets the
-// tile size (L * T <= etarget, T a multiple of 4, at least 4).
+// tile size (L * T <= etarget, T a multiple of 4, at least 4).  With nparts
+// > 1 only the tiles of part `part` (an even split of the pass's tiles into
+// nparts ranges) are done.
 __device__ inline void wl_tiled4_tiles(const WlTileJob &a, int L, int tile0, int tstep, int etarget,
-                                       float *smem, uint64_t &lo, uint64_t &hi, uint32_t &bad)
+                                       float *smem, uint64_t &lo, uint64_t &hi, uint32_t &bad,
+                                       int part = 0, int nparts = 1)
 {
     const int64_t N = a.N, Np = a.Np;
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -169,10 +174,12 @@ __device__ inline void wl_tiled4_tiles(const WlTileJob &a, int L, int tile0, int
         lanebase[i * TL_LMAX + l] = slot0[i] + p * SL[i] + (int)r;
     }
     const int maxlen = (int)((N + L - 1) / L);
-    const int ntiles = (maxlen + T - 1) / T;
+    const int ntiles_all = (maxlen + T - 1) / T;
+    const int tbeg = (int)((int64_t)ntiles_all * part / nparts);
+    const int ntiles = (int)((int64_t)ntiles_all * (part + 1) / nparts);
     __syncthreads();
 
-    for (int tile = tile0; tile < ntiles; tile += tstep) {
+    for (int tile = tbeg + tile0; tile < ntiles; tile += tstep) {
         const int t0 = tile * T;
         const int Tt = min(T, maxlen - t0);
         if (tid == 0)

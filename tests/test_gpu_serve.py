@@ -113,3 +113,26 @@ def test_server_trace_replay_reports_latency():
     st = srv.stats()
     assert st.completed == n and np.all(lat > 0) and st.p99_ms >= st.p50_ms > 0
     assert st.values_delivered == int(count.sum())
+
+
+@pytest.mark.parametrize("ppt", [1, 3])
+def test_server_large_pools_split_into_units(orc, ppt):
+    """Pools of 2^18..2^20 values run pass-major in several work units per
+    pass (tiled and plain-gather strides); every value still exact."""
+    Ns = np.array([1 << 16, 1 << 17, 100003, 45045, 70000, 300], dtype=np.int64)
+    seeds = np.array([21, 22, 23, 24, 25, 26], dtype=np.uint32)
+    srv = W.Server(4, Ns, seeds, 1 / 3, 1 << 30)
+    srv.set_tuning(ppt, 4096, 3)
+    rng = np.random.default_rng(9)
+    reqs = [(int(rng.integers(0, 6)), int(rng.integers(1, 400000)), float(rng.uniform(-2, 2)), 1.5)
+            for _ in range(40)]
+    ids = []
+    for k, (c, cnt, mu, sg) in enumerate(reqs):
+        ids.append(srv.submit(c, cnt, mu, sg))
+        if k % 5 == 4:
+            srv.progress()
+    srv.drain()
+    oracles = [orc.Generator(4, int(N), int(sd), 1 / 3) for N, sd in zip(Ns, seeds)]
+    for rid, (c, cnt, mu, sg) in zip(ids, reqs):
+        ref = oracles[c].fill(cnt, np.float32(mu), np.float32(sg))
+        assert np.array_equal(srv.result_host(rid).view(np.uint32), ref.view(np.uint32)), (c, cnt)
