@@ -111,19 +111,34 @@ __device__ __forceinline__ bool wl_stride_free(int32_t a, int64_t N, const int32
     return true;
 }
 
+// Every candidate divides 45 (315), so it is coprime to N exactly when N
+// shares none of its prime factors among 3, 5, 7: one bit per prime.  This
+// keeps the finaliser (one thread, between two passes) free of Euclid's
+// algorithm except in the rare fallback.
 __device__ inline void wl_draw_params(int n, int64_t N, uint64_t &s, int32_t *alpha, int64_t *gamma)
 {
     const int32_t div45[5] = {3, 5, 9, 15, 45};
+    const uint8_t fac45[5] = {1, 2, 1, 3, 3};            // bit 0: 3 | a, bit 1: 5 | a, bit 2: 7 | a
     const int32_t div315[11] = {3, 5, 7, 9, 15, 21, 35, 45, 63, 105, 315};
+    const uint8_t fac315[11] = {1, 2, 4, 1, 3, 5, 6, 3, 5, 7, 7};
     const int32_t *cand = n == 4 ? div45 : div315;
+    const uint8_t *fac = n == 4 ? fac45 : fac315;
     const int ncand = n == 4 ? 5 : 11;
+    const uint64_t uN = (uint64_t)N;
+    const uint32_t nfac = (uN % 3u == 0 ? 1u : 0u) | (uN % 5u == 0 ? 2u : 0u) | (uN % 7u == 0 ? 4u : 0u);
     for (int i = 0; i < n; i++) {
         const uint32_t u = wl_lcg_step(s);
         int32_t freec[11];
         int nf = 0;
-        for (int k = 0; k < ncand; k++)
-            if (wl_stride_free(cand[k], N, alpha, i))
+        for (int k = 0; k < ncand; k++) {
+            if (fac[k] & nfac)
+                continue;
+            bool used = false;
+            for (int t = 0; t < i; t++)
+                used |= alpha[t] == cand[k];
+            if (!used)
                 freec[nf++] = cand[k];
+        }
         int32_t a;
         if (nf > 0) {
             a = freec[((uint64_t)u * (uint64_t)nf) >> 32];
