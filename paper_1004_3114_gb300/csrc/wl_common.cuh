@@ -36,6 +36,8 @@ struct WlDevState {
     uint64_t acc_hi;
     uint32_t acc_bad;       // a value was non-finite or |y| >= 256
     uint32_t ticket;        // CTAs finished in the pass in flight
+    uint32_t tile_ctr;      // next tile of the pass in flight (dynamically scheduled kernels)
+    uint32_t pad2_;
     uint64_t q_lo, q_hi;    // Q of the most recent pool
     double q, S, S_prev, c, drift;
     int32_t have_prev;
@@ -339,6 +341,7 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
     st->acc_hi = 0;
     st->acc_bad = 0;
     __threadfence();
+    st->tile_ctr = 0;
     st->ticket = 0;
 }
 

@@ -8,7 +8,8 @@
 // strides drawn from the odd divisors of 45, L = 45 and a tile is 45 lanes by
 // T = 64 lane times: at most 32 spans of 0.75 to 11.5 KB.
 //
-// Pipeline (one CTA per SM, persistent over tiles):
+// Pipeline (one CTA per SM, persistent; tiles handed out dynamically from a
+// per-generator counter that the end-of-pass finaliser resets):
 //   producer warps -- for each span of the tile: its address, its 16-byte
 //                     alignment lead (stored for the consumers), its byte
 //                     count, and one bulk copy (cp.async.bulk, the TMA engine;
@@ -29,6 +30,8 @@
 // Every wait is bounded by a cycle budget; on expiry the CTA records
 // WALLACE_ETIMEOUT in the state, stops issuing work, waits (bounded) for its
 // copies still in flight, and leaves.
+#include <string.h>
+
 #include "wl_common.cuh"
 #include "wl_launch.h"
 
@@ -122,9 +125,15 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar_full[TM_STAGES];
     __shared__ __align__(8) uint64_t bar_empty[TM_STAGES];
+    __shared__ __align__(8) uint64_t bar_tile[TM_STAGES];   // a stage's tile index is published
+    __shared__ volatile int s_stage_tile[TM_STAGES];
     __shared__ uint64_t red[3 * (TM_THREADS / 32 + 1)];
     __shared__ volatile int s_abort;
 
+    // Launched as a programmatic dependent of the previous pass: the CTAs may
+    // start while that pass's last CTAs finish; wait for it to complete (its
+    // pool and parameters visible) before reading anything it wrote.
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     WlDevState *st = a.st;
     const float *__restrict__ src = (const float *)a.src;
     float *__restrict__ dst = (float *)a.dst;
@@ -214,6 +223,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
             for (int s = 0; s < TM_STAGES; s++) {
                 mbar_init(smem_u32(&bar_full[s]), 32 * TM_PROD_WARPS);
                 mbar_init(smem_u32(&bar_empty[s]), TM_CONS_WARPS);
+                mbar_init(smem_u32(&bar_tile[s]), 1);
             }
             s_abort = 0;
             asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -255,8 +265,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
 #pragma unroll
             for (int s = 0; s < TM_STAGES; s++)
                 issued[s] = 0;
-            int it = 0;
-            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+            const int pw = warp - TM_CONS_WARPS;
+            for (int it = 0;; it++) {
                 const int s = it % TM_STAGES;
                 const int k = it / TM_STAGES;
                 if (s_abort)
@@ -264,6 +274,26 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
                 if (k > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (uint32_t)((k - 1) & 1))) {
                     s_abort = 1;
                     atomicOr(&st->status, WL_ETIMEOUT);
+                    break;
+                }
+                // tiles are handed out dynamically: producer warp 0 takes the
+                // next one from the generator's counter and publishes it
+                if (pw == 0) {
+                    if (lane == 0) {
+                        s_stage_tile[s] = (int)atomicAdd(&st->tile_ctr, 1u);
+                        mbar_arrive(smem_u32(&bar_tile[s]));
+                    }
+                    __syncwarp();
+                } else if (!mbar_wait(smem_u32(&bar_tile[s]), (uint32_t)(k & 1))) {
+                    s_abort = 1;
+                    atomicOr(&st->status, WL_ETIMEOUT);
+                    break;
+                }
+                const int tile = s_stage_tile[s];
+                if (tile >= ntiles) {
+                    // no more tiles: release the consumers without data
+                    mbar_arrive(smem_u32(&bar_full[s]));
+                    issued[s] = k + 1;
                     break;
                 }
                 const int t0 = tile * T;
@@ -324,8 +354,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
                 outk[k] = mode[k] == 1 ? out + (q0 - w0) : out;
             }
             uint32_t emax = 0;
-            int it = 0;
-            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+            for (int it = 0;; it++) {
                 const int s = it % TM_STAGES;
                 const int k = it / TM_STAGES;
                 if (s_abort)
@@ -335,10 +364,14 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
                     atomicOr(&st->status, WL_ETIMEOUT);
                     break;
                 }
+                const int tile = s_stage_tile[s];
+                if (tile >= ntiles)
+                    break;
                 const int t0 = tile * T;
                 const int Tt = min(T, maxlen - t0);
                 const float *sdata = stage0 + s * tm_stage_words();
                 const int *lead = (const int *)(sdata + tm_stage_data_words());
+                uint64_t tl = 0;   // this tile's terms: at most 24 per thread, each below 2^48
                 for (int l = warp; l < L; l += TM_CONS_WARPS) {
                     const int jl = J[l];
                     const int tmax = min(Tt, J[l + 1] - jl - t0);   // lane times of lane l in this tile
@@ -364,8 +397,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
                         for (int kk = 0; kk < 4; kk++) {
                             dstk[kk][j] = y[kk];
                             if (v2) dstk[kk][j + 32] = z[kk];
-                            lo += term32(y[kk], emax);
-                            if (v2) lo += term32(z[kk], emax);
+                            tl += term32(y[kk], emax);
+                            if (v2) tl += term32(z[kk], emax);
                             if (mode[kk] == 1) {
                                 outk[kk][j] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
                                 if (v2) outk[kk][j + 32] = __fadd_rn(mu, __fmul_rn(sigma, z[kk]));
@@ -380,6 +413,9 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
                         }
                     }
                 }
+                // a CTA may take any number of tiles: carry into 128 bits
+                lo += tl;
+                hi += lo < tl ? 1ull : 0ull;
                 __syncwarp();
                 if (lane == 0)
                     mbar_arrive(smem_u32(&bar_empty[s]));
@@ -388,6 +424,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
         }
     }
 
+    // this CTA's tiles are done: the next pass may start launching
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st) && tid == 0) {
         double x = (double)__ldcg(&dst[wl_phys(a.nu - 1, N, Np)]);
@@ -401,12 +439,9 @@ bool g_tma_configured = false;
 
 bool wl_tma_supported(int n, int64_t N, int fp64, int sm_count)
 {
-    // each consumer thread sums at most ceil(nu / (SMs * consumer threads))
-    // terms below 2^48 in 64 bits: keep that count below 2^16
-    const int64_t nu = (int64_t)n * N;
-    const int64_t per_thread = nu / ((int64_t)(sm_count > 0 ? sm_count : 1) * TM_CONS_THREADS) + 1;
-    return n == 4 && !fp64 && N >= TM_MIN_N && (N & 3) == 0 && N <= ((int64_t)1 << 28) &&
-           per_thread < 65536;
+    // lane starts, span starts and slot offsets are held in 32-bit integers
+    (void)sm_count;
+    return n == 4 && !fp64 && N >= TM_MIN_N && (N & 3) == 0 && N <= ((int64_t)1 << 28);
 }
 
 cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, cudaStream_t stream)
@@ -419,6 +454,19 @@ cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, cudaStream_t stream
             return e;
         g_tma_configured = true;
     }
-    tma_kernel<<<sm_count, TM_THREADS, smem, stream>>>(a);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(sm_count);
+    cfg.blockDim = dim3(TM_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, tma_kernel, a);
+    if (e != cudaSuccess)
+        return e;
     return cudaGetLastError();
 }
