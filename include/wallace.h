@@ -80,13 +80,16 @@ typedef struct {
     int64_t passes;       /* passes completed                                            */
     int32_t status;       /* sticky WALLACE_* bits                                       */
     int32_t bad;          /* a pool value was non-finite or |y| >= 256                   */
-    uint64_t lcg;         /* uniform generator state after the last draw                 */
+    uint64_t lcg;         /* uniform generator state after the strides of the most recent
+                             pass were drawn (after the initial pool before any pass)    */
     int32_t alpha[8];     /* strides of the most recent pass                             */
     int64_t gamma[8];     /* offsets of the most recent pass                             */
     int64_t R;            /* values returned per pass                                    */
     int64_t cursor;       /* index in the current pool of the next value to return       */
     double kernel_ms;     /* summed pass-kernel time when timing is on                   */
     int64_t kernel_launches; /* pass kernels timed                                       */
+    int64_t launches;     /* kernels launched by passes and fills (pass and drain kernels),
+                             counted whether or not timing is on                         */
 } wallace_stats_t;
 
 /*

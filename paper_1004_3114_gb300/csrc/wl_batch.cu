@@ -458,7 +458,7 @@ int wallace_batch_stats(wallace_batch_t *b, int s, wallace_stats_t *out)
     out->passes = x.passes;
     out->status = b->status | x.status;
     out->bad = x.bad;
-    out->lcg = x.lcg;
+    out->lcg = x.lcg_rep;
     for (int i = 0; i < 8; i++) {
         out->alpha[i] = x.last.alpha[i];
         out->gamma[i] = x.last.gamma[i];

@@ -22,6 +22,7 @@ struct wallace {
     cudaStream_t stream = nullptr;
     void *pool[2] = {nullptr, nullptr};
     int cur = 0;
+    int64_t pass_index = 0;   // passes launched (selects a pass's strides slot)
     WlDevState *st = nullptr;
     int64_t cursor = 0;
     int status = 0;
@@ -31,6 +32,7 @@ struct wallace {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
     double kernel_ms = 0.0;
     int64_t kernel_launches = 0;
+    int64_t launches = 0;   // pass and drain kernels, always counted
     // host-fill pipeline
     float *stage[2] = {nullptr, nullptr};
     int64_t stage_cap = 0;
@@ -69,6 +71,7 @@ struct KernelTimer {
     cudaEvent_t a = nullptr, b = nullptr;
     explicit KernelTimer(wallace_t *hh) : h(hh)
     {
+        h->launches++;
         if (h->timing) {
             a = take_event(h);
             b = take_event(h);
@@ -122,6 +125,7 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
         // a single fused pass: output window must start at 0 (a prefix)
         e = wl_launch_fused(h->pool[h->cur], h->pool[1 - h->cur], fp64, h->n, h->N, h->Np, h->st,
                             1, h->R, w1 - w0, out, mu, sigma, h->stream);
+        h->pass_index += 1;
         // fused writes the new pool back in place: current buffer unchanged
         return cuda_fail(h, e);
     }
@@ -138,6 +142,7 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
     a.w1 = w1;
     a.mu = mu;
     a.sigma = sigma;
+    a.pass = h->pass_index;
     {
         KernelTimer t(h);
         if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_TMA) &&
@@ -153,6 +158,7 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
     if (e != cudaSuccess)
         return cuda_fail(h, e);
     h->cur = 1 - h->cur;
+    h->pass_index += 1;
     return WALLACE_OK;
 }
 
@@ -167,6 +173,7 @@ int fill_impl(wallace_t *h, void *out, int64_t count, double mu, double sigma)
         int64_t take = h->R - h->cursor;
         if (take > count)
             take = count;
+        h->launches++;
         cudaError_t e = wl_launch_drain(h->pool[h->cur], fp64, h->N, h->Np, h->cursor, take, o, mu,
                                         sigma, h->sm_count, h->stream);
         if (e != cudaSuccess)
@@ -187,6 +194,7 @@ int fill_impl(wallace_t *h, void *out, int64_t count, double mu, double sigma)
             e = wl_launch_fused(h->pool[h->cur], h->pool[1 - h->cur], fp64, h->n, h->N, h->Np,
                                 h->st, passes, h->R, last, o + done * es, mu, sigma, h->stream);
         }
+        h->pass_index += passes;
         if (e != cudaSuccess)
             return cuda_fail(h, e);
         h->cursor = last;
@@ -499,7 +507,7 @@ int wallace_stats(wallace_t *h, wallace_stats_t *out)
     out->passes = s.passes;
     out->status = h->status | s.status;
     out->bad = s.bad;
-    out->lcg = s.lcg;
+    out->lcg = s.lcg_rep;
     for (int i = 0; i < 8; i++) {
         out->alpha[i] = s.last.alpha[i];
         out->gamma[i] = s.last.gamma[i];
@@ -508,6 +516,7 @@ int wallace_stats(wallace_t *h, wallace_stats_t *out)
     out->cursor = h->cursor;
     out->kernel_ms = h->kernel_ms;
     out->kernel_launches = h->kernel_launches;
+    out->launches = h->launches;
     return out->status;
 }
 

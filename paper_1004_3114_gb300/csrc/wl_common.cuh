@@ -26,14 +26,30 @@ struct WlParams {
     double c64;
 };
 
+// Strides and offsets of one pass.
+struct WlStrides {
+    int32_t alpha[8];
+    int64_t gamma[8];
+};
+
 // One generator's device state.  The finaliser of a pass writes `next`;
-// the following pass reads it.  The accumulators are zero between passes.
+// the following pass reads it.  The strides are drawn one pass ahead: with k
+// passes completed, ahead[k & 1] holds pass k's (also in `next`) and
+// ahead[(k + 1) & 1] pass k + 1's, so a kernel can read its own pass's
+// strides before the previous pass has finished.  The uniform sequence is
+// the same; `lcg_rep` is the state after the most recent pass's strides were
+// drawn (after the initial pool before the first pass).  The accumulators are
+// zero between passes.
 struct WlDevState {
     WlParams next;          // parameters for the next pass
     WlParams last;          // parameters the most recent pass used
-    uint64_t lcg;           // uniform generator state
-    uint64_t acc_lo;        // running Q of the pass in flight (128-bit)
-    uint64_t acc_hi;
+    WlStrides ahead[2];     // strides of passes k and k + 1, in slots k & 1 and (k + 1) & 1
+    uint64_t lcg;           // uniform generator state (after the draw for pass k + 1)
+    uint64_t lcg_pend;      // state before the draw for pass k + 1
+    uint64_t lcg_rep;       // state before the draw for pass k (after the draw for pass k - 1)
+    uint64_t acc0;          // running Q of the pass in flight, as three limbs that
+    uint64_t acc1;          // CTAs add to without carries: bits 0-31, 32-63 and
+    uint64_t acc2;          // 64-127 of each CTA's 128-bit sum (see wl_acc_read)
     uint32_t acc_bad;       // a value was non-finite or |y| >= 256
     uint32_t ticket;        // CTAs finished in the pass in flight
     uint32_t tile_ctr;      // next tile of the pass in flight (dynamically scheduled kernels)
@@ -273,15 +289,43 @@ __device__ __forceinline__ void wl_cta_reduce_to_state(uint64_t lo, uint64_t hi,
         }
         bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
         if (lane == 0) {
-            unsigned long long old = atomicAdd((unsigned long long *)&st->acc_lo,
-                                               (unsigned long long)lo);
-            uint64_t carry = ((uint64_t)old + lo < (uint64_t)old) ? 1ull : 0ull;
-            if (hi + carry)
-                atomicAdd((unsigned long long *)&st->acc_hi, (unsigned long long)(hi + carry));
+            // fire-and-forget adds: each limb sum stays below 2^64 for up to
+            // 2^32 CTAs, so no carry has to travel between the limbs here
+            atomicAdd((unsigned long long *)&st->acc0, (unsigned long long)(lo & 0xffffffffull));
+            atomicAdd((unsigned long long *)&st->acc1, (unsigned long long)(lo >> 32));
+            if (hi)
+                atomicAdd((unsigned long long *)&st->acc2, (unsigned long long)hi);
             if (bad)
                 atomicOr(&st->acc_bad, 1u);
         }
     }
+}
+
+// The pass's Q = acc0 + acc1 2^32 + acc2 2^64 as a 128-bit integer.
+__device__ __forceinline__ void wl_acc_read(WlDevState *st, uint64_t &lo, uint64_t &hi)
+{
+    volatile WlDevState *vs = st;
+    const uint64_t a0 = vs->acc0, a1 = vs->acc1, a2 = vs->acc2;
+    const uint64_t t = a0 + (a1 << 32);
+    hi = a2 + (a1 >> 32) + (t < a0 ? 1ull : 0ull);
+    lo = t;
+}
+
+// With k = st->passes (already counted): `next` takes pass k's strides from
+// their slot and pass k + 1's are drawn into the other.  s is the uniform
+// state after the draw for pass k, rep the state before it.
+__device__ inline void wl_advance_strides(WlDevState *st, int n, int64_t N, uint64_t s, uint64_t rep)
+{
+    const int64_t k = st->passes;
+    const WlStrides &cur = st->ahead[k & 1];
+    for (int i = 0; i < 8; i++) {
+        st->next.alpha[i] = cur.alpha[i];
+        st->next.gamma[i] = cur.gamma[i];
+    }
+    st->lcg_rep = rep;
+    st->lcg_pend = s;
+    wl_draw_params(n, N, s, st->ahead[(k + 1) & 1].alpha, st->ahead[(k + 1) & 1].gamma);
+    st->lcg = s;
 }
 
 // ---- end of pass: chi-squared rescale (Eq. 3) and drift monitor ------------
@@ -293,7 +337,9 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
                                    bool fp64, bool is_pass)
 {
     volatile WlDevState *vs = st;
-    uint64_t lo = vs->acc_lo, hi = vs->acc_hi;
+    __threadfence();
+    uint64_t lo, hi;
+    wl_acc_read(st, lo, hi);
     uint32_t bad = vs->acc_bad;
     double q;
     if (!fp64) {
@@ -328,37 +374,115 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
     st->drift = drift;
     st->bad = (int32_t)bad;
     st->status = status;
+    uint64_t s = st->lcg, rep = st->lcg_pend;
     if (is_pass) {
         st->last = st->next;
         st->passes += 1;
+    } else {
+        // initial pool: draw the strides of the first pass as well
+        rep = s;
+        wl_draw_params(n, N, s, st->ahead[st->passes & 1].alpha, st->ahead[st->passes & 1].gamma);
     }
+    wl_advance_strides(st, n, N, s, rep);
     st->next.c64 = c;
     st->next.c32 = __double2float_rn(c);
-    uint64_t s = st->lcg;
-    wl_draw_params(n, N, s, st->next.alpha, st->next.gamma);
-    st->lcg = s;
-    st->acc_lo = 0;
-    st->acc_hi = 0;
+    st->acc0 = 0;
+    st->acc1 = 0;
+    st->acc2 = 0;
     st->acc_bad = 0;
     __threadfence();
     st->tile_ctr = 0;
     st->ticket = 0;
 }
 
-// Last-CTA detection: every thread fences its global writes, then one thread
-// takes a ticket; the CTA that draws the last ticket runs the finaliser.
+// The same end-of-pass update as wl_finalise for a pass over a binary32 pool,
+// run by the whole last CTA: its three independent chains go to three warps
+// -- the scale (S and c, Eq. 3), the drift ratio (Section 8) and the next
+// pass's parameters -- so their binary64 divisions and square roots and the
+// parameter draw overlap.  rnu = sqrt(2 nu - 1), correctly rounded; xp points
+// at the withheld last value of the new pool.  Every thread of the CTA calls.
+__device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, double rnu, const float *xp)
+{
+    __shared__ double s_S, s_c;
+    __shared__ int32_t s_flag[2];
+    volatile WlDevState *vs = st;
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0 && warp < 3) {
+        __threadfence();
+        if (warp < 2) {
+            uint64_t lo, hi;
+            wl_acc_read(st, lo, hi);
+            const double q = __dmul_rn(__ull2double_rn(lo), 1.0 / 4294967296.0);
+            if (warp == 0) {
+                const uint32_t bad = (vs->acc_bad != 0u || hi != 0) ? 1u : 0u;
+                const double xr = __dadd_rn((double)__ldcg(xp), rnu);
+                const double S = __dmul_rn(__dmul_rn(xr, xr), 0.5);
+                double c = 1.0;
+                int32_t f = 0;
+                if (bad || !(q > 0.0))
+                    f = WL_ECORRUPT;
+                else
+                    c = __dsqrt_rn(__ddiv_rn(S, q));
+                st->q_lo = lo;
+                st->q_hi = hi;
+                st->q = q;
+                st->S = S;
+                st->c = c;
+                st->bad = (int32_t)bad;
+                s_S = S;
+                s_c = c;
+                s_flag[0] = f;
+            } else {
+                double drift = 0.0;
+                int32_t f = 0;
+                if (vs->have_prev) {
+                    drift = __dsub_rn(__ddiv_rn(q, vs->S_prev), 1.0);
+                    if (!(fabs(drift) <= 1e-3))
+                        f = WL_ECORRUPT;
+                }
+                st->drift = drift;
+                s_flag[1] = f;
+            }
+        } else {
+            st->last = st->next;
+            st->passes = vs->passes + 1;
+            wl_advance_strides(st, n, N, vs->lcg, vs->lcg_pend);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->next.c64 = s_c;
+        st->next.c32 = __double2float_rn(s_c);
+        st->S_prev = s_S;
+        st->have_prev = 1;
+        st->status = vs->status | s_flag[0] | s_flag[1];
+        st->acc0 = 0;
+        st->acc1 = 0;
+        st->acc2 = 0;
+        st->acc_bad = 0;
+        __threadfence();
+        st->tile_ctr = 0;
+        st->ticket = 0;
+    }
+}
+
+// Last-CTA detection: after a CTA barrier one thread takes a ticket with an
+// acquire-release atomic, which publishes the CTA's writes (release is
+// cumulative over the barrier) and, for the CTA that draws the last ticket,
+// makes every other CTA's writes visible before the finaliser runs.
 __device__ __forceinline__ bool wl_last_cta(WlDevState *st)
 {
     __shared__ bool s_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned t = atomicAdd(&st->ticket, 1u);
+        unsigned t;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;\n"
+                     : "=r"(t)
+                     : "l"(&st->ticket)
+                     : "memory");
         s_last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
     }
     __syncthreads();
-    if (s_last)
-        __threadfence();
     return s_last;
 }
 

@@ -19,6 +19,7 @@ struct WlPassArgs {
     void *out;
     int64_t w0, w1;
     double mu, sigma;
+    int64_t pass;   // passes completed before this one (selects its strides' slot)
 };
 
 cudaError_t wl_launch_init(void *pool, int fp64, int n, int64_t N, int64_t Np, uint32_t seed,

@@ -284,11 +284,18 @@ struct Request {
     double t_submit = 0, t_done = 0;
 };
 
+struct CopyBack {
+    float *dst;
+    const float *src;
+    size_t bytes;
+};
+
 struct Tick {
     cudaEvent_t ev;
     int slot;
     std::vector<int64_t> finishing;
     std::vector<void *> deferred_free;
+    std::vector<CopyBack> copies;   // pools that end in a scratch buffer, copied home
 };
 
 double now_s()
@@ -314,6 +321,7 @@ struct wallace_server {
     std::vector<int64_t> active;
     std::deque<Tick> inflight;
     std::vector<int64_t> completed_unpolled;
+    int64_t held_outputs = 0;   // completed requests whose output is not yet released
     // tick slots: device work arrays and work counters
     int nslots = 4;
     std::vector<char *> d_work;
@@ -419,6 +427,8 @@ void reap(wallace_server_t *s, bool block)
         for (int64_t id : t.finishing) {
             Request &r = s->reqs[id];
             r.reaped = true;
+            if (r.out)
+                s->held_outputs++;
             r.t_done = tn;
             s->latencies.push_back(1e3 * (tn - r.t_submit));
             s->completed++;
@@ -539,14 +549,15 @@ int enqueue_tick(wallace_server_t *s)
         if (r.done >= r.count) {
             r.finished = true;
             t.finishing.push_back(id);
-            // the pool ends in the scratch buffer: it becomes the resident one
+            // Client pools never move: a pool that ends in the scratch buffer
+            // is copied back to its home after this tick.  (Adopting the
+            // scratch buffer as the new home would scatter pools through the
+            // arena until no free block fits a request, with nothing in flight
+            // to free one.)
             if (r.scratch) {
-                if (r.loc == 1) {
-                    t.deferred_free.push_back(c.buf);
-                    c.buf = r.scratch;
-                } else {
-                    t.deferred_free.push_back(r.scratch);
-                }
+                if (r.loc == 1)
+                    t.copies.push_back(CopyBack{c.buf, r.scratch, pool_bytes(s, c)});
+                t.deferred_free.push_back(r.scratch);
                 r.scratch = nullptr;
                 r.loc = 0;
             }
@@ -612,6 +623,9 @@ int enqueue_tick(wallace_server_t *s)
             (int)punits[p].size(), dq + 1 + p);
         e = cudaGetLastError();
     }
+    for (size_t k = 0; k < t.copies.size() && e == cudaSuccess; k++)
+        e = cudaMemcpyAsync(t.copies[k].dst, t.copies[k].src, t.copies[k].bytes, cudaMemcpyDeviceToDevice,
+                            s->stream);
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming);
     if (e == cudaSuccess)
@@ -798,6 +812,11 @@ int wallace_server_progress(wallace_server_t *s)
     admit(s);
     int rc = enqueue_tick(s);
     reap(s, false);
+    // Requests wait, none runs, nothing in flight and every output released:
+    // no later call can free memory, so the head request can never fit.
+    if (!rc && s->active.empty() && s->inflight.empty() && !s->admit_order.empty() &&
+        s->held_outputs == 0)
+        s->status |= WALLACE_ENOMEM;
     return rc ? rc : s->status;
 }
 
@@ -867,6 +886,8 @@ int wallace_server_release(wallace_server_t *s, int64_t id)
     if (!r.reaped)
         return WALLACE_ESTATE;
     if (!r.released) {
+        if (r.out)
+            s->held_outputs--;
         s->arena.free(r.out);
         r.out = nullptr;
         r.released = true;

@@ -21,13 +21,13 @@
 #include "wallace.h"
 #include "wl_common.cuh"
 
-#define WL_STATIC_STATE_BYTES 512
+#define WL_STATIC_STATE_BYTES 1024
 #define WL_STATIC_BYTES (WL_STATIC_STATE_BYTES + 4ull * WALLACE_STATIC_MAX_VALUES)
 
 static_assert(sizeof(WlDevState) <= WL_STATIC_STATE_BYTES, "state block does not fit");
 
-// Scratch of wallace_pass_static: [0, 512) reduction/finaliser block,
-// [512, 512 + 4 * WALLACE_STATIC_MAX_VALUES) the new pool.
+// Scratch of wallace_pass_static: [0, 1024) reduction/finaliser block,
+// [1024, 1024 + 4 * WALLACE_STATIC_MAX_VALUES) the new pool.
 static __device__ __align__(256) unsigned char g_wl_static_scratch[WL_STATIC_BYTES];
 
 namespace {

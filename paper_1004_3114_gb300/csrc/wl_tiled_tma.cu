@@ -30,6 +30,7 @@
 // Every wait is bounded by a cycle budget; on expiry the CTA records
 // WALLACE_ETIMEOUT in the state, stops issuing work, waits (bounded) for its
 // copies still in flight, and leaves.
+#include <math.h>
 #include <string.h>
 
 #include "wl_common.cuh"
@@ -54,6 +55,26 @@ __host__ __device__ constexpr int tm_common_words() { return (TM_LMAX + 1) + 4 *
 __host__ __device__ constexpr size_t tm_smem_bytes()
 {
     return sizeof(float) * (size_t)(TM_STAGES * tm_stage_words() + tm_common_words());
+}
+
+// x / d for x >= 0 and d a divisor of 45: constant divisors, so each case
+// is a multiply and shift instead of a division routine
+__device__ __forceinline__ int tm_div45(int x, int d)
+{
+    switch (d) {
+    case 1:
+        return x;
+    case 3:
+        return x / 3;
+    case 5:
+        return x / 5;
+    case 9:
+        return x / 9;
+    case 15:
+        return x / 15;
+    default:
+        return x / 45;
+    }
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -120,7 +141,21 @@ __device__ __forceinline__ uint64_t term32(float y, uint32_t &emax)
     return ((uint64_t)m * (uint64_t)m) >> rs;
 }
 
-__global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
+// Wait for the previous pass to complete (its pool, state and scale visible),
+// let the next pass's CTAs launch (they take SMs as this pass's CTAs leave
+// and run their own prologue meanwhile), and return this pass's scale c.
+// Every thread of the CTA calls.
+__device__ __forceinline__ float tm_wait_prev(WlDevState *st, volatile float *s_c)
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    if (threadIdx.x == 0)
+        *s_c = st->next.c32;
+    __syncthreads();
+    return *s_c;
+}
+
+__global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double rnu)
 {
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar_full[TM_STAGES];
@@ -130,36 +165,63 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
     __shared__ uint64_t red[3 * (TM_THREADS / 32 + 1)];
     __shared__ volatile int s_abort;
 
-    // Launched as a programmatic dependent of the previous pass: the CTAs may
-    // start while that pass's last CTAs finish; wait for it to complete (its
-    // pool and parameters visible) before reading anything it wrote.
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    // Launched as a programmatic dependent of the previous pass: the CTAs
+    // start while that pass drains.  Everything up to tm_wait_prev() uses only
+    // this pass's strides, drawn two finalisers back (slot pass & 1, final
+    // since the pass before the previous one completed); the pool and the
+    // scale c are read after the wait.
     WlDevState *st = a.st;
     const float *__restrict__ src = (const float *)a.src;
     float *__restrict__ dst = (float *)a.dst;
     const int64_t N = a.N, Np = a.Np;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // one warp per CTA reads the strides and shares them: every CTA starts at
+    // once, and 600 threads each loading the same few words would queue on
+    // one L2 slice
+    __shared__ int64_t s_gam[4];
+    __shared__ int s_alpha[4];
+    __shared__ volatile float s_c;
+    if (warp == 0) {
+        const WlStrides *cur = &st->ahead[a.pass & 1];
+        if (lane < 4)
+            s_alpha[lane] = __ldcg(&cur->alpha[lane]);
+        else if (lane < 8)
+            s_gam[lane - 4] = (int64_t)__ldcg((const long long *)&cur->gamma[lane - 4]);
+    }
+    __syncthreads();
     int alpha[4];
     int64_t gam[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        alpha[i] = st->next.alpha[i];
-        gam[i] = st->next.gamma[i];
+        alpha[i] = s_alpha[i];
+        gam[i] = s_gam[i];
     }
-    const float c = st->next.c32;
+    float c;
     float *out = (float *)a.out;
     const float mu = (float)a.mu, sigma = (float)a.sigma;
     const int64_t w0 = a.w0, w1 = a.w1;
 
-    int L = alpha[0];
+    // L = lcm of the strides when all divide 45 (3^e3 5^e5); any other stride
+    // (the coprimality fallback) sends the pass to the plain gather below
+    int e3 = 0, e5 = 0;
+    bool div45 = true;
 #pragma unroll
-    for (int i = 1; i < 4; i++)
-        L = L / (int)wl_gcd(L, alpha[i]) * alpha[i];
+    for (int i = 0; i < 4; i++) {
+        const int al = alpha[i];
+        if (al == 3 || al == 15)
+            e3 = max(e3, 1);
+        if (al == 9 || al == 45)
+            e3 = 2;
+        if (al == 5 || al == 15 || al == 45)
+            e5 = 1;
+        div45 &= al == 3 || al == 5 || al == 9 || al == 15 || al == 45;
+    }
+    const int L = div45 ? (e3 == 2 ? 9 : (e3 == 1 ? 3 : 1)) * (e5 ? 5 : 1) : TM_LMAX + 1;
     int m[4], sb[5];
     sb[0] = 0;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        m[i] = L <= TM_LMAX ? L / alpha[i] : 0;
+        m[i] = div45 ? tm_div45(L, alpha[i]) : 0;
         sb[i + 1] = sb[i] + m[i];
     }
     const int nspans = sb[4];
@@ -169,6 +231,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
 
     if (L > TM_LMAX || nspans > TM_MAXSPANS || N < TM_MIN_N || (N & 3)) {
         // plain strided gather for this pass (strides with a larger lcm)
+        c = tm_wait_prev(st, &s_c);
         const int64_t G = (int64_t)gridDim.x * blockDim.x;
         int64_t j = (int64_t)blockIdx.x * blockDim.x + tid;
         int64_t idx[4], stp[4];
@@ -197,7 +260,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
             }
         }
     } else {
-        const int T = TM_ETARGET / L;
+        const int T = tm_div45(TM_ETARGET, L);
         int SL[4], slot0[4];
         slot0[0] = 0;
 #pragma unroll
@@ -212,12 +275,18 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
         int *lanebase = J + (TM_LMAX + 1);
         int *spanC = lanebase + 4 * TM_LMAX;
 
-        for (int l = tid; l <= L; l += TM_THREADS)
-            J[l] = (int)(((int64_t)l * N + L - 1) / L);
+        // ceil(l N / L) and ceil(p N / m_i) as l (N / L) + ceil(l (N mod L) / L):
+        // 32-bit arithmetic (N < 2^31, l (N mod L) < L^2)
+        const int N32 = (int)N;
+        for (int l = tid; l <= L; l += TM_THREADS) {
+            const int qN = tm_div45(N32, L), rN = N32 - qN * L;
+            J[l] = l * qN + tm_div45(l * rN + L - 1, L);
+        }
         for (int s = tid; s < nspans; s += TM_THREADS) {
-            int i = (s >= sb[1]) + (s >= sb[2]) + (s >= sb[3]);
-            int p = s - sb[i];
-            spanC[s] = (int)(((int64_t)p * N + m[i] - 1) / m[i]);
+            const int i = (s >= sb[1]) + (s >= sb[2]) + (s >= sb[3]);
+            const int p = s - sb[i], mi = m[i];
+            const int qN = tm_div45(N32, mi), rN = N32 - qN * mi;
+            spanC[s] = p * qN + tm_div45(p * rN + mi - 1, mi);
         }
         if (tid == 0) {
             for (int s = 0; s < TM_STAGES; s++) {
@@ -233,13 +302,14 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
         // per lane and sub-vector: slot offset of the lane's first value,
         // packed with the index of the span that holds it (span < 32)
         for (int e = tid; e < 4 * L; e += TM_THREADS) {
-            int i = e / L, l = e - i * L;
-            int w = l / m[i], p = l - w * m[i];
+            int i = tm_div45(e, L), l = e - i * L;
+            int w = tm_div45(l, m[i]), p = l - w * m[i];
             int64_t r = (int64_t)alpha[i] * J[l] - (int64_t)w * N - spanC[sb[i] + p];
             lanebase[i * TM_LMAX + l] = ((slot0[i] + p * SL[i] + (int)r) << 5) | (sb[i] + p);
         }
         __syncthreads();
-        const int maxlen = (int)((N + L - 1) / L);
+        c = tm_wait_prev(st, &s_c);
+        const int maxlen = tm_div45(N32 + L - 1, L);
         const int ntiles = (maxlen + T - 1) / T;
 
         if (warp >= TM_CONS_WARPS) {
@@ -424,13 +494,9 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a)
         }
     }
 
-    // this CTA's tiles are done: the next pass may start launching
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
-    if (wl_last_cta(st) && tid == 0) {
-        double x = (double)__ldcg(&dst[wl_phys(a.nu - 1, N, Np)]);
-        wl_finalise(st, 4, N, a.nu, x, false, true);
-    }
+    if (wl_last_cta(st))
+        wl_finalise_cta(st, 4, N, rnu, &dst[wl_phys(a.nu - 1, N, Np)]);
 }
 
 bool g_tma_configured = false;
@@ -465,7 +531,8 @@ cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, cudaStream_t stream
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, tma_kernel, a);
+    const double rnu = sqrt(2.0 * (double)a.nu - 1.0);   // IEEE square root: correctly rounded
+    cudaError_t e = cudaLaunchKernelEx(&cfg, tma_kernel, a, rnu);
     if (e != cudaSuccess)
         return e;
     return cudaGetLastError();

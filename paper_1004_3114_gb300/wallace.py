@@ -34,7 +34,7 @@ class Stats(C.Structure):
         ("c", C.c_double), ("c32", C.c_float), ("drift", C.c_double), ("passes", C.c_int64),
         ("status", C.c_int32), ("bad", C.c_int32), ("lcg", C.c_uint64),
         ("alpha", C.c_int32 * 8), ("gamma", C.c_int64 * 8), ("R", C.c_int64),
-        ("cursor", C.c_int64), ("kernel_ms", C.c_double), ("kernel_launches", C.c_int64),
+        ("cursor", C.c_int64), ("kernel_ms", C.c_double), ("kernel_launches", C.c_int64), ("launches", C.c_int64),
     ]
 
     @property

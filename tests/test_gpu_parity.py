@@ -42,6 +42,8 @@ def assert_stats_equal(g, o, what=""):
     assert gs.Q == os_.Q, what
     assert gs.S == os_.S and gs.c == os_.c and gs.c32 == os_.c32, what
     assert gs.passes == os_.passes, what
+    assert gs.drift == os_.drift, what
+    assert gs.lcg == os_.lcg, what     # uniform state after drawing the next pass's strides
     assert list(gs.alpha[:g.n]) == list(os_.alpha[:g.n]), what
     assert list(gs.gamma[:g.n]) == list(os_.gamma[:g.n]), what
     assert gs.status == os_.status, what
@@ -211,6 +213,14 @@ def test_streams_and_timing(orc):
     assert_same(out.cpu().numpy(), o.fill(g.R * 3))
     st = g.stats()
     assert st.kernel_launches == 3 and st.kernel_ms > 0
+    assert st.launches == 3            # three passes, nothing left to drain first
+    g.set_timing(False)
+    with torch.cuda.stream(s):
+        g.fill(out[: g.R // 2])
+        g.fill(out[: g.R])             # drains the rest of the pool, then one pass
+    s.synchronize()
+    st = g.stats()
+    assert st.kernel_launches == 3 and st.launches == 3 + 1 + 2
 
 
 def test_full_size_pool_parity(orc):

@@ -6,6 +6,8 @@ request's output equals the oracle's fill of the same count, mu and sigma
 after that client's earlier requests, and the same client's requests served
 alone give the same bytes as in the mix.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -78,7 +80,9 @@ def test_server_tight_budget_still_completes(orc):
     srv = W.Server(4, Ns, seeds, 0.5, pools + 2 * (max_out + max_scratch) + (1 << 16))
     ids = [srv.submit(c, cnt, mu, sg) for c, cnt, mu, sg in reqs]
     got = {}
+    deadline = time.monotonic() + 120.0
     while len(got) < len(ids):
+        assert time.monotonic() < deadline, f"only {len(got)} of {len(ids)} requests completed"
         srv.progress()
         for rid in srv.poll():
             got[rid] = srv.result_host(rid)
