@@ -160,22 +160,28 @@ def reduce_over_ranks(ms: float, units: int, dist, device) -> tuple[float, int]:
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    warm, steps = max(args.warmup, 0), max(args.steps, 1)
+    # One oracle pass takes about 0.2 s on one host core: the run is bounded
+    # by a time budget (at most 2 warm-up passes, then steps until K are done
+    # or the budget is spent), and the rate is taken over the steps done.
+    warm, steps = min(max(args.warmup, 0), 2), max(args.steps, 1)
     from oracle import py_oracle as orc
     import numpy as np
     g = orc.Generator(N_SUB, N_LEN, SEED, FRAC)
     out = np.empty(R, dtype=np.float32)
     for _ in range(warm):
         orc.lib().orc_fill32(g._h, out, R, np.float32(0.0), np.float32(1.0))
+    done = 0
     t0 = time.perf_counter()
-    for _ in range(steps):
+    while done < steps and (done == 0 or time.perf_counter() - t0 < args.reference_budget_s):
         orc.lib().orc_fill32(g._h, out, R, np.float32(0.0), np.float32(1.0))
+        done += 1
     dt = time.perf_counter() - t0
-    value = steps * R / dt
-    sample = f"{steps} full oracle passes of the workload (creation excluded), 1 thread"
+    value = done * R / dt
+    sample = (f"{done} of {steps} steps, each one full oracle pass of the workload "
+              f"({dt:.1f} s, budget {args.reference_budget_s:.0f} s; creation excluded), 1 thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * dt / steps,
+        "steps": done, "warmup": warm, "ms_per_step": 1e3 * dt / done,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded generator state; no dataset)",
         "config": {"workload": WORKLOAD, "n": N_SUB, "N": N_LEN, "frac": FRAC,
@@ -467,6 +473,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-passes", type=int, default=50)
+    ap.add_argument("--reference-budget-s", type=float, default=90.0,
+                    help="--impl reference: time budget of the timed oracle steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--batched", action="store_true",
