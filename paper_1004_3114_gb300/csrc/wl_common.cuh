@@ -407,8 +407,9 @@ __device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, double 
     __shared__ int32_t s_flag[2];
     volatile WlDevState *vs = st;
     const int warp = threadIdx.x >> 5;
+    // The caller's last-CTA ticket (acquire by thread 0, then a CTA barrier)
+    // already orders every other CTA's writes before these reads.
     if ((threadIdx.x & 31) == 0 && warp < 3) {
-        __threadfence();
         if (warp < 2) {
             uint64_t lo, hi;
             wl_acc_read(st, lo, hi);
@@ -456,11 +457,11 @@ __device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, double 
         st->S_prev = s_S;
         st->have_prev = 1;
         st->status = vs->status | s_flag[0] | s_flag[1];
+        // the next pass reads these after this grid completes: no fence
         st->acc0 = 0;
         st->acc1 = 0;
         st->acc2 = 0;
         st->acc_bad = 0;
-        __threadfence();
         st->tile_ctr = 0;
         st->ticket = 0;
     }

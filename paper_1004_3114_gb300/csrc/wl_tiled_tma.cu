@@ -40,7 +40,7 @@
 #define TM_CONS_THREADS (TM_CONS_WARPS * 32)
 #define TM_PROD_WARPS 4          /* one warp issues a bulk copy only every ~80 cycles */
 #define TM_THREADS (TM_CONS_THREADS + 32 * TM_PROD_WARPS)
-#define TM_STAGES 4
+#define TM_STAGES 3
 #define TM_ETARGET 2880          /* lane-times per tile: L * T <= this (T = 64 at L = 45) */
 #define TM_LMAX 45
 #define TM_MAXSPANS 32           /* sum_i 45 / alpha_i <= 15 + 9 + 5 + 3 */
