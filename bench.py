@@ -144,6 +144,71 @@ def cpu_baseline(passes: int):
     return passes * R / dt, dt
 
 
+def oracle_threads(jobs, threads=None):
+    """Run `jobs` (callables that each drive their own oracle generators) on a
+    pool of host threads -- the oracle's C calls release the GIL -- and return
+    (seconds, threads used)."""
+    from concurrent.futures import ThreadPoolExecutor
+    threads = threads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        for f in [ex.submit(j) for j in jobs]:
+            f.result()
+    return time.perf_counter() - t0, threads
+
+
+def batched_cpu_baseline(Ns, seeds, passes: int = 5, every: int = 8):
+    """The oracle on a sample of the batched workload (every `every`-th
+    generator), one generator per task on all host cores, `passes` passes
+    each (creation excluded)."""
+    import numpy as np
+    from oracle import py_oracle as orc
+    pick = list(range(0, len(Ns), every))
+    gens = [orc.Generator(4, int(Ns[k]), int(seeds[k]), 1.0) for k in pick]
+    Rs = [int(g.stats().R) for g in gens]
+    returned = sum(Rs) * passes
+
+    def job(g, r):
+        def run():
+            out = np.empty(r, dtype=np.float32)
+            for _ in range(passes):
+                orc.lib().orc_fill32(g._h, out, r, np.float32(0.0), np.float32(1.0))
+        return run
+    dt, threads = oracle_threads([job(g, r) for g, r in zip(gens, Rs)])
+    for g in gens:
+        g.close()
+    return {"value": returned / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(gens)} of {len(Ns)} generators (one in {every}), {passes} passes each, "
+                      f"one generator per task on {threads} threads ({dt:.1f} s, creation excluded)"}
+
+
+def serve_cpu_baseline(Ns, seeds, tr, n_requests: int = 100):
+    """The oracle serving the first `n_requests` requests of the trace: each
+    client's requests in arrival order, clients spread over all host cores
+    (creation of the clients' generators excluded)."""
+    import numpy as np
+    from oracle import py_oracle as orc
+    by_client = {}
+    for k in range(min(n_requests, len(tr["count"]))):
+        by_client.setdefault(int(tr["client"][k]), []).append(k)
+    gens = {c: orc.Generator(4, int(Ns[c]), int(seeds[c]), 1 / 3) for c in by_client}
+    values = int(sum(int(tr["count"][k]) for ks in by_client.values() for k in ks))
+
+    def job(c):
+        def run():
+            g = gens[c]
+            for k in by_client[c]:
+                out = np.empty(int(tr["count"][k]), dtype=np.float32)
+                orc.lib().orc_fill32(g._h, out, out.size, np.float32(tr["mu"][k]), np.float32(tr["sigma"][k]))
+        return run
+    dt, threads = oracle_threads([job(c) for c in by_client])
+    for g in gens.values():
+        g.close()
+    return {"value": values / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n_requests} requests ({len(by_client)} clients, {values} values), "
+                      f"one client per task on {threads} threads ({dt:.1f} s, creation excluded)"}
+
+
 def reduce_over_ranks(ms: float, units: int, dist, device) -> tuple[float, int]:
     """Max of the per-rank times and sum of the per-rank units over the
     process group (any backend): the job's time is its slowest rank."""
@@ -410,8 +475,10 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
     seq_value = seq_passes * R_total / (seq_ms * 1e-3)
     for h in handles:
         h.close()
+    cpu = batched_cpu_baseline(Ns, seeds)
     print(json.dumps({
         "metric": "batched generators: N(0,1) variates/s", "value": value, "unit": UNIT,
+        "cpu_baseline": cpu,
         "workload": f"4096 generators, n=4, N log-uniform on [2^8, 2^18]"
                     f"{' (powers of two)' if power_of_two else ''}, seeds 0..4095, frac=1",
         "sum_nu": nu_total, "passes": passes, "runs": runs, "ms": ms,
@@ -451,8 +518,10 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
     peak, kind = hbm_peak()
     bytes_moved = 28 * values        # per returned value at f = 3: 3 x 8 B pool read+write + 4 B out
     srv.close()
+    cpu = serve_cpu_baseline(Ns, seeds, tr)
     print(json.dumps({
         "metric": "served N(mu, sigma^2) variates/s", "value": values / st.elapsed_s, "unit": UNIT,
+        "cpu_baseline": cpu,
         "workload": f"{n_clients} clients, n=4, N log-uniform on [2^10, 2^20], frac=1/3; "
                     f"{n_requests} requests, Poisson {rate:.0f}/s, count log-uniform on [2^10, 2^24], "
                     f"mu~U[-10,10], sigma~U[0.1,10]; budget {budget_gb} GB",
