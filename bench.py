@@ -420,6 +420,123 @@ def precision_study(passes: int = 1000, N: int = 1 << 22, seed: int = 3):
     print(json.dumps(res), flush=True)
 
 
+def small_config_bench(passes: int = 1000, reps: int = 20):
+    """n = 4, N = 256, seed 1, frac = 1 (R = 1023 returned per pass), mu = 0,
+    sigma = 1: one small generator whose pool stays in shared memory, so a
+    fill of `passes` passes is one launch; against the oracle on one core."""
+    import numpy as np
+    import torch
+    from oracle import py_oracle as orc
+    from paper_1004_3114_gb300 import wallace as W
+    n, N, seed = 4, 256, 1
+    stream = torch.cuda.Stream()
+    g = W.Wallace(n, N, seed, 1.0, stream=stream)
+    count = passes * g.R
+    out = torch.empty(count, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            g.fill(out)
+    g.sync()
+    s0 = g.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            g.fill(out)
+        e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    s1 = g.stats()
+    status = g.sync()
+    g.close()
+    nu, R = n * N, int(s1.R)
+    o = orc.Generator(n, N, seed, 1.0)
+    host = np.empty(count, dtype=np.float32)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        orc.lib().orc_fill32(o._h, host, count, np.float32(0.0), np.float32(1.0))
+    cpu_s = time.perf_counter() - t0
+    o.close()
+    total_passes = reps * passes
+    print(json.dumps({
+        "metric": "small-pool generator: N(0,1) variates/s", "value": total_passes * R / (ms * 1e-3),
+        "unit": UNIT, "workload": f"n={n}, N={N}, seed {seed}, frac=1 (R={R}), mu=0, sigma=1; "
+                                  f"{reps} fills of {passes} passes",
+        "us_per_pass": 1e3 * ms / total_passes,
+        "launches_per_fill": (s1.launches - s0.launches) / reps,
+        "bytes_per_pass": {"algorithmic": 8 * nu + 4 * R, "dram": 4 * R,
+                           "note": "the pool stays in shared memory for a whole fill; only the "
+                                   "returned values reach HBM"},
+        "bound": "latency (one CTA, passes in sequence)",
+        "cpu_baseline": {"value": total_passes * R / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"the same {reps} fills ({cpu_s:.2f} s)"},
+        "status": int(status)}), flush=True)
+
+
+def boxmuller_bench(count: int = 1 << 28, reps: int = 20):
+    """The Box-Muller comparison generator (the paper's competitor method):
+    `reps` launches of `count` values each, binary32 (fast) and binary64
+    (exact) arithmetic, beside the Wallace pass at frac = 1/2 and frac = 1 on
+    the default pool (n = 4, N = 2^24)."""
+    import numpy as np
+    import torch
+    from oracle import py_oracle as orc
+    from paper_1004_3114_gb300 import wallace as W
+    stream = torch.cuda.Stream()
+    out = torch.empty(count, dtype=torch.float32, device="cuda")
+    res = {}
+    for name, exact in (("fast", False), ("exact", True)):
+        n_reps = reps if not exact else max(2, reps // 10)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                W.boxmuller_fill(out, 1, 0, 0, 0.0, 1.0, exact, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(n_reps):
+                W.boxmuller_fill(out, 1, 0, k * count, 0.0, 1.0, exact, stream)
+            e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[name] = {"value": n_reps * count / (ms * 1e-3), "ms_per_launch": ms / n_reps}
+    del out
+    peak, kind = hbm_peak()
+    wal = {}
+    for frac in (0.5, 1.0):
+        g = W.Wallace(N_SUB, N_LEN, SEED, frac, stream=stream)
+        o = torch.empty(g.R, dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                g.fill(o)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(300):
+                g.fill(o)
+            e1.record(stream)
+        e1.synchronize()
+        wal[f"frac_{frac:g}"] = 300 * g.R / (e0.elapsed_time(e1) * 1e-3)
+        g.close()
+        del o
+    m = 1 << 22
+    host = np.empty(m, dtype=np.float32)
+    t0 = time.perf_counter()
+    orc.lib().orc_boxmuller_stream(1, 0, 0, m, np.float32(0.0), np.float32(1.0), host)
+    cpu_s = time.perf_counter() - t0
+    fast = res["fast"]
+    print(json.dumps({
+        "metric": "Box-Muller comparison generator: N(0,1) variates/s", "value": fast["value"],
+        "unit": UNIT, "workload": f"{reps} launches of {count} values (binary32 logf/log1pf/sincospif), "
+                                 f"seed 1, stream 0",
+        "roofline": {"bound": "hbm", "achieved": 4 * fast["value"] / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": 4 * fast["value"] / 1e9 / peak, "peak_kind": kind,
+                     "algorithmic_bytes_per_value": 4},
+        "exact_binary64": res["exact"],
+        "wallace_pass_same_box": {"frac_0.5": wal["frac_0.5"], "frac_1": wal["frac_1"],
+                                  "workload": "n=4, N=2^24, seed 7, back-to-back single passes"},
+        "cpu_baseline": {"value": m / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{m} values of the binary64 Box-Muller stream ({cpu_s:.2f} s)"}}),
+          flush=True)
+
+
 def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
                   power_of_two: bool = False):
     """4096 generators, n = 4, N log-uniform on [2^8, 2^18], seeds 0..4095,
@@ -549,6 +666,10 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="4096 uneven generators in one persistent launch vs one handle each")
     ap.add_argument("--pow2", action="store_true", help="with --batched: power-of-two pool sizes")
+    ap.add_argument("--boxmuller", action="store_true",
+                    help="the Box-Muller comparison generator beside the Wallace pass")
+    ap.add_argument("--small", action="store_true",
+                    help="the small correctness configuration (n=4, N=256, frac=1, 1000 passes per fill)")
     ap.add_argument("--serve", action="store_true",
                     help="continuous-batching serving loop (10^4 clients, Poisson arrivals)")
     ap.add_argument("--serve-requests", type=int, default=20_000)
@@ -562,6 +683,12 @@ def main():
         return
     if args.batched:
         batched_bench(power_of_two=args.pow2)
+        return
+    if args.small:
+        small_config_bench()
+        return
+    if args.boxmuller:
+        boxmuller_bench()
         return
     if args.serve:
         serve_bench(n_requests=args.serve_requests, rate=args.serve_rate,

@@ -364,7 +364,7 @@ int wallace_server_stats(wallace_server_t *s, wallace_server_stats_t *out);
  * create a handle (wallace_create allocates the double buffer and state), so
  * here the caller keeps the pool and the per-pass parameters itself, and the
  * pass's scratch (the second pool buffer and the reduction/finaliser block)
- * lives in one fixed array of 4 * WALLACE_STATIC_MAX_VALUES + 512 bytes
+ * lives in one fixed array of 4 * WALLACE_STATIC_MAX_VALUES + 1024 bytes
  * inside the library, present on every device that loads the library until
  * the process exits.  Neither this call nor anything it calls allocates.
  *
@@ -405,6 +405,31 @@ typedef struct {
 int wallace_pass_static(int n, int64_t N, float *pool, const int32_t *alpha, const int64_t *gamma,
                         float c32, float *out, int64_t out_count, float mu, float sigma,
                         wallace_pass_result_t *result, void *cuda_stream);
+
+/*
+ * wallace_boxmuller_fill -- the Box-Muller method as a stand-alone generator,
+ * the comparison point of the paper (its abstract and Section 1 measure RANN4
+ * against the Box-Muller and Polar methods).  Writes values
+ * [offset, offset + count) of the Box-Muller stream of (seed, stream_id):
+ * pair p is formed from uniforms 2p and 2p+1 of the generator's uniform
+ * source (u1 = (U+1) 2^-32, u2 = U' 2^-32; r = sqrt(-2 ln u1),
+ * y = (r cos 2 pi u2, r sin 2 pi u2)), each mapped to mu + sigma*y (binary32
+ * multiply, then add).  Values [0, n*N) of a stream are the initial pool of
+ * the Wallace generator with the same seed and stream id (Sections 5 and 8).
+ *   seed, stream_id as for wallace_create_ex
+ *   offset      first value index, >= 0
+ *   out         device, count floats, written in order
+ *   count       >= 0
+ *   exact       1: binary64 arithmetic with the library's own series, bit-
+ *               identical to the initial pool; 0: binary32 with CUDA's logf,
+ *               log1pf and sincospif (within a few binary32 ulps of exact)
+ *   cuda_stream stream to run on (NULL: legacy default stream)
+ * Asynchronous on cuda_stream; no state, no allocation.  Returns WALLACE_OK,
+ * WALLACE_EINVAL (negative offset or count, NULL out, offset too large) or
+ * WALLACE_ECUDA (launch failure).
+ */
+int wallace_boxmuller_fill(uint32_t seed, uint32_t stream_id, int64_t offset, float *out,
+                           int64_t count, float mu, float sigma, int exact, void *cuda_stream);
 
 /* wallace_strerror -- static text for a status code (lowest set bit). */
 const char *wallace_strerror(int code);

@@ -70,6 +70,8 @@ def lib():
             "orc_sincos_quarter": (None, [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "orc_sincos_2pi": (None, [C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "orc_box_muller": (None, [C.c_uint32, C.c_uint32, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+            "orc_boxmuller_stream": (None, [C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, C.c_float,
+                                            C.c_float, f32p]),
             "orc_draw_params": (None, [C.c_int, C.c_int64, C.POINTER(C.c_uint64), i32p, i64p]),
             "orc_transform32": (None, [C.c_int, f32p, C.c_float, f32p]),
             "orc_transform64": (None, [C.c_int, f64p, C.c_double, f64p]),
@@ -137,6 +139,13 @@ def box_muller(u1: int, u2: int) -> tuple[np.float32, np.float32]:
     a, b = C.c_float(), C.c_float()
     lib().orc_box_muller(u1, u2, C.byref(a), C.byref(b))
     return np.float32(a.value), np.float32(b.value)
+
+
+def boxmuller_stream(seed: int, stream: int, offset: int, count: int, mu: float = 0.0,
+                     sigma: float = 1.0) -> np.ndarray:
+    out = np.empty(count, dtype=np.float32)
+    lib().orc_boxmuller_stream(seed, stream, offset, count, np.float32(mu), np.float32(sigma), out)
+    return out
 
 
 def draw_params(n: int, N: int, state: int) -> tuple[np.ndarray, np.ndarray, int]:

@@ -153,6 +153,34 @@ void orc_box_muller(uint32_t u1, uint32_t u2, float *a, float *b)
     *b = (float)(r * s);
 }
 
+/* The Box-Muller method as a generator in its own right: the comparison
+ * method of the paper's abstract and Section 1.  Values [offset, offset +
+ * count) of the stream of pairs formed from consecutive uniforms of the
+ * (seed, stream) source -- the pairs of the initial pool (Sections 5 and 8)
+ * -- each mapped to mu + sigma*y (binary32 multiply, then add). */
+void orc_boxmuller_stream(uint32_t seed, uint32_t stream, int64_t offset, int64_t count,
+                          float mu, float sigma, float *out)
+{
+    uint64_t s = orc_seed_state(seed, stream);
+    int64_t p0 = offset / 2;
+    for (int64_t k = 0; k < 2 * p0; k++)
+        (void)orc_lcg_next(&s);
+    int64_t v = 2 * p0; /* value index of the next pair's first value */
+    int64_t done = 0;
+    while (done < count) {
+        uint32_t u1 = orc_lcg_next(&s);
+        uint32_t u2 = orc_lcg_next(&s);
+        float y[2];
+        orc_box_muller(u1, u2, &y[0], &y[1]);
+        for (int h = 0; h < 2; h++, v++) {
+            if (v >= offset && done < count) {
+                float t = sigma * y[h];
+                out[done++] = mu + t;
+            }
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ *
  * Per-pass parameters (Eq. 1 and Eq. 2; Sections 3, 7 and 8).  The paper asks
  * for strides that are distinct, greater than one, odd, and coprime to N, and

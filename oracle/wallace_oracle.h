@@ -63,6 +63,8 @@ double orc_log_w(uint64_t w);                      /* ln(w * 2^-32), 1 <= w <= 2
 void orc_sincos_quarter(double g, double *s, double *c); /* sin, cos of g*pi/2, 0<=g<=1/2 */
 void orc_sincos_2pi(uint32_t u, double *s, double *c);   /* sin, cos of 2*pi*u*2^-32      */
 void orc_box_muller(uint32_t u1, uint32_t u2, float *a, float *b);
+void orc_boxmuller_stream(uint32_t seed, uint32_t stream, int64_t offset, int64_t count,
+                          float mu, float sigma, float *out);
 void orc_draw_params(int n, int64_t N, uint64_t *state, int32_t *alpha, int64_t *gamma);
 void orc_transform32(int n, const float *g, float c, float *y);
 void orc_transform64(int n, const double *g, double c, double *y);

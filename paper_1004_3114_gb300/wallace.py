@@ -119,6 +119,8 @@ _SIGS = {
     "wallace_pass_static": (C.c_int, [C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_float, C.c_void_p, C.c_int64, C.c_float, C.c_float,
                                       C.POINTER(PassResult), C.c_void_p]),
+    "wallace_boxmuller_fill": (C.c_int, [C.c_uint32, C.c_uint32, C.c_int64, C.c_void_p, C.c_int64,
+                                         C.c_float, C.c_float, C.c_int, C.c_void_p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -312,6 +314,15 @@ def pass_static(n: int, N: int, pool, alpha, gamma, c32: float, out=None, out_co
                                   C.c_void_p(out.data_ptr() if out is not None else 0), out_count,
                                   mu, sigma, C.byref(res), _stream_ptr(stream))
     return int(rc), res
+
+
+def boxmuller_fill(out, seed: int, stream_id: int = 0, offset: int = 0, mu: float = 0.0,
+                   sigma: float = 1.0, exact: bool = False, stream=None) -> None:
+    """wallace_boxmuller_fill: values [offset, offset + out.numel()) of the
+    Box-Muller stream of (seed, stream_id) into a CUDA float32 tensor."""
+    _check(_lib.wallace_boxmuller_fill(seed, stream_id, offset, C.c_void_p(out.data_ptr()),
+                                       out.numel(), mu, sigma, 1 if exact else 0, _stream_ptr(stream)),
+           "wallace_boxmuller_fill")
 
 
 class WallaceError(RuntimeError):

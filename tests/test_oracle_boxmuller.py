@@ -96,3 +96,51 @@ def test_initial_pool_uses_consecutive_uniform_pairs(orc):
     for p in range(128):
         a, b = orc.box_muller(int(u[2 * p]), int(u[2 * p + 1]))
         assert pool[2 * p] == a and pool[2 * p + 1] == b
+
+
+# ---- the Box-Muller method as a stand-alone generator (the paper's comparison
+# method, abstract and Section 1) ----------------------------------------------
+
+def test_boxmuller_stream_is_the_initial_pool(orc):
+    """Values [0, nN) of a stream are the initial pool of the Wallace generator
+    with the same seed (Sections 5 and 8), itself pinned above to libm."""
+    for n, N, seed in [(4, 256, 1), (8, 1001, 9), (4, 4097, 3)]:
+        g = orc.Generator(n, N, seed, 1.0)
+        assert np.array_equal(orc.boxmuller_stream(seed, 0, 0, n * N).view(np.uint32),
+                              g.pool32().view(np.uint32))
+
+
+def test_boxmuller_stream_pairs_follow_the_uniforms(orc):
+    """Pair p uses uniforms 2p and 2p+1 of the (seed, stream) source in order."""
+    u, _ = orc.lcg_stream(orc.seed_state(21, 5), 64)
+    ref = []
+    for p in range(32):
+        a, b = orc.box_muller(int(u[2 * p]), int(u[2 * p + 1]))
+        ref += [a, b]
+    got = orc.boxmuller_stream(21, 5, 0, 64)
+    assert np.array_equal(got.view(np.uint32), np.array(ref, dtype=np.float32).view(np.uint32))
+
+
+@pytest.mark.parametrize("offset,count", [(0, 1), (1, 1), (1, 2), (7, 10), (100, 33), (2, 0)])
+def test_boxmuller_stream_windows(orc, offset, count):
+    """A window of the stream is the same slice of a longer call."""
+    full = orc.boxmuller_stream(4, 2, 0, 200)
+    got = orc.boxmuller_stream(4, 2, offset, count)
+    assert np.array_equal(got.view(np.uint32), full[offset:offset + count].view(np.uint32))
+
+
+def test_boxmuller_stream_affine_map(orc):
+    """mu + sigma*y is a binary32 multiply then a binary32 add."""
+    y = orc.boxmuller_stream(8, 0, 0, 1000)
+    mu, sigma = np.float32(-3.25), np.float32(0.7)
+    got = orc.boxmuller_stream(8, 0, 0, 1000, float(mu), float(sigma))
+    ref = (mu + (sigma * y).astype(np.float32)).astype(np.float32)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+def test_boxmuller_stream_moments(orc):
+    y = orc.boxmuller_stream(12345, 0, 0, 1 << 20).astype(np.float64)
+    m = y.size
+    assert abs(y.mean()) < 5 / math.sqrt(m)
+    assert abs(y.var() - 1.0) < 5 * math.sqrt(2 / m)
+    assert abs((y ** 4).mean() - 3.0) < 5 * math.sqrt(96 / m)
