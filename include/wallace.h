@@ -55,6 +55,12 @@ typedef struct wallace wallace_t;
 /* pool precision */
 #define WALLACE_FP32      0   /* binary32 pool; exact integer sum of squares, binary64 scale */
 #define WALLACE_FP64POOL  1   /* binary64 pool (reference mode for precision studies)        */
+/* mode flag, OR-ed into either precision: the chi-squared sample of Section 4
+ * by Wilson and Hilferty's cube (Abramowitz and Stegun 26.4.17),
+ * S = nu (1 - a + x sqrt(a))^3 with a = 2/(9 nu), instead of Eq. 3's
+ * (x + sqrt(2 nu - 1))^2 / 2 -- closer to chi-squared for small pools.  A
+ * sample that is not positive marks the pool corrupt (c stays 1). */
+#define WALLACE_CHI_WH    0x100
 
 /* pass kernel selection (wallace_set_variant) */
 #define WALLACE_VARIANT_AUTO    0  /* pick by pool size                                 */
@@ -111,7 +117,7 @@ int wallace_create(int n, int64_t N, uint32_t seed, double frac, wallace_t **out
  * wallace_create_ex -- as wallace_create, plus:
  *   stream_id  appended to the seed (Section 8: DP_VRANU4 appends the
  *              processor number so that processors get different sequences)
- *   mode       WALLACE_FP32 or WALLACE_FP64POOL
+ *   mode       WALLACE_FP32 or WALLACE_FP64POOL, optionally OR WALLACE_CHI_WH
  *   cuda_stream  cudaStream_t to run on (NULL: legacy default stream)
  */
 int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, double frac,

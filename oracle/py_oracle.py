@@ -20,6 +20,7 @@ HDR = os.path.join(HERE, "wallace_oracle.h")
 LIB = os.path.join(HERE, "liborc.so")
 
 FP32, FP64 = 0, 1
+CHI_WH = 0x100   # mode flag: Wilson-Hilferty chi-squared sample
 OK, EINVAL, ENOMEM, ECORRUPT = 0, 1, 2, 4
 
 CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
@@ -219,7 +220,8 @@ class Generator:
 
     def __init__(self, n: int, N: int, seed: int, frac: float = 1.0,
                  mode: int = FP32, stream: int = 0):
-        self.n, self.N, self.mode = n, N, mode
+        self.n, self.N, self.mode = n, N, mode & ~CHI_WH
+        self.chi_wh = bool(mode & CHI_WH)
         self.nu = n * N
         self._h = lib().orc_create(n, N, seed, stream, frac, mode)
         if not self._h:

@@ -402,7 +402,7 @@ int64_t orc_returned_count(int64_t nu, double frac)
  * A whole generator.
  * ------------------------------------------------------------------------ */
 struct orc_gen {
-    int n, mode;
+    int n, mode, chi;
     int64_t N, nu, R;
     double frac;
     float *p32[2];
@@ -418,7 +418,13 @@ struct orc_gen {
  * gives a chi-squared sample S = (x + sqrt(2 nu - 1))^2 / 2; the next pass
  * scales A by c = sqrt(S / q) so that the next pool's sum of squares is S.
  * The ratio q_k / S_{k-1} - 1 is the drift the monitor watches; beyond 1e-3
- * the work area is taken to be overwritten. */
+ * the work area is taken to be overwritten.
+ *
+ * With ORC_CHI_WH the sample is Wilson and Hilferty's cube instead, one of
+ * the more accurate approximations Section 4 points to (Abramowitz and
+ * Stegun 26.4.17): with a = 2/(9 nu), S = nu (1 - a + x sqrt(a))^3.  A
+ * sample that is not positive (x below -(1 - a)/sqrt(a)) marks the pool
+ * corrupt and keeps c = 1, as a non-positive q does. */
 static void orc_finalise(orc_gen *g)
 {
     uint64_t lo, hi;
@@ -435,11 +441,21 @@ static void orc_finalise(orc_gen *g)
         x = g->p64[g->cur][g->nu - 1];
         q = (double)hi + (double)lo * (1.0 / 18446744073709551616.0);
     }
-    double r = sqrt(2.0 * (double)g->nu - 1.0);
-    double xr = x + r;
-    double S = (xr * xr) * 0.5;
+    double S;
+    int bad_s = 0;
+    if (!g->chi) {
+        double r = sqrt(2.0 * (double)g->nu - 1.0);
+        double xr = x + r;
+        S = (xr * xr) * 0.5;
+    } else {
+        double a = 2.0 / (9.0 * (double)g->nu);
+        double b = sqrt(a);
+        double t = (1.0 - a) + x * b;
+        S = ((t * t) * t) * (double)g->nu;
+        bad_s = !(S > 0.0);
+    }
     double c = 1.0;
-    if (bad || !(q > 0.0)) {
+    if (bad || bad_s || !(q > 0.0)) {
         g->st.status |= ORC_ECORRUPT;
     } else {
         c = sqrt(S / q);
@@ -466,6 +482,8 @@ orc_gen *orc_create(int n, int64_t N, uint32_t seed, uint32_t stream, double fra
 {
     if ((n != 4 && n != 8) || N < 4 || (int64_t)n * N > ((int64_t)1 << 30))
         return NULL;
+    int chi = (mode & ORC_CHI_WH) != 0;
+    mode &= ~ORC_CHI_WH;
     if (!(frac > 0.0 && frac <= 1.0) || (mode != ORC_FP32 && mode != ORC_FP64))
         return NULL;
     int64_t nu = (int64_t)n * N;
@@ -476,6 +494,7 @@ orc_gen *orc_create(int n, int64_t N, uint32_t seed, uint32_t stream, double fra
     if (!g)
         return NULL;
     g->n = n;
+    g->chi = chi;
     g->N = N;
     g->nu = nu;
     g->R = R;

@@ -27,6 +27,8 @@ extern "C" {
 #endif
 
 enum { ORC_FP32 = 0, ORC_FP64 = 1 };
+/* mode flag: Wilson-Hilferty chi-squared sample instead of Eq. 3's */
+enum { ORC_CHI_WH = 0x100 };
 
 enum {
     ORC_OK = 0,

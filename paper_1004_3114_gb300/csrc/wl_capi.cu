@@ -245,6 +245,8 @@ int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, doubl
     *out = nullptr;
     if ((n != 4 && n != 8) || N < 4 || (int64_t)n * N > ((int64_t)1 << 30))
         return WALLACE_EINVAL;
+    const int chi = (mode & WALLACE_CHI_WH) ? 1 : 0;
+    mode &= ~WALLACE_CHI_WH;
     if (!(frac > 0.0 && frac <= 1.0) || (mode != WALLACE_FP32 && mode != WALLACE_FP64POOL))
         return WALLACE_EINVAL;
     const int64_t nu = (int64_t)n * N;
@@ -292,7 +294,7 @@ int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, doubl
         e = cudaMemsetAsync(h->st, 0, sizeof(WlDevState), h->stream);
     if (e == cudaSuccess)
         e = wl_launch_init(h->pool[0], mode == WALLACE_FP64POOL, n, N, h->Np, seed, stream_id,
-                           h->st, h->sm_count, h->stream);
+                           h->st, h->sm_count, h->stream, chi);
     if (e != cudaSuccess) {
         wallace_destroy(h);
         return WALLACE_ECUDA;

@@ -59,7 +59,7 @@ struct WlDevState {
     int32_t have_prev;
     int32_t status;         // sticky WL_* bits
     int32_t bad;
-    int32_t pad_;
+    int32_t chi;            // 0: Eq. 3's sample; 1: Wilson-Hilferty's (set at creation)
     int64_t passes;
 };
 
@@ -329,6 +329,25 @@ __device__ inline void wl_advance_strides(WlDevState *st, int n, int64_t N, uint
 }
 
 // ---- end of pass: chi-squared rescale (Eq. 3) and drift monitor ------------
+// The chi-squared sample S from the withheld value x (Section 4).  chi = 0:
+// Eq. 3, S = (x + sqrt(2 nu - 1))^2 / 2.  chi = 1: Wilson and Hilferty's cube
+// (Abramowitz and Stegun 26.4.17), a = 2/(9 nu), S = nu (1 - a + x sqrt(a))^3,
+// one of the more accurate approximations the section points to; a sample
+// that is not positive marks the pool corrupt (c stays 1).
+__device__ __forceinline__ double wl_chi_sample(int chi, int64_t nu, double x)
+{
+    const double dnu = (double)nu;
+    if (!chi) {
+        const double r = __dsqrt_rn(__dsub_rn(__dmul_rn(2.0, dnu), 1.0));
+        const double xr = __dadd_rn(x, r);
+        return __dmul_rn(__dmul_rn(xr, xr), 0.5);
+    }
+    const double a = __ddiv_rn(2.0, __dmul_rn(9.0, dnu));
+    const double b = __dsqrt_rn(a);
+    const double t = __dadd_rn(__dsub_rn(1.0, a), __dmul_rn(x, b));
+    return __dmul_rn(__dmul_rn(__dmul_rn(t, t), t), dnu);
+}
+
 // One thread.  x is the withheld last value of the new pool; with
 // r = sqrt(2 nu - 1), S = (x + r)^2 / 2; the next pass scales A by
 // c = sqrt(S / q).  q / S_prev - 1 beyond 1e-3 means the pool was overwritten
@@ -349,12 +368,10 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
     } else {
         q = __dadd_rn(__ull2double_rn(hi), __dmul_rn(__ull2double_rn(lo), 1.0 / 18446744073709551616.0));
     }
-    double r = __dsqrt_rn(__dsub_rn(__dmul_rn(2.0, (double)nu), 1.0));
-    double xr = __dadd_rn(x, r);
-    double S = __dmul_rn(__dmul_rn(xr, xr), 0.5);
+    const double S = wl_chi_sample(st->chi, nu, x);
     double c = 1.0;
     int32_t status = st->status;
-    if (bad || !(q > 0.0))
+    if (bad || (st->chi && !(S > 0.0)) || !(q > 0.0))
         status |= WL_ECORRUPT;
     else
         c = __dsqrt_rn(__ddiv_rn(S, q));
@@ -401,7 +418,8 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
 // pass's parameters -- so their binary64 divisions and square roots and the
 // parameter draw overlap.  rnu = sqrt(2 nu - 1), correctly rounded; xp points
 // at the withheld last value of the new pool.  Every thread of the CTA calls.
-__device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, double rnu, const float *xp)
+__device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, int64_t nu, double rnu,
+                                       const float *xp)
 {
     __shared__ double s_S, s_c;
     __shared__ int32_t s_flag[2];
@@ -416,11 +434,17 @@ __device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, double 
             const double q = __dmul_rn(__ull2double_rn(lo), 1.0 / 4294967296.0);
             if (warp == 0) {
                 const uint32_t bad = (vs->acc_bad != 0u || hi != 0) ? 1u : 0u;
-                const double xr = __dadd_rn((double)__ldcg(xp), rnu);
-                const double S = __dmul_rn(__dmul_rn(xr, xr), 0.5);
+                const int chi = vs->chi;
+                double S;
+                if (!chi) {
+                    const double xr = __dadd_rn((double)__ldcg(xp), rnu);
+                    S = __dmul_rn(__dmul_rn(xr, xr), 0.5);
+                } else {
+                    S = wl_chi_sample(1, nu, (double)__ldcg(xp));
+                }
                 double c = 1.0;
                 int32_t f = 0;
-                if (bad || !(q > 0.0))
+                if (bad || (chi && !(S > 0.0)) || !(q > 0.0))
                     f = WL_ECORRUPT;
                 else
                     c = __dsqrt_rn(__ddiv_rn(S, q));

@@ -13,7 +13,7 @@ using wl_bm::box_muller;
 template <typename T>
 __global__ void __launch_bounds__(256) init_kernel(T *pool, int n, int64_t N, int64_t Np,
                                                    int64_t nu, uint32_t seed, uint32_t stream,
-                                                   WlDevState *st)
+                                                   WlDevState *st, int chi)
 {
     __shared__ uint64_t red[3 * 8];
     const uint64_t s0 = wl_seed_mix(seed, stream);
@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(256) init_kernel(T *pool, int n, int64_t N, in
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st) && threadIdx.x == 0) {
         st->lcg = wl_lcg_jump(s0, (uint64_t)nu);
+        st->chi = chi;
         double x = (double)__ldcg(&pool[wl_phys(nu - 1, N, Np)]);
         wl_finalise(st, n, N, nu, x, sizeof(T) == 8, false);
     }
@@ -58,7 +59,8 @@ __global__ void __launch_bounds__(256) init_kernel(T *pool, int n, int64_t N, in
 } // namespace
 
 cudaError_t wl_launch_init(void *pool, int fp64, int n, int64_t N, int64_t Np, uint32_t seed,
-                           uint32_t stream_id, WlDevState *st, int sm_count, cudaStream_t stream)
+                           uint32_t stream_id, WlDevState *st, int sm_count, cudaStream_t stream,
+                           int chi)
 {
     int64_t nu = (int64_t)n * N;
     int64_t npairs = nu / 2;
@@ -67,9 +69,9 @@ cudaError_t wl_launch_init(void *pool, int fp64, int n, int64_t N, int64_t Np, u
     int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
     if (fp64)
         init_kernel<double><<<grid, 256, 0, stream>>>((double *)pool, n, N, Np, nu, seed,
-                                                      stream_id, st);
+                                                      stream_id, st, chi);
     else
         init_kernel<float><<<grid, 256, 0, stream>>>((float *)pool, n, N, Np, nu, seed,
-                                                     stream_id, st);
+                                                     stream_id, st, chi);
     return cudaGetLastError();
 }

@@ -22,8 +22,10 @@ struct WlPassArgs {
     int64_t pass;   // passes completed before this one (selects its strides' slot)
 };
 
+// chi: the chi-squared sample the generator uses (0: Eq. 3, 1: Wilson-Hilferty)
 cudaError_t wl_launch_init(void *pool, int fp64, int n, int64_t N, int64_t Np, uint32_t seed,
-                           uint32_t stream_id, WlDevState *st, int sm_count, cudaStream_t stream);
+                           uint32_t stream_id, WlDevState *st, int sm_count, cudaStream_t stream,
+                           int chi = 0);
 
 // direct strided gather from global memory, any n, N, either precision
 cudaError_t wl_launch_gather(const WlPassArgs &a, int fp64, int sm_count, cudaStream_t stream);

@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
 
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st))
-        wl_finalise_cta(st, 4, N, rnu, &dst[wl_phys(a.nu - 1, N, Np)]);
+        wl_finalise_cta(st, 4, N, a.nu, rnu, &dst[wl_phys(a.nu - 1, N, Np)]);
 }
 
 bool g_tma_configured = false;

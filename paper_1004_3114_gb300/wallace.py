@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "wallace.h")
 
 OK, EINVAL, ENOMEM, ECORRUPT, ECUDA, ETIMEOUT, ESTATE = 0, 1, 2, 4, 8, 16, 32
 FP32, FP64POOL = 0, 1
+CHI_WH = 0x100   # mode flag: Wilson-Hilferty chi-squared sample
 VARIANT_AUTO, VARIANT_GATHER, VARIANT_TILED, VARIANT_FUSED = 0, 1, 2, 3
 VARIANT_TILED_ASYNC, VARIANT_TILED_TMA = 4, 5
 
@@ -349,7 +350,7 @@ class Wallace:
 
     def __init__(self, n: int, N: int, seed: int, frac: float = 1.0, *, stream_id: int = 0,
                  mode: int = FP32, stream=None):
-        self.n, self.N, self.mode = n, N, mode
+        self.n, self.N, self.mode = n, N, mode & ~CHI_WH
         self.nu = n * N
         h = _h()
         rc = _lib.wallace_create_ex(n, N, seed, stream_id, frac, mode, _stream_ptr(stream),

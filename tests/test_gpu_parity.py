@@ -248,3 +248,25 @@ def test_full_size_pool_parity(orc):
     Q, bad = orc.sumsq32(after)
     assert Q == st.Q and bad == 0
     assert_same(out.cpu().numpy(), (np.float32(0) + np.float32(1) * after[:g.R]).astype(np.float32))
+
+
+@pytest.mark.parametrize("n,N,variant,mode", [
+    (4, 1 << 17, W.VARIANT_TILED_TMA, W.FP32),
+    (4, 20000, W.VARIANT_TILED_ASYNC, W.FP32),
+    (4, 6000, W.VARIANT_GATHER, W.FP32),
+    (8, 3001, W.VARIANT_FUSED, W.FP32),
+    (4, 1024, W.VARIANT_AUTO, W.FP64POOL),
+])
+def test_wilson_hilferty_sample_bit_exact(orc, n, N, variant, mode):
+    """The Wilson-Hilferty chi-squared option (Section 4's more accurate
+    approximations) through every finaliser: CTA-parallel (TMA pass), last-CTA
+    (tiled, gather) and in-kernel (fused), and the binary64 pool."""
+    g = W.Wallace(n, N, 13, 0.5, mode=mode | W.CHI_WH)
+    g.set_variant(variant)
+    o = orc.Generator(n, N, 13, 0.5, mode=(orc.FP32 if mode == W.FP32 else orc.FP64) | orc.CHI_WH)
+    assert_stats_equal(g, o, "initial pool")
+    for k in range(5):
+        got = fill_dev(g, g.R)
+        ref = o.fill(g.R)
+        assert_same(got, ref, f"pass {k + 1} output")
+        assert_stats_equal(g, o, f"pass {k + 1}")
