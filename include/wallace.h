@@ -166,6 +166,20 @@ int wallace_set_stream(wallace_t *h, void *cuda_stream);
  * FUSED request on a pool too large for shared memory. */
 int wallace_set_variant(wallace_t *h, int variant);
 
+/*
+ * wallace_set_restart -- Section 5 (restarting): refill the pool by
+ * Box-Muller from the uniform source before every pass that follows a
+ * multiple of `interval` passes (counted from creation), and take the
+ * chi-squared sample, scale and drift history afresh from the new pool, as at
+ * creation.  Restart r = 1, 2, ... takes the uniforms at positions
+ * [r 2^40, r 2^40 + n*N) of the generator's sequence, apart from the initial
+ * pool and the per-pass draws, which are unchanged.  The paper suggests a
+ * restart after about 1000 N returned numbers (interval ~ 1000 N / R).  The
+ * refilled pool is not returned.  interval = 0 (the default) never restarts.
+ * Returns WALLACE_OK or WALLACE_EINVAL (NULL handle, interval < 0).
+ */
+int wallace_set_restart(wallace_t *h, int64_t interval);
+
 /* wallace_set_timing -- when on, every pass kernel is bracketed by CUDA
  * events on the handle's stream; the summed time appears in kernel_ms. */
 int wallace_set_timing(wallace_t *h, int on);

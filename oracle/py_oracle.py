@@ -71,6 +71,9 @@ def lib():
             "orc_sincos_quarter": (None, [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "orc_sincos_2pi": (None, [C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "orc_box_muller": (None, [C.c_uint32, C.c_uint32, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+            "orc_lcg_jump": (C.c_uint64, [C.c_uint64, C.c_uint64]),
+            "orc_set_restart": (None, [C.c_void_p, C.c_int64]),
+            "orc_restart_pool": (None, [C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, f32p]),
             "orc_boxmuller_stream": (None, [C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, C.c_float,
                                             C.c_float, f32p]),
             "orc_draw_params": (None, [C.c_int, C.c_int64, C.POINTER(C.c_uint64), i32p, i64p]),
@@ -237,6 +240,9 @@ class Generator:
             self.close()
         except Exception:
             pass
+
+    def set_restart(self, interval: int) -> None:
+        lib().orc_set_restart(self._h, interval)
 
     def pass_(self) -> int:
         return int(lib().orc_pass(self._h))

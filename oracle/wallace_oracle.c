@@ -47,6 +47,25 @@ uint32_t orc_lcg_next(uint64_t *state)
     return (uint32_t)(*state >> 32);
 }
 
+/* The state m steps ahead: the step is the affine map s -> a s + b (mod
+ * 2^64); m steps compose to s -> A s + B, built by binary powering of the map
+ * (F. B. Brown, "Random number generation with arbitrary strides", 1994). */
+uint64_t orc_lcg_jump(uint64_t s, uint64_t m)
+{
+    uint64_t A = 1, B = 0;                          /* accumulated map */
+    uint64_t a = 6364136223846793005ULL, b = 1442695040888963407ULL; /* map for 2^k steps */
+    while (m) {
+        if (m & 1) {
+            A = a * A;
+            B = a * B + b;
+        }
+        b = a * b + b;
+        a = a * a;
+        m >>= 1;
+    }
+    return A * s + B;
+}
+
 /* ------------------------------------------------------------------------ *
  * Elementary functions for the initial Box-Muller fill (Section 5 refills the
  * pool with Box-Muller; Section 8 initialises from the uniform generator).
@@ -403,6 +422,8 @@ int64_t orc_returned_count(int64_t nu, double frac)
  * ------------------------------------------------------------------------ */
 struct orc_gen {
     int n, mode, chi;
+    uint32_t seed, stream;
+    int64_t restart; /* refill interval in passes (0: never) */
     int64_t N, nu, R;
     double frac;
     float *p32[2];
@@ -495,6 +516,8 @@ orc_gen *orc_create(int n, int64_t N, uint32_t seed, uint32_t stream, double fra
         return NULL;
     g->n = n;
     g->chi = chi;
+    g->seed = seed;
+    g->stream = stream;
     g->N = N;
     g->nu = nu;
     g->R = R;
@@ -533,8 +556,45 @@ orc_gen *orc_create(int n, int64_t N, uint32_t seed, uint32_t stream, double fra
     return g;
 }
 
+/* Section 5 (Restarting): the pool is refilled by Box-Muller from the
+ * uniform source and the chi-squared sample, scale and drift history are
+ * taken afresh from it, as at creation.  Reading: restart r = 1, 2, ... takes
+ * the uniforms at positions [r 2^40, r 2^40 + nu) of the generator's LCG
+ * sequence (its seed state jumped r 2^40 steps): apart from the initial pool
+ * (positions [0, nu)) and the per-pass draws (2n a pass from position nu), so
+ * no uniform serves twice, and the draws of later passes are unchanged.  The
+ * refilled pool is not returned. */
+void orc_restart_pool(uint32_t seed, uint32_t stream, int64_t r, int64_t nu, float *pool)
+{
+    uint64_t s = orc_lcg_jump(orc_seed_state(seed, stream), (uint64_t)r << 40);
+    for (int64_t q = 0; q < nu / 2; q++) {
+        uint32_t u1 = orc_lcg_next(&s);
+        uint32_t u2 = orc_lcg_next(&s);
+        orc_box_muller(u1, u2, &pool[2 * q], &pool[2 * q + 1]);
+    }
+}
+
+static void orc_restart(orc_gen *g, int64_t r)
+{
+    float *p = g->p32[g->cur];
+    orc_restart_pool(g->seed, g->stream, r, g->nu, p);
+    if (g->mode == ORC_FP64)
+        for (int64_t q = 0; q < g->nu; q++)
+            g->p64[g->cur][q] = (double)p[q];
+    g->have_prev = 0;
+    orc_finalise(g);
+}
+
+void orc_set_restart(orc_gen *g, int64_t interval)
+{
+    g->restart = interval > 0 ? interval : 0;
+}
+
 int orc_pass(orc_gen *g)
 {
+    /* after every `restart` passes, refill before the next pass */
+    if (g->restart > 0 && g->st.passes > 0 && g->st.passes % g->restart == 0)
+        orc_restart(g, g->st.passes / g->restart);
     orc_draw_params(g->n, g->N, &g->lcg, g->st.alpha, g->st.gamma);
     int src = g->cur, dst = 1 - g->cur;
     if (g->mode == ORC_FP32)

@@ -65,6 +65,7 @@ double orc_log_w(uint64_t w);                      /* ln(w * 2^-32), 1 <= w <= 2
 void orc_sincos_quarter(double g, double *s, double *c); /* sin, cos of g*pi/2, 0<=g<=1/2 */
 void orc_sincos_2pi(uint32_t u, double *s, double *c);   /* sin, cos of 2*pi*u*2^-32      */
 void orc_box_muller(uint32_t u1, uint32_t u2, float *a, float *b);
+uint64_t orc_lcg_jump(uint64_t state, uint64_t steps);
 void orc_boxmuller_stream(uint32_t seed, uint32_t stream, int64_t offset, int64_t count,
                           float mu, float sigma, float *out);
 void orc_draw_params(int n, int64_t N, uint64_t *state, int32_t *alpha, int64_t *gamma);
@@ -83,6 +84,12 @@ int64_t orc_returned_count(int64_t nu, double frac);
 
 /* ---- a whole generator ------------------------------------------------- */
 orc_gen *orc_create(int n, int64_t N, uint32_t seed, uint32_t stream, double frac, int mode);
+/* refill the pool (Section 5, restarting) before every pass that follows a
+ * multiple of `interval` passes; 0 turns it off (the default) */
+void orc_set_restart(orc_gen *g, int64_t interval);
+/* the pool of restart r (nu values): Box-Muller pairs from uniforms
+ * [r 2^40, r 2^40 + nu) of the (seed, stream) sequence */
+void orc_restart_pool(uint32_t seed, uint32_t stream, int64_t r, int64_t nu, float *pool);
 int orc_pass(orc_gen *g);
 int orc_fill32(orc_gen *g, float *out, int64_t count, float mu, float sigma);
 int orc_fill64(orc_gen *g, double *out, int64_t count, double mu, double sigma);

@@ -23,6 +23,9 @@ struct wallace {
     void *pool[2] = {nullptr, nullptr};
     int cur = 0;
     int64_t pass_index = 0;   // passes launched (selects a pass's strides slot)
+    uint32_t seed = 0, stream_id = 0;
+    int64_t restart = 0;          // refill interval in passes (0: never)
+    int64_t restarted_at = 0;     // pass index of the last refill
     WlDevState *st = nullptr;
     int64_t cursor = 0;
     int status = 0;
@@ -115,11 +118,29 @@ int pick_variant(const wallace_t *h)
 
 // One pass on the device.  Values q in [w0, w1) of the new pool are also
 // written, mapped, to out[q - w0].
+// Section 5 (restarting): before the pass that follows every `restart`
+// passes, refill the current pool by Box-Muller (restart r takes uniforms
+// [r 2^40, r 2^40 + nu) of the generator's sequence) and take the scale and
+// drift history afresh from it.
+cudaError_t maybe_restart(wallace_t *h)
+{
+    if (h->restart <= 0 || h->pass_index == 0 || h->pass_index % h->restart != 0 ||
+        h->restarted_at == h->pass_index)
+        return cudaSuccess;
+    h->restarted_at = h->pass_index;
+    h->launches++;
+    return wl_launch_restart(h->pool[h->cur], h->mode == WALLACE_FP64POOL, h->n, h->N, h->Np,
+                             h->seed, h->stream_id, h->pass_index / h->restart, h->st,
+                             h->sm_count, h->stream);
+}
+
 int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, double sigma)
 {
     const int fp64 = h->mode == WALLACE_FP64POOL;
     const int v = pick_variant(h);
-    cudaError_t e;
+    cudaError_t e = maybe_restart(h);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e);
     if (v == WALLACE_VARIANT_FUSED) {
         KernelTimer t(h);
         // a single fused pass: output window must start at 0 (a prefix)
@@ -184,8 +205,8 @@ int fill_impl(wallace_t *h, void *out, int64_t count, double mu, double sigma)
     if (done >= count)
         return WALLACE_OK;
     int64_t remaining = count - done;
-    if (pick_variant(h) == WALLACE_VARIANT_FUSED) {
-        // all remaining passes in one launch
+    if (pick_variant(h) == WALLACE_VARIANT_FUSED && h->restart == 0) {
+        // all remaining passes in one launch (pass by pass when refills are due)
         int64_t passes = (remaining + h->R - 1) / h->R;
         int64_t last = remaining - (passes - 1) * h->R;
         cudaError_t e;
@@ -267,6 +288,8 @@ int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, doubl
     h->R = R;
     h->frac = frac;
     h->mode = mode;
+    h->seed = seed;
+    h->stream_id = stream_id;
     h->stream = (cudaStream_t)cuda_stream;
     h->cursor = R;   // the initial pool is not returned
     cudaError_t e = cudaGetDevice(&h->device);
@@ -460,6 +483,14 @@ int wallace_set_variant(wallace_t *h, int variant)
         return WALLACE_EINVAL;
     }
     h->variant = variant;
+    return WALLACE_OK;
+}
+
+int wallace_set_restart(wallace_t *h, int64_t interval)
+{
+    if (check(h) || interval < 0)
+        return WALLACE_EINVAL;
+    h->restart = interval;
     return WALLACE_OK;
 }
 

@@ -352,8 +352,15 @@ __device__ __forceinline__ double wl_chi_sample(int chi, int64_t nu, double x)
 // r = sqrt(2 nu - 1), S = (x + r)^2 / 2; the next pass scales A by
 // c = sqrt(S / q).  q / S_prev - 1 beyond 1e-3 means the pool was overwritten
 // (Section 8).  Then the next pass's parameters are drawn.
+// kind: what made the pool -- WL_FIN_INIT (creation: the strides of the
+// first two passes are drawn), WL_FIN_PASS (a pass: the strides advance), or
+// WL_FIN_RESTART (a Box-Muller refill, Section 5: the drift history restarts,
+// the strides and the pass count are untouched).
+#define WL_FIN_INIT 0
+#define WL_FIN_PASS 1
+#define WL_FIN_RESTART 2
 __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu, double x,
-                                   bool fp64, bool is_pass)
+                                   bool fp64, int kind)
 {
     volatile WlDevState *vs = st;
     __threadfence();
@@ -376,7 +383,7 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
     else
         c = __dsqrt_rn(__ddiv_rn(S, q));
     double drift = 0.0;
-    if (st->have_prev) {
+    if (st->have_prev && kind != WL_FIN_RESTART) {
         drift = __dsub_rn(__ddiv_rn(q, st->S_prev), 1.0);
         if (!(fabs(drift) <= 1e-3))
             status |= WL_ECORRUPT;
@@ -391,16 +398,18 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
     st->drift = drift;
     st->bad = (int32_t)bad;
     st->status = status;
-    uint64_t s = st->lcg, rep = st->lcg_pend;
-    if (is_pass) {
-        st->last = st->next;
-        st->passes += 1;
-    } else {
-        // initial pool: draw the strides of the first pass as well
-        rep = s;
-        wl_draw_params(n, N, s, st->ahead[st->passes & 1].alpha, st->ahead[st->passes & 1].gamma);
+    if (kind != WL_FIN_RESTART) {
+        uint64_t s = st->lcg, rep = st->lcg_pend;
+        if (kind == WL_FIN_PASS) {
+            st->last = st->next;
+            st->passes += 1;
+        } else {
+            // initial pool: draw the strides of the first pass as well
+            rep = s;
+            wl_draw_params(n, N, s, st->ahead[st->passes & 1].alpha, st->ahead[st->passes & 1].gamma);
+        }
+        wl_advance_strides(st, n, N, s, rep);
     }
-    wl_advance_strides(st, n, N, s, rep);
     st->next.c64 = c;
     st->next.c32 = __double2float_rn(c);
     st->acc0 = 0;

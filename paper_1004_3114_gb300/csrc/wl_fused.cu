@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
         __syncthreads();
         if (tid == 0) {
             __threadfence_block();
-            wl_finalise(st, NSUB, N, (int64_t)nu, (double)dst[nu - 1], sizeof(T) == 8, true);
+            wl_finalise(st, NSUB, N, (int64_t)nu, (double)dst[nu - 1], sizeof(T) == 8, WL_FIN_PASS);
         }
         __syncthreads();
         T *t = src;

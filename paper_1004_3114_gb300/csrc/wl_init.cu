@@ -10,20 +10,25 @@ namespace {
 
 using wl_bm::box_muller;
 
+// kind = WL_FIN_INIT: the pool of a new generator, from uniforms [0, nu).
+// kind = WL_FIN_RESTART: restart r refills the current pool from uniforms
+// [r 2^40, r 2^40 + nu) of the same sequence (Section 5, restarting).
 template <typename T>
 __global__ void __launch_bounds__(256) init_kernel(T *pool, int n, int64_t N, int64_t Np,
                                                    int64_t nu, uint32_t seed, uint32_t stream,
-                                                   WlDevState *st, int chi)
+                                                   WlDevState *st, int chi, int kind,
+                                                   uint64_t restart)
 {
     __shared__ uint64_t red[3 * 8];
     const uint64_t s0 = wl_seed_mix(seed, stream);
+    const uint64_t base = wl_lcg_jump(s0, restart << 40);
     const int64_t npairs = nu / 2;
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // map for 2G steps, to hop from pair p to pair p + G
     const uint64_t one = wl_lcg_jump(0, 2 * (uint64_t)G);         // C_{2G}
     const uint64_t AG = wl_lcg_jump(1, 2 * (uint64_t)G) - one;     // A_{2G}
-    uint64_t s = wl_lcg_jump(s0, 2 * (uint64_t)p);
+    uint64_t s = wl_lcg_jump(base, 2 * (uint64_t)p);
     uint64_t lo = 0, hi = 0;
     uint32_t bad = 0;
     for (; p < npairs; p += G) {
@@ -49,10 +54,12 @@ __global__ void __launch_bounds__(256) init_kernel(T *pool, int n, int64_t N, in
     }
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st) && threadIdx.x == 0) {
-        st->lcg = wl_lcg_jump(s0, (uint64_t)nu);
-        st->chi = chi;
+        if (kind == WL_FIN_INIT) {
+            st->lcg = wl_lcg_jump(s0, (uint64_t)nu);
+            st->chi = chi;
+        }
         double x = (double)__ldcg(&pool[wl_phys(nu - 1, N, Np)]);
-        wl_finalise(st, n, N, nu, x, sizeof(T) == 8, false);
+        wl_finalise(st, n, N, nu, x, sizeof(T) == 8, kind);
     }
 }
 
@@ -69,9 +76,27 @@ cudaError_t wl_launch_init(void *pool, int fp64, int n, int64_t N, int64_t Np, u
     int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
     if (fp64)
         init_kernel<double><<<grid, 256, 0, stream>>>((double *)pool, n, N, Np, nu, seed,
-                                                      stream_id, st, chi);
+                                                      stream_id, st, chi, WL_FIN_INIT, 0);
     else
         init_kernel<float><<<grid, 256, 0, stream>>>((float *)pool, n, N, Np, nu, seed,
-                                                     stream_id, st, chi);
+                                                     stream_id, st, chi, WL_FIN_INIT, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t wl_launch_restart(void *pool, int fp64, int n, int64_t N, int64_t Np, uint32_t seed,
+                              uint32_t stream_id, int64_t r, WlDevState *st, int sm_count,
+                              cudaStream_t stream)
+{
+    int64_t nu = (int64_t)n * N;
+    int64_t npairs = nu / 2;
+    int64_t want = (npairs + 255) / 256;
+    int64_t cap = (int64_t)sm_count * 8;
+    int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    if (fp64)
+        init_kernel<double><<<grid, 256, 0, stream>>>((double *)pool, n, N, Np, nu, seed,
+                                                      stream_id, st, 0, WL_FIN_RESTART, (uint64_t)r);
+    else
+        init_kernel<float><<<grid, 256, 0, stream>>>((float *)pool, n, N, Np, nu, seed,
+                                                     stream_id, st, 0, WL_FIN_RESTART, (uint64_t)r);
     return cudaGetLastError();
 }

@@ -27,6 +27,11 @@ cudaError_t wl_launch_init(void *pool, int fp64, int n, int64_t N, int64_t Np, u
                            uint32_t stream_id, WlDevState *st, int sm_count, cudaStream_t stream,
                            int chi = 0);
 
+// Box-Muller refill of the current pool for restart r = 1, 2, ... (Section 5)
+cudaError_t wl_launch_restart(void *pool, int fp64, int n, int64_t N, int64_t Np, uint32_t seed,
+                              uint32_t stream_id, int64_t r, WlDevState *st, int sm_count,
+                              cudaStream_t stream);
+
 // direct strided gather from global memory, any n, N, either precision
 cudaError_t wl_launch_gather(const WlPassArgs &a, int fp64, int sm_count, cudaStream_t stream);
 

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) gather_kernel(WlPassArgs a)
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st) && threadIdx.x == 0) {
         double x = (double)__ldcg(&dst[wl_phys(a.nu - 1, N, Np)]);
-        wl_finalise(st, a.n, N, a.nu, x, f64, true);
+        wl_finalise(st, a.n, N, a.nu, x, f64, WL_FIN_PASS);
     }
 }
 

@@ -120,7 +120,7 @@ __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red, int32
         wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
         __syncthreads();
         if (tid == 0)
-            wl_finalise(d.st, NSUB, N, nu, (double)dst[nu - 1], false, true);
+            wl_finalise(d.st, NSUB, N, nu, (double)dst[nu - 1], false, WL_FIN_PASS);
         float *t = src;
         src = dst;
         dst = t;
@@ -185,7 +185,7 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
         wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
         __syncthreads();
         if (tid == 0)
-            wl_finalise(d.st, NSUB, N, nu, (double)__ldcg(&dst[wl_phys(nu - 1, N, d.Np)]), false, true);
+            wl_finalise(d.st, NSUB, N, nu, (double)__ldcg(&dst[wl_phys(nu - 1, N, d.Np)]), false, WL_FIN_PASS);
         cur = 1 - cur;
     }
     return cur;

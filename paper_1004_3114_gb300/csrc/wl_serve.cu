@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(SV_THREADS, 3) pass_units_kernel(const PassIte
         wl_cta_reduce_to_state(lo, hi, bad, it.st, red);
         if (last_unit(it.st, it.nunits) && tid == 0)
             wl_finalise(it.st, it.n, N, it.nu, (double)__ldcg(&it.dst[wl_phys(it.nu - 1, N, it.Np)]),
-                        false, true);
+                        false, WL_FIN_PASS);
     }
 }
 

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) static_gather_kernel(const float *__restr
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st) && threadIdx.x == 0) {
         double x = (double)__ldcg(&dst[nu - 1]);
-        wl_finalise(st, NSUB, N, nu, x, false, false);
+        wl_finalise(st, NSUB, N, nu, x, false, WL_FIN_INIT);
     }
 }
 

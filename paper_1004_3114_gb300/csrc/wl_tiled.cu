@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(TL_THREADS, 3) tiled_kernel(WlPassArgs a)
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st) && threadIdx.x == 0) {
         double x = (double)__ldcg(&job.dst[wl_phys(a.nu - 1, job.N, job.Np)]);
-        wl_finalise(st, 4, job.N, a.nu, x, false, true);
+        wl_finalise(st, 4, job.N, a.nu, x, false, WL_FIN_PASS);
     }
 }
 

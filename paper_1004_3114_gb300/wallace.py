@@ -81,6 +81,7 @@ _SIGS = {
     "wallace_set_stream": (C.c_int, [_h, C.c_void_p]),
     "wallace_set_variant": (C.c_int, [_h, C.c_int]),
     "wallace_set_timing": (C.c_int, [_h, C.c_int]),
+    "wallace_set_restart": (C.c_int, [_h, C.c_int64]),
     "wallace_sync": (C.c_int, [_h]),
     "wallace_stats": (C.c_int, [_h, C.POINTER(Stats)]),
     "wallace_get_pool": (C.c_int, [_h, C.c_void_p]),
@@ -410,6 +411,11 @@ class Wallace:
 
     def set_timing(self, on: bool) -> None:
         _check(_lib.wallace_set_timing(self._h, int(on)), "wallace_set_timing")
+
+    def set_restart(self, interval: int) -> None:
+        """Refill the pool by Box-Muller before every pass that follows a
+        multiple of `interval` passes (0: never)."""
+        _check(_lib.wallace_set_restart(self._h, interval), "wallace_set_restart")
 
     def sync(self) -> int:
         return _check(_lib.wallace_sync(self._h), "wallace_sync", allow=ECORRUPT)

@@ -270,3 +270,31 @@ def test_wilson_hilferty_sample_bit_exact(orc, n, N, variant, mode):
         ref = o.fill(g.R)
         assert_same(got, ref, f"pass {k + 1} output")
         assert_stats_equal(g, o, f"pass {k + 1}")
+
+
+@pytest.mark.parametrize("n,N,variant,mode", [
+    (4, 1 << 17, W.VARIANT_TILED_TMA, W.FP32),
+    (4, 20000, W.VARIANT_TILED_ASYNC, W.FP32),
+    (4, 6000, W.VARIANT_GATHER, W.FP32),
+    (8, 3001, W.VARIANT_FUSED, W.FP32),
+    (4, 1024, W.VARIANT_AUTO, W.FP64POOL),
+])
+def test_restart_bit_exact(orc, n, N, variant, mode):
+    """Section 5's restart (Box-Muller refill every 2 passes) through every
+    pass kernel and the binary64 pool: outputs, pools and state per pass, and
+    one fill spanning several restarts."""
+    omode = orc.FP32 if mode == W.FP32 else orc.FP64
+    g = W.Wallace(n, N, 21, 0.5, mode=mode)
+    g.set_variant(variant)
+    g.set_restart(2)
+    o = orc.Generator(n, N, 21, 0.5, mode=omode)
+    o.set_restart(2)
+    for k in range(5):
+        got = fill_dev(g, g.R)
+        ref = o.fill(g.R)
+        assert_same(got, ref, f"pass {k + 1} output")
+        assert_stats_equal(g, o, f"pass {k + 1}")
+        if mode == W.FP32:
+            assert_same(g.pool(), o.pool32(), f"pass {k + 1} pool")
+    assert_same(fill_dev(g, 5 * g.R + 7), o.fill(5 * g.R + 7), "fill over restarts")
+    assert_stats_equal(g, o, "after the long fill")
