@@ -61,6 +61,12 @@ typedef struct wallace wallace_t;
  * (x + sqrt(2 nu - 1))^2 / 2 -- closer to chi-squared for small pools.  A
  * sample that is not positive marks the pool corrupt (c stays 1). */
 #define WALLACE_CHI_WH    0x100
+/* mode flag: a different orthogonal matrix at each pass (Section 3 prefers
+ * it to a fixed A): pass k uses A D_k with D_k = diag(+-1), its pattern the
+ * top n bits of one more uniform drawn after the pass's strides and offsets.
+ * Breaks the fixed matrix's invariant sum(pool)/sqrt(Q) (A 1 = 1).
+ * Single-generator handles only. */
+#define WALLACE_MATRIX_SIGNS 0x200
 
 /* pass kernel selection (wallace_set_variant) */
 #define WALLACE_VARIANT_AUTO    0  /* pick by pool size                                 */
@@ -96,6 +102,8 @@ typedef struct {
     int64_t kernel_launches; /* pass kernels timed                                       */
     int64_t launches;     /* kernels launched by passes and fills (pass and drain kernels),
                              counted whether or not timing is on                         */
+    uint32_t signs;       /* sign pattern of the most recent pass (WALLACE_MATRIX_SIGNS;
+                             bit i: sub-vector i negated before A)                        */
 } wallace_stats_t;
 
 /*
@@ -117,7 +125,8 @@ int wallace_create(int n, int64_t N, uint32_t seed, double frac, wallace_t **out
  * wallace_create_ex -- as wallace_create, plus:
  *   stream_id  appended to the seed (Section 8: DP_VRANU4 appends the
  *              processor number so that processors get different sequences)
- *   mode       WALLACE_FP32 or WALLACE_FP64POOL, optionally OR WALLACE_CHI_WH
+ *   mode       WALLACE_FP32 or WALLACE_FP64POOL, optionally OR-ed with
+ *              WALLACE_CHI_WH and/or WALLACE_MATRIX_SIGNS
  *   cuda_stream  cudaStream_t to run on (NULL: legacy default stream)
  */
 int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, double frac,

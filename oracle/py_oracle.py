@@ -21,6 +21,7 @@ LIB = os.path.join(HERE, "liborc.so")
 
 FP32, FP64 = 0, 1
 CHI_WH = 0x100   # mode flag: Wilson-Hilferty chi-squared sample
+SIGNS = 0x200    # mode flag: random sign pattern per pass (matrix A D_k)
 OK, EINVAL, ENOMEM, ECORRUPT = 0, 1, 2, 4
 
 CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
@@ -45,6 +46,7 @@ class Stats(C.Structure):
         ("drift", C.c_double), ("passes", C.c_int64), ("status", C.c_int),
         ("bad", C.c_int), ("lcg", C.c_uint64), ("alpha", C.c_int32 * 8),
         ("gamma", C.c_int64 * 8), ("R", C.c_int64), ("cursor", C.c_int64),
+        ("signs", C.c_uint32),
     ]
 
     @property
@@ -80,8 +82,10 @@ def lib():
             "orc_transform32": (None, [C.c_int, f32p, C.c_float, f32p]),
             "orc_transform64": (None, [C.c_int, f64p, C.c_double, f64p]),
             "orc_term32": (C.c_uint64, [C.c_float, C.POINTER(C.c_int)]),
-            "orc_pass_explicit32": (None, [C.c_int, C.c_int64, f32p, f32p, i32p, i64p, C.c_float]),
-            "orc_pass_explicit64": (None, [C.c_int, C.c_int64, f64p, f64p, i32p, i64p, C.c_double]),
+            "orc_pass_explicit32": (None, [C.c_int, C.c_int64, f32p, f32p, i32p, i64p, C.c_float,
+                                           C.c_uint32]),
+            "orc_pass_explicit64": (None, [C.c_int, C.c_int64, f64p, f64p, i32p, i64p, C.c_double,
+                                           C.c_uint32]),
             "orc_sumsq32": (C.c_int, [f32p, C.c_int64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
             "orc_sumsq64": (C.c_int, [f64p, C.c_int64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
             "orc_returned_count": (C.c_int64, [C.c_int64, C.c_double]),
@@ -186,17 +190,19 @@ def _pad8(a, dtype):
     return out
 
 
-def pass_explicit32(n, N, x, alpha, gamma, c) -> np.ndarray:
+def pass_explicit32(n, N, x, alpha, gamma, c, signs: int = 0) -> np.ndarray:
     x = np.ascontiguousarray(x, dtype=np.float32)
     y = np.empty_like(x)
-    lib().orc_pass_explicit32(n, N, x, y, _pad8(alpha, np.int32), _pad8(gamma, np.int64), np.float32(c))
+    lib().orc_pass_explicit32(n, N, x, y, _pad8(alpha, np.int32), _pad8(gamma, np.int64), np.float32(c),
+                              signs)
     return y
 
 
-def pass_explicit64(n, N, x, alpha, gamma, c) -> np.ndarray:
+def pass_explicit64(n, N, x, alpha, gamma, c, signs: int = 0) -> np.ndarray:
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.empty_like(x)
-    lib().orc_pass_explicit64(n, N, x, y, _pad8(alpha, np.int32), _pad8(gamma, np.int64), float(c))
+    lib().orc_pass_explicit64(n, N, x, y, _pad8(alpha, np.int32), _pad8(gamma, np.int64), float(c),
+                              signs)
     return y
 
 
@@ -223,7 +229,7 @@ class Generator:
 
     def __init__(self, n: int, N: int, seed: int, frac: float = 1.0,
                  mode: int = FP32, stream: int = 0):
-        self.n, self.N, self.mode = n, N, mode & ~CHI_WH
+        self.n, self.N, self.mode = n, N, mode & ~(CHI_WH | SIGNS)
         self.chi_wh = bool(mode & CHI_WH)
         self.nu = n * N
         self._h = lib().orc_create(n, N, seed, stream, frac, mode)

@@ -318,17 +318,22 @@ void orc_transform64(int n, const double *g, double c, double *y)
     }
 }
 
-/* One pass, Eq. 1 with n sub-vectors: x'_i[j] = (A g)_i, g_i = x_i[(alpha_i j +
+/* One pass, Eq. 1 with n sub-vectors: x'_i[j] = (A D g)_i, g_i = x_i[(alpha_i j +
  * gamma_i) mod N], j = 0..N-1, into a second buffer (double buffering,
- * Section 2).  Pool layout: sub-vector i occupies x[i*N .. i*N+N-1]. */
+ * Section 2).  Pool layout: sub-vector i occupies x[i*N .. i*N+N-1].
+ * D = diag(+-1): bit i of `signs` negates g_i (0 for the fixed matrix A;
+ * Section 3 prefers a different orthogonal matrix at each pass, and A D is
+ * orthogonal for every sign pattern). */
 void orc_pass_explicit32(int n, int64_t N, const float *x, float *y,
-                         const int32_t *alpha, const int64_t *gamma, float c)
+                         const int32_t *alpha, const int64_t *gamma, float c, uint32_t signs)
 {
     float g[8], t[8];
     for (int64_t j = 0; j < N; j++) {
         for (int i = 0; i < n; i++) {
             uint64_t idx = ((uint64_t)alpha[i] * (uint64_t)j + (uint64_t)gamma[i]) % (uint64_t)N;
             g[i] = x[(int64_t)i * N + (int64_t)idx];
+            if ((signs >> i) & 1u)
+                g[i] = -g[i];
         }
         orc_transform32(n, g, c, t);
         for (int k = 0; k < n; k++)
@@ -337,13 +342,15 @@ void orc_pass_explicit32(int n, int64_t N, const float *x, float *y,
 }
 
 void orc_pass_explicit64(int n, int64_t N, const double *x, double *y,
-                         const int32_t *alpha, const int64_t *gamma, double c)
+                         const int32_t *alpha, const int64_t *gamma, double c, uint32_t signs)
 {
     double g[8], t[8];
     for (int64_t j = 0; j < N; j++) {
         for (int i = 0; i < n; i++) {
             uint64_t idx = ((uint64_t)alpha[i] * (uint64_t)j + (uint64_t)gamma[i]) % (uint64_t)N;
             g[i] = x[(int64_t)i * N + (int64_t)idx];
+            if ((signs >> i) & 1u)
+                g[i] = -g[i];
         }
         orc_transform64(n, g, c, t);
         for (int k = 0; k < n; k++)
@@ -421,7 +428,7 @@ int64_t orc_returned_count(int64_t nu, double frac)
  * A whole generator.
  * ------------------------------------------------------------------------ */
 struct orc_gen {
-    int n, mode, chi;
+    int n, mode, chi, msigns;
     uint32_t seed, stream;
     int64_t restart; /* refill interval in passes (0: never) */
     int64_t N, nu, R;
@@ -504,7 +511,8 @@ orc_gen *orc_create(int n, int64_t N, uint32_t seed, uint32_t stream, double fra
     if ((n != 4 && n != 8) || N < 4 || (int64_t)n * N > ((int64_t)1 << 30))
         return NULL;
     int chi = (mode & ORC_CHI_WH) != 0;
-    mode &= ~ORC_CHI_WH;
+    int msigns = (mode & ORC_SIGNS) != 0;
+    mode &= ~(ORC_CHI_WH | ORC_SIGNS);
     if (!(frac > 0.0 && frac <= 1.0) || (mode != ORC_FP32 && mode != ORC_FP64))
         return NULL;
     int64_t nu = (int64_t)n * N;
@@ -516,6 +524,7 @@ orc_gen *orc_create(int n, int64_t N, uint32_t seed, uint32_t stream, double fra
         return NULL;
     g->n = n;
     g->chi = chi;
+    g->msigns = msigns;
     g->seed = seed;
     g->stream = stream;
     g->N = N;
@@ -596,13 +605,16 @@ int orc_pass(orc_gen *g)
     if (g->restart > 0 && g->st.passes > 0 && g->st.passes % g->restart == 0)
         orc_restart(g, g->st.passes / g->restart);
     orc_draw_params(g->n, g->N, &g->lcg, g->st.alpha, g->st.gamma);
+    /* ORC_SIGNS (reading of Section 3's per-pass matrices): one more uniform
+     * per pass; its top n bits are the sign pattern of D_k */
+    g->st.signs = g->msigns ? orc_lcg_next(&g->lcg) >> (32 - g->n) : 0u;
     int src = g->cur, dst = 1 - g->cur;
     if (g->mode == ORC_FP32)
         orc_pass_explicit32(g->n, g->N, g->p32[src], g->p32[dst], g->st.alpha, g->st.gamma,
-                            g->st.c32);
+                            g->st.c32, g->st.signs);
     else
         orc_pass_explicit64(g->n, g->N, g->p64[src], g->p64[dst], g->st.alpha, g->st.gamma,
-                            g->st.c);
+                            g->st.c, g->st.signs);
     g->cur = dst;
     g->st.passes++;
     orc_finalise(g);

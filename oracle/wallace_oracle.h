@@ -29,6 +29,8 @@ extern "C" {
 enum { ORC_FP32 = 0, ORC_FP64 = 1 };
 /* mode flag: Wilson-Hilferty chi-squared sample instead of Eq. 3's */
 enum { ORC_CHI_WH = 0x100 };
+/* mode flag: a random sign pattern per pass, matrix A D_k (Section 3) */
+enum { ORC_SIGNS = 0x200 };
 
 enum {
     ORC_OK = 0,
@@ -55,6 +57,7 @@ typedef struct {
     int64_t gamma[8];      /* offsets of the most recent pass                */
     int64_t R;             /* values returned per pass                       */
     int64_t cursor;        /* next returned index in the current pool        */
+    uint32_t signs;        /* sign pattern of the most recent pass (ORC_SIGNS) */
 } orc_stats;
 
 /* ---- building blocks (exposed so the tests can pin each one) ---------- */
@@ -74,9 +77,9 @@ void orc_transform64(int n, const double *g, double c, double *y);
 uint64_t orc_term32(float y, int *bad);
 /* one pass from explicit parameters (no correction bookkeeping) */
 void orc_pass_explicit32(int n, int64_t N, const float *x, float *y,
-                         const int32_t *alpha, const int64_t *gamma, float c);
+                         const int32_t *alpha, const int64_t *gamma, float c, uint32_t signs);
 void orc_pass_explicit64(int n, int64_t N, const double *x, double *y,
-                         const int32_t *alpha, const int64_t *gamma, double c);
+                         const int32_t *alpha, const int64_t *gamma, double c, uint32_t signs);
 /* exact sum of squares of an FP32 pool: returns 0/1 "bad" flag */
 int orc_sumsq32(const float *pool, int64_t nu, uint64_t *q_lo, uint64_t *q_hi);
 int orc_sumsq64(const double *pool, int64_t nu, uint64_t *q_lo, uint64_t *q_hi);

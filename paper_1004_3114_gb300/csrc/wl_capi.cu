@@ -25,6 +25,7 @@ struct wallace {
     int64_t pass_index = 0;   // passes launched (selects a pass's strides slot)
     uint32_t seed = 0, stream_id = 0;
     int64_t restart = 0;          // refill interval in passes (0: never)
+    int msigns = 0;               // per-pass sign patterns (WALLACE_MATRIX_SIGNS)
     int64_t restarted_at = 0;     // pass index of the last refill
     WlDevState *st = nullptr;
     int64_t cursor = 0;
@@ -168,7 +169,7 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
         KernelTimer t(h);
         if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_TMA) &&
             wl_tma_supported(h->n, h->N, fp64, h->sm_count))
-            e = wl_launch_tma(a, h->sm_count, h->stream);
+            e = wl_launch_tma(a, h->sm_count, h->msigns, h->stream);
         else if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_ASYNC ||
                   v == WALLACE_VARIANT_TILED_TMA) &&
                  wl_tiled_supported(h->n, h->N, fp64))
@@ -266,8 +267,8 @@ int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, doubl
     *out = nullptr;
     if ((n != 4 && n != 8) || N < 4 || (int64_t)n * N > ((int64_t)1 << 30))
         return WALLACE_EINVAL;
-    const int chi = (mode & WALLACE_CHI_WH) ? 1 : 0;
-    mode &= ~WALLACE_CHI_WH;
+    const int opts = ((mode & WALLACE_CHI_WH) ? 1 : 0) | ((mode & WALLACE_MATRIX_SIGNS) ? 2 : 0);
+    mode &= ~(WALLACE_CHI_WH | WALLACE_MATRIX_SIGNS);
     if (!(frac > 0.0 && frac <= 1.0) || (mode != WALLACE_FP32 && mode != WALLACE_FP64POOL))
         return WALLACE_EINVAL;
     const int64_t nu = (int64_t)n * N;
@@ -288,6 +289,7 @@ int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, doubl
     h->R = R;
     h->frac = frac;
     h->mode = mode;
+    h->msigns = (opts >> 1) & 1;
     h->seed = seed;
     h->stream_id = stream_id;
     h->stream = (cudaStream_t)cuda_stream;
@@ -317,7 +319,7 @@ int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, doubl
         e = cudaMemsetAsync(h->st, 0, sizeof(WlDevState), h->stream);
     if (e == cudaSuccess)
         e = wl_launch_init(h->pool[0], mode == WALLACE_FP64POOL, n, N, h->Np, seed, stream_id,
-                           h->st, h->sm_count, h->stream, chi);
+                           h->st, h->sm_count, h->stream, opts);
     if (e != cudaSuccess) {
         wallace_destroy(h);
         return WALLACE_ECUDA;
@@ -549,6 +551,7 @@ int wallace_stats(wallace_t *h, wallace_stats_t *out)
     out->cursor = h->cursor;
     out->kernel_ms = h->kernel_ms;
     out->kernel_launches = h->kernel_launches;
+    out->signs = s.last.signs;
     out->launches = h->launches;
     return out->status;
 }

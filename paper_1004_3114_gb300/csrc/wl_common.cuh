@@ -22,7 +22,7 @@ struct WlParams {
     int32_t alpha[8];
     int64_t gamma[8];
     float c32;
-    float pad_;
+    uint32_t signs;     // bit i: sub-vector i negated before A (0 for the fixed A)
     double c64;
 };
 
@@ -30,6 +30,8 @@ struct WlParams {
 struct WlStrides {
     int32_t alpha[8];
     int64_t gamma[8];
+    uint32_t signs;
+    uint32_t pad_;
 };
 
 // One generator's device state.  The finaliser of a pass writes `next`;
@@ -52,15 +54,18 @@ struct WlDevState {
     uint64_t acc2;          // 64-127 of each CTA's 128-bit sum (see wl_acc_read)
     uint32_t acc_bad;       // a value was non-finite or |y| >= 256
     uint32_t ticket;        // CTAs finished in the pass in flight
-    uint32_t tile_ctr;      // next tile of the pass in flight (dynamically scheduled kernels)
-    uint32_t pad2_;
     uint64_t q_lo, q_hi;    // Q of the most recent pool
     double q, S, S_prev, c, drift;
     int32_t have_prev;
     int32_t status;         // sticky WL_* bits
     int32_t bad;
     int32_t chi;            // 0: Eq. 3's sample; 1: Wilson-Hilferty's (set at creation)
+    int32_t msigns;         // 1: a random sign pattern per pass, matrix A D_k (set at creation)
+    int32_t pad3_;
     int64_t passes;
+    // next tile of the pass in flight (dynamically scheduled kernels): every
+    // CTA takes tiles from it all pass long, so it has a cache line to itself
+    alignas(128) uint32_t tile_ctr;
 };
 
 // ---- uniform source --------------------------------------------------------
@@ -311,10 +316,31 @@ __device__ __forceinline__ void wl_acc_read(WlDevState *st, uint64_t &lo, uint64
     lo = t;
 }
 
+// The draws of one pass into a strides slot: 2n uniforms for the strides
+// and offsets, then (per-pass sign patterns on) one whose top n bits are
+// the pattern (Section 3 prefers a different orthogonal matrix each pass).
+__device__ __forceinline__ void wl_draw_pass(int n, int64_t N, uint64_t &s, WlStrides &slot,
+                                             int msigns)
+{
+    wl_draw_params(n, N, s, slot.alpha, slot.gamma);
+    slot.signs = msigns ? wl_lcg_step(s) >> (32 - n) : 0u;
+}
+
+// Negate g when bit i of the pattern is set (a sign-bit flip: exact).
+__device__ __forceinline__ float wl_sgn(float g, uint32_t signs, int i)
+{
+    return __uint_as_float(__float_as_uint(g) ^ (((signs >> i) & 1u) << 31));
+}
+__device__ __forceinline__ double wl_sgn(double g, uint32_t signs, int i)
+{
+    return __longlong_as_double(__double_as_longlong(g) ^ ((long long)((signs >> i) & 1u) << 63));
+}
+
 // With k = st->passes (already counted): `next` takes pass k's strides from
 // their slot and pass k + 1's are drawn into the other.  s is the uniform
 // state after the draw for pass k, rep the state before it.
-__device__ inline void wl_advance_strides(WlDevState *st, int n, int64_t N, uint64_t s, uint64_t rep)
+__device__ inline void wl_advance_strides(WlDevState *st, int n, int64_t N, uint64_t s, uint64_t rep,
+                                          int msigns)
 {
     const int64_t k = st->passes;
     const WlStrides &cur = st->ahead[k & 1];
@@ -322,9 +348,10 @@ __device__ inline void wl_advance_strides(WlDevState *st, int n, int64_t N, uint
         st->next.alpha[i] = cur.alpha[i];
         st->next.gamma[i] = cur.gamma[i];
     }
+    st->next.signs = cur.signs;
     st->lcg_rep = rep;
     st->lcg_pend = s;
-    wl_draw_params(n, N, s, st->ahead[(k + 1) & 1].alpha, st->ahead[(k + 1) & 1].gamma);
+    wl_draw_pass(n, N, s, st->ahead[(k + 1) & 1], msigns);
     st->lcg = s;
 }
 
@@ -406,9 +433,9 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
         } else {
             // initial pool: draw the strides of the first pass as well
             rep = s;
-            wl_draw_params(n, N, s, st->ahead[st->passes & 1].alpha, st->ahead[st->passes & 1].gamma);
+            wl_draw_pass(n, N, s, st->ahead[st->passes & 1], st->msigns);
         }
-        wl_advance_strides(st, n, N, s, rep);
+        wl_advance_strides(st, n, N, s, rep, st->msigns);
     }
     st->next.c64 = c;
     st->next.c32 = __double2float_rn(c);
@@ -428,7 +455,7 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
 // parameter draw overlap.  rnu = sqrt(2 nu - 1), correctly rounded; xp points
 // at the withheld last value of the new pool.  Every thread of the CTA calls.
 __device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, int64_t nu, double rnu,
-                                       const float *xp)
+                                       const float *xp, int msigns)
 {
     __shared__ double s_S, s_c;
     __shared__ int32_t s_flag[2];
@@ -480,7 +507,7 @@ __device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, int64_t
         } else {
             st->last = st->next;
             st->passes = vs->passes + 1;
-            wl_advance_strides(st, n, N, vs->lcg, vs->lcg_pend);
+            wl_advance_strides(st, n, N, vs->lcg, vs->lcg_pend, msigns);
         }
     }
     __syncthreads();

@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
     __shared__ int32_t s_alpha[NSUB];
     __shared__ int32_t s_gamma[NSUB];
     __shared__ T s_c;
+    __shared__ uint32_t s_signs;
     const int tid = threadIdx.x;
     const int nu = NSUB * (int)N;
     T *buf0 = (T *)fsm;
@@ -49,9 +50,11 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
                 s_c = st->next.c64;
             else
                 s_c = st->next.c32;
+            s_signs = st->next.signs;
         }
         __syncthreads();
         const T c = s_c;
+        const uint32_t signs = s_signs;
         const int take = (int)(pass + 1 < passes ? R : last_take);
         T *o = out + pass * R;
         int idx[NSUB], stp[NSUB];
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
             T g[NSUB], y[NSUB];
 #pragma unroll
             for (int i = 0; i < NSUB; i++) {
-                g[i] = src[i * (int)N + idx[i]];
+                g[i] = wl_sgn(src[i * (int)N + idx[i]], signs, i);
                 idx[i] += stp[i];
                 if (idx[i] >= (int)N)
                     idx[i] -= (int)N;

@@ -16,7 +16,7 @@ using wl_bm::box_muller;
 template <typename T>
 __global__ void __launch_bounds__(256) init_kernel(T *pool, int n, int64_t N, int64_t Np,
                                                    int64_t nu, uint32_t seed, uint32_t stream,
-                                                   WlDevState *st, int chi, int kind,
+                                                   WlDevState *st, int opts, int kind,
                                                    uint64_t restart)
 {
     __shared__ uint64_t red[3 * 8];
@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(256) init_kernel(T *pool, int n, int64_t N, in
     if (wl_last_cta(st) && threadIdx.x == 0) {
         if (kind == WL_FIN_INIT) {
             st->lcg = wl_lcg_jump(s0, (uint64_t)nu);
-            st->chi = chi;
+            st->chi = opts & 1;
+            st->msigns = (opts >> 1) & 1;
         }
         double x = (double)__ldcg(&pool[wl_phys(nu - 1, N, Np)]);
         wl_finalise(st, n, N, nu, x, sizeof(T) == 8, kind);
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(256) init_kernel(T *pool, int n, int64_t N, in
 
 cudaError_t wl_launch_init(void *pool, int fp64, int n, int64_t N, int64_t Np, uint32_t seed,
                            uint32_t stream_id, WlDevState *st, int sm_count, cudaStream_t stream,
-                           int chi)
+                           int opts)
 {
     int64_t nu = (int64_t)n * N;
     int64_t npairs = nu / 2;
@@ -76,10 +77,10 @@ cudaError_t wl_launch_init(void *pool, int fp64, int n, int64_t N, int64_t Np, u
     int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
     if (fp64)
         init_kernel<double><<<grid, 256, 0, stream>>>((double *)pool, n, N, Np, nu, seed,
-                                                      stream_id, st, chi, WL_FIN_INIT, 0);
+                                                      stream_id, st, opts, WL_FIN_INIT, 0);
     else
         init_kernel<float><<<grid, 256, 0, stream>>>((float *)pool, n, N, Np, nu, seed,
-                                                     stream_id, st, chi, WL_FIN_INIT, 0);
+                                                     stream_id, st, opts, WL_FIN_INIT, 0);
     return cudaGetLastError();
 }
 

@@ -22,10 +22,11 @@ struct WlPassArgs {
     int64_t pass;   // passes completed before this one (selects its strides' slot)
 };
 
-// chi: the chi-squared sample the generator uses (0: Eq. 3, 1: Wilson-Hilferty)
+// opts: bit 0 -- the Wilson-Hilferty chi-squared sample instead of Eq. 3's;
+//       bit 1 -- a random sign pattern per pass (matrix A D_k)
 cudaError_t wl_launch_init(void *pool, int fp64, int n, int64_t N, int64_t Np, uint32_t seed,
                            uint32_t stream_id, WlDevState *st, int sm_count, cudaStream_t stream,
-                           int chi = 0);
+                           int opts = 0);
 
 // Box-Muller refill of the current pool for restart r = 1, 2, ... (Section 5)
 cudaError_t wl_launch_restart(void *pool, int fp64, int n, int64_t N, int64_t Np, uint32_t seed,
@@ -47,7 +48,8 @@ cudaError_t wl_launch_tiled(const WlPassArgs &a, int sm_count, cudaStream_t stre
 // warp-specialised lane-tiled gather with bulk (TMA) copies into a stage ring
 // (binary32, n = 4, N a multiple of 4)
 bool wl_tma_supported(int n, int64_t N, int fp64, int sm_count);
-cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, cudaStream_t stream);
+// signs: the generator draws a sign pattern per pass (matrix A D_k)
+cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream);
 
 // whole pool resident in shared memory for `passes` passes in one launch.
 // Pass k (0-based) writes its values [0, take_k) to out + out_off_k where

@@ -31,13 +31,14 @@ __global__ void __launch_bounds__(256) gather_kernel(WlPassArgs a)
     }
     T *out = (T *)a.out;
     const T mu = (T)a.mu, sigma = (T)a.sigma;
+    const uint32_t signs = st->next.signs;
     uint64_t lo = 0, hi = 0;
     uint32_t bad = 0;
     for (; j < N; j += G) {
         T g[NSUB], y[NSUB];
 #pragma unroll
         for (int i = 0; i < NSUB; i++) {
-            g[i] = src[i * Np + idx[i]];
+            g[i] = wl_sgn(src[i * Np + idx[i]], signs, i);
             idx[i] += step[i];
             if (idx[i] >= N)
                 idx[i] -= N;

@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(TL_THREADS, 3) tiled_kernel(WlPassArgs a)
         job.gam[i] = st->next.gamma[i];
     }
     job.c = st->next.c32;
+    job.signs = st->next.signs;
     job.out = (float *)a.out;
     job.w0 = a.w0;
     job.w1 = a.w1;

@@ -38,6 +38,7 @@ struct WlTileJob {
     float *out;
     int64_t w0, w1;
     float mu, sigma;
+    uint32_t signs = 0;   // per-pass sign pattern (bit i negates g_i)
 };
 
 __host__ __device__ constexpr int tl_data_words() { return 4 * TL_EMAX + 4 * TL_MAXSPANS; }
@@ -102,7 +103,7 @@ __device__ inline void wl_gather4_range(const WlTileJob &a, int64_t j, int64_t G
         float g[4], y[4];
 #pragma unroll
         for (int i = 0; i < 4; i++) {
-            g[i] = a.src[i * Np + idx[i]];
+            g[i] = wl_sgn(a.src[i * Np + idx[i]], a.signs, i);
             idx[i] += stp[i];
             if (idx[i] >= N)
                 idx[i] -= N;
@@ -259,7 +260,7 @@ __device__ inline void wl_tiled4_tiles(const WlTileJob &a, int L, int tile0, int
             float g[4], y[4];
 #pragma unroll
             for (int i = 0; i < 4; i++)
-                g[i] = smem[laneoff[i * TL_LMAX + l] + a.alpha[i] * t];
+                g[i] = wl_sgn(smem[laneoff[i * TL_LMAX + l] + a.alpha[i] * t], a.signs, i);
             wl_xform4(g, a.c, y);
             const int64_t j = (int64_t)jl + tt;
 #pragma unroll

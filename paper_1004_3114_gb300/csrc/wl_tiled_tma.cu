@@ -155,6 +155,9 @@ __device__ __forceinline__ float tm_wait_prev(WlDevState *st, volatile float *s_
     return *s_c;
 }
 
+// SG: the generator draws a sign pattern each pass (matrix A D_k); the
+// fixed-matrix kernel has no trace of it.
+template <bool SG>
 __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double rnu)
 {
     extern __shared__ __align__(128) float smem[];
@@ -180,6 +183,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
     // one L2 slice
     __shared__ int64_t s_gam[4];
     __shared__ int s_alpha[4];
+    __shared__ uint32_t s_signs;
     __shared__ volatile float s_c;
     if (warp == 0) {
         const WlStrides *cur = &st->ahead[a.pass & 1];
@@ -187,8 +191,11 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
             s_alpha[lane] = __ldcg(&cur->alpha[lane]);
         else if (lane < 8)
             s_gam[lane - 4] = (int64_t)__ldcg((const long long *)&cur->gamma[lane - 4]);
+        else if (lane == 8)
+            s_signs = SG ? __ldcg(&cur->signs) : 0u;
     }
     __syncthreads();
+    const uint32_t signs = SG ? s_signs : 0u;
     int alpha[4];
     int64_t gam[4];
 #pragma unroll
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
             float g[4], y[4];
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                g[i] = src[i * Np + idx[i]];
+                g[i] = wl_sgn(src[i * Np + idx[i]], signs, i);
                 idx[i] += stp[i];
                 if (idx[i] >= N)
                     idx[i] -= N;
@@ -459,6 +466,10 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
                         for (int i = 0; i < 4; i++) {
                             g[i] = gp[i][alpha[i] * t];
                             h[i] = v2 ? gp[i][alpha[i] * (t + 32)] : 0.f;
+                            if (SG) {   // the pass's matrix is A D_k
+                                g[i] = wl_sgn(g[i], signs, i);
+                                h[i] = wl_sgn(h[i], signs, i);
+                            }
                         }
                         wl_xform4(g, c, y);
                         wl_xform4(h, c, z);
@@ -496,10 +507,10 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
 
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st))
-        wl_finalise_cta(st, 4, N, a.nu, rnu, &dst[wl_phys(a.nu - 1, N, Np)]);
+        wl_finalise_cta(st, 4, N, a.nu, rnu, &dst[wl_phys(a.nu - 1, N, Np)], SG ? 1 : 0);
 }
 
-bool g_tma_configured = false;
+bool g_tma_configured[2] = {false, false};
 
 } // namespace
 
@@ -510,15 +521,15 @@ bool wl_tma_supported(int n, int64_t N, int fp64, int sm_count)
     return n == 4 && !fp64 && N >= TM_MIN_N && (N & 3) == 0 && N <= ((int64_t)1 << 28);
 }
 
-cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, cudaStream_t stream)
+cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream)
 {
     const size_t smem = tm_smem_bytes();
-    if (!g_tma_configured) {
-        cudaError_t e = cudaFuncSetAttribute(tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    auto kern = signs ? tma_kernel<true> : tma_kernel<false>;
+    if (!g_tma_configured[signs ? 1 : 0]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        g_tma_configured = true;
+        g_tma_configured[signs ? 1 : 0] = true;
     }
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
@@ -532,7 +543,7 @@ cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, cudaStream_t stream
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const double rnu = sqrt(2.0 * (double)a.nu - 1.0);   // IEEE square root: correctly rounded
-    cudaError_t e = cudaLaunchKernelEx(&cfg, tma_kernel, a, rnu);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, rnu);
     if (e != cudaSuccess)
         return e;
     return cudaGetLastError();

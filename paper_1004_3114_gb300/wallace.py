@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "wallace.h")
 OK, EINVAL, ENOMEM, ECORRUPT, ECUDA, ETIMEOUT, ESTATE = 0, 1, 2, 4, 8, 16, 32
 FP32, FP64POOL = 0, 1
 CHI_WH = 0x100   # mode flag: Wilson-Hilferty chi-squared sample
+MATRIX_SIGNS = 0x200   # mode flag: random sign pattern per pass (matrix A D_k)
 VARIANT_AUTO, VARIANT_GATHER, VARIANT_TILED, VARIANT_FUSED = 0, 1, 2, 3
 VARIANT_TILED_ASYNC, VARIANT_TILED_TMA = 4, 5
 
@@ -36,6 +37,7 @@ class Stats(C.Structure):
         ("status", C.c_int32), ("bad", C.c_int32), ("lcg", C.c_uint64),
         ("alpha", C.c_int32 * 8), ("gamma", C.c_int64 * 8), ("R", C.c_int64),
         ("cursor", C.c_int64), ("kernel_ms", C.c_double), ("kernel_launches", C.c_int64), ("launches", C.c_int64),
+        ("signs", C.c_uint32),
     ]
 
     @property
@@ -351,7 +353,7 @@ class Wallace:
 
     def __init__(self, n: int, N: int, seed: int, frac: float = 1.0, *, stream_id: int = 0,
                  mode: int = FP32, stream=None):
-        self.n, self.N, self.mode = n, N, mode & ~CHI_WH
+        self.n, self.N, self.mode = n, N, mode & ~(CHI_WH | MATRIX_SIGNS)
         self.nu = n * N
         h = _h()
         rc = _lib.wallace_create_ex(n, N, seed, stream_id, frac, mode, _stream_ptr(stream),

@@ -46,6 +46,7 @@ def assert_stats_equal(g, o, what=""):
     assert gs.lcg == os_.lcg, what     # uniform state after drawing the next pass's strides
     assert list(gs.alpha[:g.n]) == list(os_.alpha[:g.n]), what
     assert list(gs.gamma[:g.n]) == list(os_.gamma[:g.n]), what
+    assert gs.signs == os_.signs, what
     assert gs.status == os_.status, what
 
 
@@ -298,3 +299,34 @@ def test_restart_bit_exact(orc, n, N, variant, mode):
             assert_same(g.pool(), o.pool32(), f"pass {k + 1} pool")
     assert_same(fill_dev(g, 5 * g.R + 7), o.fill(5 * g.R + 7), "fill over restarts")
     assert_stats_equal(g, o, "after the long fill")
+
+
+@pytest.mark.parametrize("n,N,variant,mode", [
+    (4, 1 << 17, W.VARIANT_TILED_TMA, W.FP32),
+    (4, 16387, W.VARIANT_TILED_TMA, W.FP32),       # N % 4 != 0: the async tiled kernel
+    (4, 20000, W.VARIANT_TILED_ASYNC, W.FP32),
+    (4, 45045, W.VARIANT_TILED, W.FP32),           # fallback strides: in-kernel gather
+    (8, 5000, W.VARIANT_GATHER, W.FP32),
+    (8, 3001, W.VARIANT_FUSED, W.FP32),
+    (4, 1024, W.VARIANT_AUTO, W.FP64POOL),
+])
+def test_sign_patterns_bit_exact(orc, n, N, variant, mode):
+    """A different orthogonal matrix each pass (A D_k, Section 3) through every
+    pass kernel and the binary64 pool; combined with the Wilson-Hilferty
+    sample and restarts on the TMA case."""
+    extra = W.CHI_WH if N == 1 << 17 else 0
+    omode = (orc.FP32 if mode == W.FP32 else orc.FP64) | orc.SIGNS | (orc.CHI_WH if extra else 0)
+    g = W.Wallace(n, N, 17, 0.5, mode=mode | W.MATRIX_SIGNS | extra)
+    g.set_variant(variant)
+    o = orc.Generator(n, N, 17, 0.5, mode=omode)
+    if extra:
+        g.set_restart(3)
+        o.set_restart(3)
+    seen = set()
+    for k in range(7):
+        got = fill_dev(g, g.R)
+        ref = o.fill(g.R)
+        assert_same(got, ref, f"pass {k + 1} output")
+        assert_stats_equal(g, o, f"pass {k + 1}")
+        seen.add(g.stats().signs)
+    assert len(seen) > 1
