@@ -46,7 +46,7 @@ class Stats(C.Structure):
         ("drift", C.c_double), ("passes", C.c_int64), ("status", C.c_int),
         ("bad", C.c_int), ("lcg", C.c_uint64), ("alpha", C.c_int32 * 8),
         ("gamma", C.c_int64 * 8), ("R", C.c_int64), ("cursor", C.c_int64),
-        ("signs", C.c_uint32),
+        ("signs", C.c_uint32), ("rot_c", C.c_double), ("rot_s", C.c_double),
     ]
 
     @property
@@ -74,6 +74,9 @@ def lib():
             "orc_sincos_2pi": (None, [C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "orc_box_muller": (None, [C.c_uint32, C.c_uint32, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
             "orc_lcg_jump": (C.c_uint64, [C.c_uint64, C.c_uint64]),
+            "orc_draw_rotation": (None, [C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+            "orc_pass_rot32": (None, [C.c_int64, f32p, f32p, i32p, i64p, C.c_float, C.c_float]),
+            "orc_pass_rot64": (None, [C.c_int64, f64p, f64p, i32p, i64p, C.c_double, C.c_double]),
             "orc_set_restart": (None, [C.c_void_p, C.c_int64]),
             "orc_restart_pool": (None, [C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, f32p]),
             "orc_boxmuller_stream": (None, [C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, C.c_float,

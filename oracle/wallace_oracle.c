@@ -238,11 +238,15 @@ static int orc_stride_ok(int32_t a, int64_t N, const int32_t *used, int nused)
     return 1;
 }
 
+/* n = 2 is RANN4 itself (Section 8): alpha from {3, 5} for x and beta from
+ * {7, 11} for y, each drawn as above among the candidates still available. */
+static const int32_t ORC_CAND2[2][2] = {{3, 5}, {7, 11}};
+
 void orc_draw_params(int n, int64_t N, uint64_t *state, int32_t *alpha, int64_t *gamma)
 {
-    const int32_t *cand = n == 4 ? ORC_CAND4 : ORC_CAND8;
-    const int ncand = n == 4 ? 5 : 11;
     for (int i = 0; i < n; i++) {
+        const int32_t *cand = n == 4 ? ORC_CAND4 : (n == 8 ? ORC_CAND8 : ORC_CAND2[i]);
+        const int ncand = n == 4 ? 5 : (n == 8 ? 11 : 2);
         uint32_t us = orc_lcg_next(state);
         int32_t avail[11];
         int na = 0;
@@ -260,6 +264,72 @@ void orc_draw_params(int n, int64_t N, uint64_t *state, int32_t *alpha, int64_t 
         alpha[i] = a;
         uint32_t uo = orc_lcg_next(state);
         gamma[i] = (int64_t)(((uint64_t)uo * (uint64_t)N) >> 32);
+    }
+}
+
+/* ------------------------------------------------------------------------ *
+ * RANN4's rotation (Section 8, n = 2): A = [[cos t, sin t], [-sin t, cos t]]
+ * with pi/6 <= |theta| <= pi/3 or 2 pi/3 <= |theta| <= 5 pi/6, so that
+ * min(|sin|, |cos|) >= 1/2; a uniform selects t = tan(theta/2) and
+ *     cos theta = (1 - t^2) / (1 + t^2),  sin theta = 2 t / (1 + t^2).
+ * Reading (the paper writes |theta| for the first range and theta for the
+ * second): both ranges for either sign of theta.  One uniform U per pass,
+ * drawn after the strides and offsets: its top two bits pick the range --
+ * t in [2 - sqrt 3, 1/sqrt 3] (theta in [pi/6, pi/3]), [sqrt 3, 2 + sqrt 3]
+ * (theta in [2 pi/3, 5 pi/6]), or their negatives -- and its low 30 bits
+ * place t uniformly in it: t = lo + (hi - lo) (U mod 2^30) 2^-30.
+ * ------------------------------------------------------------------------ */
+void orc_draw_rotation(uint64_t *state, double *cs, double *sn)
+{
+    uint32_t u = orc_lcg_next(state);
+    double r3 = sqrt(3.0);
+    double lo, hi;
+    if (((u >> 30) & 1u) == 0) {
+        lo = 2.0 - r3;
+        hi = r3 / 3.0;
+    } else {
+        lo = r3;
+        hi = 2.0 + r3;
+    }
+    double f = (double)(u & 0x3FFFFFFFu) * (1.0 / 1073741824.0);
+    double t = lo + (hi - lo) * f;
+    if (u >> 31)
+        t = -t;
+    double t2 = t * t;
+    double den = 1.0 + t2;
+    *cs = (1.0 - t2) / den;
+    *sn = (t + t) / den;
+}
+
+/* One RANN4 pass (Eq. 1 with n = 2): x'_j = C g0 + S g1, y'_j = C g1 - S g0,
+ * g0 = x[(alpha j + gamma) mod N], g1 = y[(beta j + delta) mod N], where the
+ * chi-squared scale is folded into the rotation: C = c cos theta and
+ * S = c sin theta, rounded once to the pool's precision. */
+void orc_pass_rot32(int64_t N, const float *x, float *y, const int32_t *alpha,
+                    const int64_t *gamma, float C, float S)
+{
+    for (int64_t j = 0; j < N; j++) {
+        uint64_t i0 = ((uint64_t)alpha[0] * (uint64_t)j + (uint64_t)gamma[0]) % (uint64_t)N;
+        uint64_t i1 = ((uint64_t)alpha[1] * (uint64_t)j + (uint64_t)gamma[1]) % (uint64_t)N;
+        float g0 = x[(int64_t)i0], g1 = x[N + (int64_t)i1];
+        float a = C * g0, b = S * g1;
+        float d = C * g1, e = S * g0;
+        y[j] = a + b;
+        y[N + j] = d - e;
+    }
+}
+
+void orc_pass_rot64(int64_t N, const double *x, double *y, const int32_t *alpha,
+                    const int64_t *gamma, double C, double S)
+{
+    for (int64_t j = 0; j < N; j++) {
+        uint64_t i0 = ((uint64_t)alpha[0] * (uint64_t)j + (uint64_t)gamma[0]) % (uint64_t)N;
+        uint64_t i1 = ((uint64_t)alpha[1] * (uint64_t)j + (uint64_t)gamma[1]) % (uint64_t)N;
+        double g0 = x[(int64_t)i0], g1 = x[N + (int64_t)i1];
+        double a = C * g0, b = S * g1;
+        double d = C * g1, e = S * g0;
+        y[j] = a + b;
+        y[N + j] = d - e;
     }
 }
 
@@ -508,8 +578,10 @@ static void orc_finalise(orc_gen *g)
 
 orc_gen *orc_create(int n, int64_t N, uint32_t seed, uint32_t stream, double frac, int mode)
 {
-    if ((n != 4 && n != 8) || N < 4 || (int64_t)n * N > ((int64_t)1 << 30))
+    if ((n != 2 && n != 4 && n != 8) || N < 4 || (int64_t)n * N > ((int64_t)1 << 30))
         return NULL;
+    if (n == 2 && (mode & ORC_SIGNS))
+        return NULL; /* RANN4 draws its own rotation each pass */
     int chi = (mode & ORC_CHI_WH) != 0;
     int msigns = (mode & ORC_SIGNS) != 0;
     mode &= ~(ORC_CHI_WH | ORC_SIGNS);
@@ -609,7 +681,15 @@ int orc_pass(orc_gen *g)
      * per pass; its top n bits are the sign pattern of D_k */
     g->st.signs = g->msigns ? orc_lcg_next(&g->lcg) >> (32 - g->n) : 0u;
     int src = g->cur, dst = 1 - g->cur;
-    if (g->mode == ORC_FP32)
+    if (g->n == 2) {
+        orc_draw_rotation(&g->lcg, &g->st.rot_c, &g->st.rot_s);
+        if (g->mode == ORC_FP32)
+            orc_pass_rot32(g->N, g->p32[src], g->p32[dst], g->st.alpha, g->st.gamma,
+                           (float)(g->st.c * g->st.rot_c), (float)(g->st.c * g->st.rot_s));
+        else
+            orc_pass_rot64(g->N, g->p64[src], g->p64[dst], g->st.alpha, g->st.gamma,
+                           g->st.c * g->st.rot_c, g->st.c * g->st.rot_s);
+    } else if (g->mode == ORC_FP32)
         orc_pass_explicit32(g->n, g->N, g->p32[src], g->p32[dst], g->st.alpha, g->st.gamma,
                             g->st.c32, g->st.signs);
     else

@@ -58,6 +58,7 @@ typedef struct {
     int64_t R;             /* values returned per pass                       */
     int64_t cursor;        /* next returned index in the current pool        */
     uint32_t signs;        /* sign pattern of the most recent pass (ORC_SIGNS) */
+    double rot_c, rot_s;   /* cos and sin of the most recent pass's rotation (n = 2) */
 } orc_stats;
 
 /* ---- building blocks (exposed so the tests can pin each one) ---------- */
@@ -80,6 +81,12 @@ void orc_pass_explicit32(int n, int64_t N, const float *x, float *y,
                          const int32_t *alpha, const int64_t *gamma, float c, uint32_t signs);
 void orc_pass_explicit64(int n, int64_t N, const double *x, double *y,
                          const int32_t *alpha, const int64_t *gamma, double c, uint32_t signs);
+/* n = 2 (RANN4): the rotation of one pass, and a pass with the scaled rotation */
+void orc_draw_rotation(uint64_t *state, double *cs, double *sn);
+void orc_pass_rot32(int64_t N, const float *x, float *y, const int32_t *alpha,
+                    const int64_t *gamma, float C, float S);
+void orc_pass_rot64(int64_t N, const double *x, double *y, const int32_t *alpha,
+                    const int64_t *gamma, double C, double S);
 /* exact sum of squares of an FP32 pool: returns 0/1 "bad" flag */
 int orc_sumsq32(const float *pool, int64_t nu, uint64_t *q_lo, uint64_t *q_hi);
 int orc_sumsq64(const double *pool, int64_t nu, uint64_t *q_lo, uint64_t *q_hi);
