@@ -104,6 +104,7 @@ typedef struct {
                              counted whether or not timing is on                         */
     uint32_t signs;       /* sign pattern of the most recent pass (WALLACE_MATRIX_SIGNS;
                              bit i: sub-vector i negated before A)                        */
+    double rot_c, rot_s;  /* n = 2: cos and sin of the most recent pass's rotation        */
 } wallace_stats_t;
 
 /*

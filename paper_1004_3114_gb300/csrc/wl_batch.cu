@@ -173,8 +173,7 @@ cudaError_t launch_graph(wallace_batch_t *b, const BatchArgs &args)
     const int ctas = b->sm_count * std::min(b->tune.ctas_per_sm, b->max_ctas_per_sm);
     BatchArgs a = args;
     void *params[] = {&a};
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof(kp));
+    cudaKernelNodeParams kp = {};
     kp.func = (void *)batch_kernel;
     kp.gridDim = dim3(ctas);
     kp.blockDim = dim3(BT_THREADS);
@@ -190,8 +189,7 @@ cudaError_t launch_graph(wallace_batch_t *b, const BatchArgs &args)
         e = cudaGraphCreate(&b->graph, 0);
         if (e != cudaSuccess)
             return e;
-        cudaMemsetParams mp;
-        memset(&mp, 0, sizeof(mp));
+        cudaMemsetParams mp = {};
         mp.dst = b->d_queue;
         mp.value = 0;
         mp.elementSize = 4;

@@ -265,10 +265,12 @@ int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, doubl
     if (!out)
         return WALLACE_EINVAL;
     *out = nullptr;
-    if ((n != 4 && n != 8) || N < 4 || (int64_t)n * N > ((int64_t)1 << 30))
+    if ((n != 2 && n != 4 && n != 8) || N < 4 || (int64_t)n * N > ((int64_t)1 << 30))
         return WALLACE_EINVAL;
     const int opts = ((mode & WALLACE_CHI_WH) ? 1 : 0) | ((mode & WALLACE_MATRIX_SIGNS) ? 2 : 0);
     mode &= ~(WALLACE_CHI_WH | WALLACE_MATRIX_SIGNS);
+    if (n == 2 && (opts & 2))
+        return WALLACE_EINVAL;   // RANN4 draws its own rotation each pass
     if (!(frac > 0.0 && frac <= 1.0) || (mode != WALLACE_FP32 && mode != WALLACE_FP64POOL))
         return WALLACE_EINVAL;
     const int64_t nu = (int64_t)n * N;
@@ -552,6 +554,8 @@ int wallace_stats(wallace_t *h, wallace_stats_t *out)
     out->kernel_ms = h->kernel_ms;
     out->kernel_launches = h->kernel_launches;
     out->signs = s.last.signs;
+    out->rot_c = s.last.rcos;
+    out->rot_s = s.last.rsin;
     out->launches = h->launches;
     return out->status;
 }

@@ -24,6 +24,10 @@ struct WlParams {
     float c32;
     uint32_t signs;     // bit i: sub-vector i negated before A (0 for the fixed A)
     double c64;
+    // n = 2 (RANN4): the pass's rotation, and with the scale folded in
+    // (C = c cos, S = c sin, rounded once to each precision)
+    double rcos, rsin, rc64, rs64;
+    float rc32, rs32;
 };
 
 // Strides and offsets of one pass.
@@ -32,6 +36,7 @@ struct WlStrides {
     int64_t gamma[8];
     uint32_t signs;
     uint32_t pad_;
+    double rcos, rsin;   // n = 2: the pass's rotation
 };
 
 // One generator's device state.  The finaliser of a pass writes `next`;
@@ -138,23 +143,28 @@ __device__ __forceinline__ bool wl_stride_free(int32_t a, int64_t N, const int32
 // shares none of its prime factors among 3, 5, 7: one bit per prime.  This
 // keeps the finaliser (one thread, between two passes) free of Euclid's
 // algorithm except in the rare fallback.
+//
+// n = 2 is RANN4 itself (Section 8): alpha from {3, 5} for x and beta from
+// {7, 11} for y, drawn the same way; 11's factor is not among the three bits,
+// so those tables are checked against N by Euclid.
 __device__ inline void wl_draw_params(int n, int64_t N, uint64_t &s, int32_t *alpha, int64_t *gamma)
 {
     const int32_t div45[5] = {3, 5, 9, 15, 45};
     const uint8_t fac45[5] = {1, 2, 1, 3, 3};            // bit 0: 3 | a, bit 1: 5 | a, bit 2: 7 | a
     const int32_t div315[11] = {3, 5, 7, 9, 15, 21, 35, 45, 63, 105, 315};
     const uint8_t fac315[11] = {1, 2, 4, 1, 3, 5, 6, 3, 5, 7, 7};
-    const int32_t *cand = n == 4 ? div45 : div315;
-    const uint8_t *fac = n == 4 ? fac45 : fac315;
-    const int ncand = n == 4 ? 5 : 11;
+    const int32_t rann4[2][2] = {{3, 5}, {7, 11}};
     const uint64_t uN = (uint64_t)N;
     const uint32_t nfac = (uN % 3u == 0 ? 1u : 0u) | (uN % 5u == 0 ? 2u : 0u) | (uN % 7u == 0 ? 4u : 0u);
     for (int i = 0; i < n; i++) {
+        const int32_t *cand = n == 4 ? div45 : (n == 8 ? div315 : rann4[i]);
+        const uint8_t *fac = n == 4 ? fac45 : fac315;
+        const int ncand = n == 4 ? 5 : (n == 8 ? 11 : 2);
         const uint32_t u = wl_lcg_step(s);
         int32_t freec[11];
         int nf = 0;
         for (int k = 0; k < ncand; k++) {
-            if (fac[k] & nfac)
+            if (n == 2 ? wl_gcd(cand[k], N) != 1 : (fac[k] & nfac) != 0)
                 continue;
             bool used = false;
             for (int t = 0; t < i; t++)
@@ -177,6 +187,20 @@ __device__ inline void wl_draw_params(int n, int64_t N, uint64_t &s, int32_t *al
 }
 
 // ---- the transform (Section 2; A = (2/n)J - I, scaled by c) ----------------
+// n = 2 (RANN4, Section 8): x' = C g0 + S g1, y' = C g1 - S g0 with the
+// scale folded into the rotation (C = c cos theta, S = c sin theta).
+__device__ __forceinline__ void wl_xform2(const float *g, float C, float S, float *y)
+{
+    y[0] = __fadd_rn(__fmul_rn(C, g[0]), __fmul_rn(S, g[1]));
+    y[1] = __fsub_rn(__fmul_rn(C, g[1]), __fmul_rn(S, g[0]));
+}
+
+__device__ __forceinline__ void wl_xform2d(const double *g, double C, double S, double *y)
+{
+    y[0] = __dadd_rn(__dmul_rn(C, g[0]), __dmul_rn(S, g[1]));
+    y[1] = __dsub_rn(__dmul_rn(C, g[1]), __dmul_rn(S, g[0]));
+}
+
 __device__ __forceinline__ void wl_xform4(const float *g, float c, float *y)
 {
     float s = __fadd_rn(__fadd_rn(g[0], g[1]), __fadd_rn(g[2], g[3]));
@@ -319,11 +343,40 @@ __device__ __forceinline__ void wl_acc_read(WlDevState *st, uint64_t &lo, uint64
 // The draws of one pass into a strides slot: 2n uniforms for the strides
 // and offsets, then (per-pass sign patterns on) one whose top n bits are
 // the pattern (Section 3 prefers a different orthogonal matrix each pass).
+//
+// RANN4's rotation (n = 2, Section 8): one more uniform U; its top bit is the
+// sign of theta, the next bit the range (pi/6..pi/3 or 2pi/3..5pi/6), and the
+// low 30 bits place t = tan(theta/2) uniformly in [2 - sqrt 3, 1/sqrt 3] or
+// [sqrt 3, 2 + sqrt 3]; cos = (1 - t^2)/(1 + t^2), sin = 2t/(1 + t^2).
+__device__ inline void wl_draw_rotation(uint64_t &s, double &cs, double &sn)
+{
+    const uint32_t u = wl_lcg_step(s);
+    const double r3 = __dsqrt_rn(3.0);
+    double lo, hi;
+    if (((u >> 30) & 1u) == 0) {
+        lo = __dsub_rn(2.0, r3);
+        hi = __ddiv_rn(r3, 3.0);
+    } else {
+        lo = r3;
+        hi = __dadd_rn(2.0, r3);
+    }
+    const double f = __dmul_rn((double)(u & 0x3FFFFFFFu), 1.0 / 1073741824.0);
+    double t = __dadd_rn(lo, __dmul_rn(__dsub_rn(hi, lo), f));
+    if (u >> 31)
+        t = -t;
+    const double t2 = __dmul_rn(t, t);
+    const double den = __dadd_rn(1.0, t2);
+    cs = __ddiv_rn(__dsub_rn(1.0, t2), den);
+    sn = __ddiv_rn(__dadd_rn(t, t), den);
+}
+
 __device__ __forceinline__ void wl_draw_pass(int n, int64_t N, uint64_t &s, WlStrides &slot,
                                              int msigns)
 {
     wl_draw_params(n, N, s, slot.alpha, slot.gamma);
     slot.signs = msigns ? wl_lcg_step(s) >> (32 - n) : 0u;
+    if (n == 2)
+        wl_draw_rotation(s, slot.rcos, slot.rsin);
 }
 
 // Negate g when bit i of the pattern is set (a sign-bit flip: exact).
@@ -349,6 +402,8 @@ __device__ inline void wl_advance_strides(WlDevState *st, int n, int64_t N, uint
         st->next.gamma[i] = cur.gamma[i];
     }
     st->next.signs = cur.signs;
+    st->next.rcos = cur.rcos;
+    st->next.rsin = cur.rsin;
     st->lcg_rep = rep;
     st->lcg_pend = s;
     wl_draw_pass(n, N, s, st->ahead[(k + 1) & 1], msigns);
@@ -439,6 +494,13 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
     }
     st->next.c64 = c;
     st->next.c32 = __double2float_rn(c);
+    if (n == 2) {
+        // the scale folded into the next pass's rotation
+        st->next.rc64 = __dmul_rn(c, st->next.rcos);
+        st->next.rs64 = __dmul_rn(c, st->next.rsin);
+        st->next.rc32 = __double2float_rn(st->next.rc64);
+        st->next.rs32 = __double2float_rn(st->next.rs64);
+    }
     st->acc0 = 0;
     st->acc1 = 0;
     st->acc2 = 0;

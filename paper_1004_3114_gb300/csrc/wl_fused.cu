@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
     __shared__ uint64_t red[3 * (FU_THREADS / 32)];
     __shared__ int32_t s_alpha[NSUB];
     __shared__ int32_t s_gamma[NSUB];
-    __shared__ T s_c;
+    __shared__ T s_c, s_rC, s_rS;
     __shared__ uint32_t s_signs;
     const int tid = threadIdx.x;
     const int nu = NSUB * (int)N;
@@ -46,14 +46,19 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
                 s_alpha[i] = st->next.alpha[i];
                 s_gamma[i] = (int32_t)st->next.gamma[i];
             }
-            if constexpr (sizeof(T) == 8)
+            if constexpr (sizeof(T) == 8) {
                 s_c = st->next.c64;
-            else
+                s_rC = st->next.rc64;
+                s_rS = st->next.rs64;
+            } else {
                 s_c = st->next.c32;
+                s_rC = st->next.rc32;
+                s_rS = st->next.rs32;
+            }
             s_signs = st->next.signs;
         }
         __syncthreads();
-        const T c = s_c;
+        const T c = s_c, rC = s_rC, rS = s_rS;
         const uint32_t signs = s_signs;
         const int take = (int)(pass + 1 < passes ? R : last_take);
         T *o = out + pass * R;
@@ -75,12 +80,16 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
                     idx[i] -= (int)N;
             }
             if constexpr (sizeof(T) == 8) {
-                if constexpr (NSUB == 4)
+                if constexpr (NSUB == 2)
+                    wl_xform2d(g, rC, rS, y);
+                else if constexpr (NSUB == 4)
                     wl_xform4d(g, c, y);
                 else
                     wl_xform8d(g, c, y);
             } else {
-                if constexpr (NSUB == 4)
+                if constexpr (NSUB == 2)
+                    wl_xform2(g, rC, rS, y);
+                else if constexpr (NSUB == 4)
                     wl_xform4(g, c, y);
                 else
                     wl_xform8(g, c, y);
@@ -147,7 +156,7 @@ bool wl_fused_supported(int n, int64_t N, int fp64, int64_t *smem_bytes)
     int64_t bytes = 2 * (fp64 ? 8 : 4) * (int64_t)n * N;
     if (smem_bytes)
         *smem_bytes = bytes;
-    return (n == 4 || n == 8) && N >= 4 && bytes <= FU_SMEM_MAX;
+    return (n == 2 || n == 4 || n == 8) && N >= 4 && bytes <= FU_SMEM_MAX;
 }
 
 cudaError_t wl_launch_fused(void *pool_cur, void *pool_other, int fp64, int n, int64_t N,
@@ -158,6 +167,11 @@ cudaError_t wl_launch_fused(void *pool_cur, void *pool_other, int fp64, int n, i
     (void)pool_other;
     if (passes <= 0)
         return cudaSuccess;
+    if (n == 2)
+        return fp64 ? launch_one<2, double>(pool_cur, pool_cur, N, Np, st, passes, R, last_take,
+                                            out, mu, sigma, stream)
+                    : launch_one<2, float>(pool_cur, pool_cur, N, Np, st, passes, R, last_take,
+                                           out, mu, sigma, stream);
     if (n == 4)
         return fp64 ? launch_one<4, double>(pool_cur, pool_cur, N, Np, st, passes, R, last_take,
                                             out, mu, sigma, stream)

@@ -32,6 +32,8 @@ __global__ void __launch_bounds__(256) gather_kernel(WlPassArgs a)
     T *out = (T *)a.out;
     const T mu = (T)a.mu, sigma = (T)a.sigma;
     const uint32_t signs = st->next.signs;
+    const T rC = f64 ? (T)st->next.rc64 : (T)st->next.rc32;   // n = 2: rotation with the scale
+    const T rS = f64 ? (T)st->next.rs64 : (T)st->next.rs32;
     uint64_t lo = 0, hi = 0;
     uint32_t bad = 0;
     for (; j < N; j += G) {
@@ -44,12 +46,16 @@ __global__ void __launch_bounds__(256) gather_kernel(WlPassArgs a)
                 idx[i] -= N;
         }
         if constexpr (sizeof(T) == 8) {
-            if constexpr (NSUB == 4)
+            if constexpr (NSUB == 2)
+                wl_xform2d(g, rC, rS, y);
+            else if constexpr (NSUB == 4)
                 wl_xform4d(g, c, y);
             else
                 wl_xform8d(g, c, y);
         } else {
-            if constexpr (NSUB == 4)
+            if constexpr (NSUB == 2)
+                wl_xform2(g, rC, rS, y);
+            else if constexpr (NSUB == 4)
                 wl_xform4(g, c, y);
             else
                 wl_xform8(g, c, y);
@@ -100,7 +106,12 @@ cudaError_t wl_launch_gather(const WlPassArgs &a, int fp64, int sm_count, cudaSt
     int64_t want = (a.N + 255) / 256;
     int64_t cap = (int64_t)sm_count * 8;
     int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    if (a.n == 4) {
+    if (a.n == 2) {
+        if (fp64)
+            gather_kernel<2, double><<<grid, 256, 0, stream>>>(a);
+        else
+            gather_kernel<2, float><<<grid, 256, 0, stream>>>(a);
+    } else if (a.n == 4) {
         if (fp64)
             gather_kernel<4, double><<<grid, 256, 0, stream>>>(a);
         else

@@ -31,7 +31,6 @@
 // WALLACE_ETIMEOUT in the state, stops issuing work, waits (bounded) for its
 // copies still in flight, and leaves.
 #include <math.h>
-#include <string.h>
 
 #include "wl_common.cuh"
 #include "wl_launch.h"
@@ -531,8 +530,7 @@ cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, int signs, cudaStre
             return e;
         g_tma_configured[signs ? 1 : 0] = true;
     }
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(sm_count);
     cfg.blockDim = dim3(TM_THREADS);
     cfg.dynamicSmemBytes = smem;

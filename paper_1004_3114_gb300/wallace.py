@@ -37,7 +37,7 @@ class Stats(C.Structure):
         ("status", C.c_int32), ("bad", C.c_int32), ("lcg", C.c_uint64),
         ("alpha", C.c_int32 * 8), ("gamma", C.c_int64 * 8), ("R", C.c_int64),
         ("cursor", C.c_int64), ("kernel_ms", C.c_double), ("kernel_launches", C.c_int64), ("launches", C.c_int64),
-        ("signs", C.c_uint32),
+        ("signs", C.c_uint32), ("rot_c", C.c_double), ("rot_s", C.c_double),
     ]
 
     @property

@@ -47,6 +47,7 @@ def assert_stats_equal(g, o, what=""):
     assert list(gs.alpha[:g.n]) == list(os_.alpha[:g.n]), what
     assert list(gs.gamma[:g.n]) == list(os_.gamma[:g.n]), what
     assert gs.signs == os_.signs, what
+    assert gs.rot_c == os_.rot_c and gs.rot_s == os_.rot_s, what
     assert gs.status == os_.status, what
 
 
@@ -330,3 +331,39 @@ def test_sign_patterns_bit_exact(orc, n, N, variant, mode):
         assert_stats_equal(g, o, f"pass {k + 1}")
         seen.add(g.stats().signs)
     assert len(seen) > 1
+
+
+@pytest.mark.parametrize("N,frac,variant,mode", [
+    (256, 1 / 3, W.VARIANT_AUTO, W.FP32),          # shared-memory pool
+    (1 << 14, 1 / 3, W.VARIANT_AUTO, W.FP32),      # global-memory gather
+    (20000, 1 / 3, W.VARIANT_GATHER, W.FP32),
+    (3 * 1024, 0.5, W.VARIANT_AUTO, W.FP32),       # 3 | N: alpha = 5 every pass
+    (15 * 64, 1.0, W.VARIANT_GATHER, W.FP32),      # 15 | N: coprimality fallback
+    (1 << 12, 1 / 3, W.VARIANT_AUTO, W.FP64POOL),
+    (4096, 1 / 3, W.VARIANT_FUSED, W.FP32 | W.CHI_WH),
+])
+def test_rann4_bit_exact(orc, N, frac, variant, mode):
+    """RANN4 itself (n = 2, Section 8): strides from {3,5} and {7,11} and a
+    rotation drawn each pass, with the scale folded into it."""
+    fp = mode & ~W.CHI_WH
+    omode = (orc.FP32 if fp == W.FP32 else orc.FP64) | (orc.CHI_WH if mode & W.CHI_WH else 0)
+    g = W.Wallace(2, N, 23, frac, mode=mode)
+    g.set_variant(variant)
+    o = orc.Generator(2, N, 23, frac, mode=omode)
+    if mode & W.CHI_WH:
+        g.set_restart(4)
+        o.set_restart(4)
+    assert_stats_equal(g, o, "initial pool")
+    for k in range(6):
+        got = fill_dev(g, g.R)
+        ref = o.fill(g.R)
+        assert_same(got, ref, f"pass {k + 1} output")
+        assert_stats_equal(g, o, f"pass {k + 1}")
+        if fp == W.FP32:
+            assert_same(g.pool(), o.pool32(), f"pass {k + 1} pool")
+    assert_same(fill_dev(g, 7 * g.R + 5), o.fill(7 * g.R + 5), "long fill")
+
+
+def test_rann4_rejects_sign_patterns():
+    with pytest.raises(W.WallaceError):
+        W.Wallace(2, 256, 1, 1.0, mode=W.FP32 | W.MATRIX_SIGNS)
