@@ -537,6 +537,55 @@ def boxmuller_bench(count: int = 1 << 28, reps: int = 20):
           flush=True)
 
 
+def variant_bench(steps: int = 2000, warmup: int = 5):
+    """The other generator forms on the default pool size (2^26 values), one
+    pass per step as in the default line: RANN4 itself (n = 2, N = 2^25,
+    frac = 1/3 as RANN4's f = 3), and n = 4 with a random sign pattern per
+    pass, with the Wilson-Hilferty sample, and with restarts every 1000 N / R
+    passes (Section 5)."""
+    import torch
+    from paper_1004_3114_gb300 import wallace as W
+    peak, kind = hbm_peak()
+    cases = [
+        ("rann4_n2", 2, 1 << 25, 1 / 3, W.FP32, 0),
+        ("n4_signs", 4, 1 << 24, 0.5, W.FP32 | W.MATRIX_SIGNS, 0),
+        ("n4_wilson_hilferty", 4, 1 << 24, 0.5, W.FP32 | W.CHI_WH, 0),
+        ("n4_restart", 4, 1 << 24, 0.5, W.FP32, -1),
+    ]
+    res = {}
+    stream = torch.cuda.Stream()
+    for name, n, N, frac, mode, restart in cases:
+        g = W.Wallace(n, N, SEED, frac, mode=mode, stream=stream)
+        if restart:
+            g.set_restart(max(1, (1000 * N) // g.R))
+        out = torch.empty(g.R, dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                g.fill(out)
+        g.sync()
+        s0 = g.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(steps):
+                g.fill(out)
+            e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        s1 = g.stats()
+        nu = n * N
+        bytes_pass = 8 * nu + 4 * g.R
+        launches = s1.launches - s0.launches
+        res[name] = {"n": n, "N": N, "frac": frac, "value": steps * g.R / (ms * 1e-3),
+                     "ms_per_pass": ms / steps, "launches_per_pass": launches / steps,
+                     "roofline_frac": bytes_pass * steps / (ms * 1e-3) / 1e9 / peak,
+                     "status": int(g.sync())}
+        g.close()
+        del out
+    print(json.dumps({"metric": "generator variants: N(0,1) variates/s", "unit": UNIT, "peak_gbs": peak,
+                      "peak_kind": kind, "steps": steps, "cases": res}), flush=True)
+
+
 def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
                   power_of_two: bool = False):
     """4096 generators, n = 4, N log-uniform on [2^8, 2^18], seeds 0..4095,
@@ -666,6 +715,8 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="4096 uneven generators in one persistent launch vs one handle each")
     ap.add_argument("--pow2", action="store_true", help="with --batched: power-of-two pool sizes")
+    ap.add_argument("--variants", action="store_true",
+                    help="RANN4 (n=2), per-pass sign patterns, Wilson-Hilferty and restarts on the default pool size")
     ap.add_argument("--boxmuller", action="store_true",
                     help="the Box-Muller comparison generator beside the Wallace pass")
     ap.add_argument("--small", action="store_true",
@@ -689,6 +740,9 @@ def main():
         return
     if args.boxmuller:
         boxmuller_bench()
+        return
+    if args.variants:
+        variant_bench()
         return
     if args.serve:
         serve_bench(n_requests=args.serve_requests, rate=args.serve_rate,

@@ -110,7 +110,7 @@ int pick_variant(const wallace_t *h)
     if (h->variant != WALLACE_VARIANT_AUTO)
         return h->variant;
     const int fp64 = h->mode == WALLACE_FP64POOL;
-    if (wl_tiled_supported(h->n, h->N, fp64))
+    if (wl_tiled_supported(h->n, h->N, fp64) || wl_tma_supported(h->n, h->N, fp64, h->sm_count))
         return WALLACE_VARIANT_TILED;
     if (wl_fused_supported(h->n, h->N, fp64, nullptr))
         return WALLACE_VARIANT_FUSED;
@@ -474,8 +474,11 @@ int wallace_set_variant(wallace_t *h, int variant)
     case WALLACE_VARIANT_GATHER:
         break;
     case WALLACE_VARIANT_TILED:
-    case WALLACE_VARIANT_TILED_ASYNC:
     case WALLACE_VARIANT_TILED_TMA:
+        if (!wl_tiled_supported(h->n, h->N, fp64) && !wl_tma_supported(h->n, h->N, fp64, h->sm_count))
+            return WALLACE_EINVAL;
+        break;
+    case WALLACE_VARIANT_TILED_ASYNC:
         if (!wl_tiled_supported(h->n, h->N, fp64))
             return WALLACE_EINVAL;
         break;

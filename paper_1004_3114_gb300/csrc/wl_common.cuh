@@ -576,6 +576,13 @@ __device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, int64_t
     if (threadIdx.x == 0) {
         st->next.c64 = s_c;
         st->next.c32 = __double2float_rn(s_c);
+        if (n == 2) {
+            // the scale folded into the next pass's rotation
+            st->next.rc64 = __dmul_rn(s_c, st->next.rcos);
+            st->next.rs64 = __dmul_rn(s_c, st->next.rsin);
+            st->next.rc32 = __double2float_rn(st->next.rc64);
+            st->next.rs32 = __double2float_rn(st->next.rs64);
+        }
         st->S_prev = s_S;
         st->have_prev = 1;
         st->status = vs->status | s_flag[0] | s_flag[1];

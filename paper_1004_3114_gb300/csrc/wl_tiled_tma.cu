@@ -40,8 +40,9 @@
 #define TM_PROD_WARPS 4          /* one warp issues a bulk copy only every ~80 cycles */
 #define TM_THREADS (TM_CONS_THREADS + 32 * TM_PROD_WARPS)
 #define TM_STAGES 3
-#define TM_ETARGET 2880          /* lane-times per tile: L * T <= this (T = 64 at L = 45) */
-#define TM_LMAX 45
+#define TM_ETARGET 2880          /* n = 4: lane-times per tile, L * T <= this (T = 64 at L = 45) */
+#define TM_LMAX 45               /* n = 4: strides divide 45 */
+#define TM_LMAX2 55              /* n = 2: L = alpha beta <= 5 * 11 */
 #define TM_MAXSPANS 32           /* sum_i 45 / alpha_i <= 15 + 9 + 5 + 3 */
 #define TM_MIN_N 16384
 #define TM_WAIT_CYCLES 2000000000ll   /* about one second */
@@ -50,17 +51,32 @@ namespace {
 
 __host__ __device__ constexpr int tm_stage_data_words() { return 4 * TM_ETARGET + 12 * TM_MAXSPANS; }
 __host__ __device__ constexpr int tm_stage_words() { return tm_stage_data_words() + TM_MAXSPANS; }
-__host__ __device__ constexpr int tm_common_words() { return (TM_LMAX + 1) + 4 * TM_LMAX + TM_MAXSPANS; }
+// common area: J[L + 1] (room for n = 2's 55 lanes), lane table (n * lanes <= 180), span starts
+__host__ __device__ constexpr int tm_common_words() { return (TM_LMAX2 + 1) + 4 * TM_LMAX + TM_MAXSPANS; }
 __host__ __device__ constexpr size_t tm_smem_bytes()
 {
     return sizeof(float) * (size_t)(TM_STAGES * tm_stage_words() + tm_common_words());
 }
 
-// x / d for x >= 0 and d a divisor of 45: constant divisors, so each case
-// is a multiply and shift instead of a division routine
-__device__ __forceinline__ int tm_div45(int x, int d)
+// x / d for x >= 0 and d a lane count or span count of either geometry
+// (divisors of 45; 3, 5, 7, 11 and their products for n = 2): constant
+// divisors, so each case is a multiply and shift instead of a division
+// routine
+__device__ __forceinline__ int tm_divc(int x, int d)
 {
     switch (d) {
+    case 7:
+        return x / 7;
+    case 11:
+        return x / 11;
+    case 21:
+        return x / 21;
+    case 33:
+        return x / 33;
+    case 35:
+        return x / 35;
+    case 55:
+        return x / 55;
     case 1:
         return x;
     case 3:
@@ -71,8 +87,10 @@ __device__ __forceinline__ int tm_div45(int x, int d)
         return x / 9;
     case 15:
         return x / 15;
-    default:
+    case 45:
         return x / 45;
+    default:
+        return x / d;
     }
 }
 
@@ -144,21 +162,41 @@ __device__ __forceinline__ uint64_t term32(float y, uint32_t &emax)
 // let the next pass's CTAs launch (they take SMs as this pass's CTAs leave
 // and run their own prologue meanwhile), and return this pass's scale c.
 // Every thread of the CTA calls.
-__device__ __forceinline__ float tm_wait_prev(WlDevState *st, volatile float *s_c)
+// sub-vector of span s (spans are numbered sub-vector by sub-vector)
+template <int NSUB>
+__device__ __forceinline__ int tm_sub(int s, const int *sb)
+{
+    if constexpr (NSUB == 4)
+        return (s >= sb[1]) + (s >= sb[2]) + (s >= sb[3]);
+    else
+        return s >= sb[1] ? 1 : 0;
+}
+
+// n = 2: also the scaled rotation C = c cos, S = c sin of this pass.
+__device__ __forceinline__ float tm_wait_prev(WlDevState *st, volatile float *s_c, float &C, float &S)
 {
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    if (threadIdx.x == 0)
-        *s_c = st->next.c32;
+    if (threadIdx.x == 0) {
+        s_c[0] = st->next.c32;
+        s_c[1] = st->next.rc32;
+        s_c[2] = st->next.rs32;
+    }
     __syncthreads();
-    return *s_c;
+    C = s_c[1];
+    S = s_c[2];
+    return s_c[0];
 }
 
 // SG: the generator draws a sign pattern each pass (matrix A D_k); the
-// fixed-matrix kernel has no trace of it.
-template <bool SG>
+// fixed-matrix kernel has no trace of it.  NSUB: 4 (A = J/2 - I) or 2
+// (RANN4's rotation, strides from {3,5} and {7,11}: L = alpha beta <= 55 lanes,
+// T = 5760 / L lane times per tile).
+template <bool SG, int NSUB>
 __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double rnu)
 {
+    constexpr int LMAXN = NSUB == 4 ? TM_LMAX : TM_LMAX2;     // lanes, and lane-table row stride
+    constexpr int ET = NSUB == 4 ? TM_ETARGET : 2 * TM_ETARGET;   // lane-times per tile, at most
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar_full[TM_STAGES];
     __shared__ __align__(8) uint64_t bar_empty[TM_STAGES];
@@ -180,84 +218,95 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
     // one warp per CTA reads the strides and shares them: every CTA starts at
     // once, and 600 threads each loading the same few words would queue on
     // one L2 slice
-    __shared__ int64_t s_gam[4];
-    __shared__ int s_alpha[4];
+    __shared__ int64_t s_gam[NSUB];
+    __shared__ int s_alpha[NSUB];
     __shared__ uint32_t s_signs;
-    __shared__ volatile float s_c;
+    __shared__ volatile float s_c[3];
     if (warp == 0) {
         const WlStrides *cur = &st->ahead[a.pass & 1];
-        if (lane < 4)
+        if (lane < NSUB)
             s_alpha[lane] = __ldcg(&cur->alpha[lane]);
-        else if (lane < 8)
-            s_gam[lane - 4] = (int64_t)__ldcg((const long long *)&cur->gamma[lane - 4]);
-        else if (lane == 8)
+        else if (lane < 2 * NSUB)
+            s_gam[lane - NSUB] = (int64_t)__ldcg((const long long *)&cur->gamma[lane - NSUB]);
+        else if (lane == 2 * NSUB)
             s_signs = SG ? __ldcg(&cur->signs) : 0u;
     }
     __syncthreads();
     const uint32_t signs = SG ? s_signs : 0u;
-    int alpha[4];
-    int64_t gam[4];
+    int alpha[NSUB];
+    int64_t gam[NSUB];
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
+    for (int i = 0; i < NSUB; i++) {
         alpha[i] = s_alpha[i];
         gam[i] = s_gam[i];
     }
-    float c;
+    float c, rC = 0.f, rS = 0.f;
     float *out = (float *)a.out;
     const float mu = (float)a.mu, sigma = (float)a.sigma;
     const int64_t w0 = a.w0, w1 = a.w1;
 
-    // L = lcm of the strides when all divide 45 (3^e3 5^e5); any other stride
-    // (the coprimality fallback) sends the pass to the plain gather below
-    int e3 = 0, e5 = 0;
-    bool div45 = true;
+    // n = 4: L = lcm of the strides when all divide 45 (3^e3 5^e5).  n = 2:
+    // L = alpha beta for alpha in {3, 5}, beta in {7, 11}.  Any other stride
+    // (the coprimality fallback) sends the pass to the plain gather below.
+    int L;
+    bool tileable;
+    if constexpr (NSUB == 4) {
+        int e3 = 0, e5 = 0;
+        tileable = true;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const int al = alpha[i];
-        if (al == 3 || al == 15)
-            e3 = max(e3, 1);
-        if (al == 9 || al == 45)
-            e3 = 2;
-        if (al == 5 || al == 15 || al == 45)
-            e5 = 1;
-        div45 &= al == 3 || al == 5 || al == 9 || al == 15 || al == 45;
+        for (int i = 0; i < 4; i++) {
+            const int al = alpha[i];
+            if (al == 3 || al == 15)
+                e3 = max(e3, 1);
+            if (al == 9 || al == 45)
+                e3 = 2;
+            if (al == 5 || al == 15 || al == 45)
+                e5 = 1;
+            tileable &= al == 3 || al == 5 || al == 9 || al == 15 || al == 45;
+        }
+        L = tileable ? (e3 == 2 ? 9 : (e3 == 1 ? 3 : 1)) * (e5 ? 5 : 1) : TM_LMAX + 1;
+    } else {
+        tileable = (alpha[0] == 3 || alpha[0] == 5) && (alpha[1] == 7 || alpha[1] == 11);
+        L = tileable ? alpha[0] * alpha[1] : TM_LMAX2 + 1;
     }
-    const int L = div45 ? (e3 == 2 ? 9 : (e3 == 1 ? 3 : 1)) * (e5 ? 5 : 1) : TM_LMAX + 1;
-    int m[4], sb[5];
+    int m[NSUB], sb[NSUB + 1];
     sb[0] = 0;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        m[i] = div45 ? tm_div45(L, alpha[i]) : 0;
+    for (int i = 0; i < NSUB; i++) {
+        m[i] = tileable ? tm_divc(L, alpha[i]) : 0;
         sb[i + 1] = sb[i] + m[i];
     }
-    const int nspans = sb[4];
+    const int nspans = sb[NSUB];
 
     uint64_t lo = 0, hi = 0;
     uint32_t bad = 0;
 
-    if (L > TM_LMAX || nspans > TM_MAXSPANS || N < TM_MIN_N || (N & 3)) {
+    if (!tileable || nspans > TM_MAXSPANS || N < TM_MIN_N || (N & 3)) {
         // plain strided gather for this pass (strides with a larger lcm)
-        c = tm_wait_prev(st, &s_c);
+        c = tm_wait_prev(st, s_c, rC, rS);
         const int64_t G = (int64_t)gridDim.x * blockDim.x;
         int64_t j = (int64_t)blockIdx.x * blockDim.x + tid;
-        int64_t idx[4], stp[4];
+        int64_t idx[NSUB], stp[NSUB];
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
+        for (int i = 0; i < NSUB; i++) {
             idx[i] = (int64_t)(((uint64_t)alpha[i] * (uint64_t)(j < N ? j : 0) + (uint64_t)gam[i]) % (uint64_t)N);
             stp[i] = (int64_t)(((uint64_t)alpha[i] * (uint64_t)G) % (uint64_t)N);
         }
         for (; j < N; j += G) {
-            float g[4], y[4];
+            float g[NSUB], y[NSUB];
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
+            for (int i = 0; i < NSUB; i++) {
                 g[i] = wl_sgn(src[i * Np + idx[i]], signs, i);
                 idx[i] += stp[i];
                 if (idx[i] >= N)
                     idx[i] -= N;
             }
-            wl_xform4(g, c, y);
+            if constexpr (NSUB == 4)
+                wl_xform4(g, c, y);
+            else
+                wl_xform2(g, rC, rS, y);
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
+            for (int k = 0; k < NSUB; k++) {
                 dst[k * Np + j] = y[k];
                 wl_add128(lo, hi, wl_term32(y[k], bad), 0);
                 int64_t q = k * N + j;
@@ -266,33 +315,34 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
             }
         }
     } else {
-        const int T = tm_div45(TM_ETARGET, L);
-        int SL[4], slot0[4];
+        // n = 2: whole 64-time chunks (a consumer thread takes t and t + 32)
+        const int T = NSUB == 4 ? tm_divc(ET, L) : (tm_divc(ET, L) & ~63);
+        int SL[NSUB], slot0[NSUB];
         slot0[0] = 0;
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
+        for (int i = 0; i < NSUB; i++) {
             SL[i] = (alpha[i] * T + 8 + 3) & ~3;   // 16-byte aligned slots; wrap copies need +6
-            if (i < 3)
+            if (i < NSUB - 1)
                 slot0[i + 1] = slot0[i] + m[i] * SL[i];
         }
         float *stage0 = smem;
         int *common = (int *)(smem + TM_STAGES * tm_stage_words());
         int *J = common;
-        int *lanebase = J + (TM_LMAX + 1);
+        int *lanebase = J + (TM_LMAX2 + 1);
         int *spanC = lanebase + 4 * TM_LMAX;
 
         // ceil(l N / L) and ceil(p N / m_i) as l (N / L) + ceil(l (N mod L) / L):
         // 32-bit arithmetic (N < 2^31, l (N mod L) < L^2)
         const int N32 = (int)N;
         for (int l = tid; l <= L; l += TM_THREADS) {
-            const int qN = tm_div45(N32, L), rN = N32 - qN * L;
-            J[l] = l * qN + tm_div45(l * rN + L - 1, L);
+            const int qN = tm_divc(N32, L), rN = N32 - qN * L;
+            J[l] = l * qN + tm_divc(l * rN + L - 1, L);
         }
         for (int s = tid; s < nspans; s += TM_THREADS) {
-            const int i = (s >= sb[1]) + (s >= sb[2]) + (s >= sb[3]);
+            const int i = tm_sub<NSUB>(s, sb);
             const int p = s - sb[i], mi = m[i];
-            const int qN = tm_div45(N32, mi), rN = N32 - qN * mi;
-            spanC[s] = p * qN + tm_div45(p * rN + mi - 1, mi);
+            const int qN = tm_divc(N32, mi), rN = N32 - qN * mi;
+            spanC[s] = p * qN + tm_divc(p * rN + mi - 1, mi);
         }
         if (tid == 0) {
             for (int s = 0; s < TM_STAGES; s++) {
@@ -307,15 +357,15 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
         __syncthreads();
         // per lane and sub-vector: slot offset of the lane's first value,
         // packed with the index of the span that holds it (span < 32)
-        for (int e = tid; e < 4 * L; e += TM_THREADS) {
-            int i = tm_div45(e, L), l = e - i * L;
-            int w = tm_div45(l, m[i]), p = l - w * m[i];
+        for (int e = tid; e < NSUB * L; e += TM_THREADS) {
+            int i = tm_divc(e, L), l = e - i * L;
+            int w = tm_divc(l, m[i]), p = l - w * m[i];
             int64_t r = (int64_t)alpha[i] * J[l] - (int64_t)w * N - spanC[sb[i] + p];
-            lanebase[i * TM_LMAX + l] = ((slot0[i] + p * SL[i] + (int)r) << 5) | (sb[i] + p);
+            lanebase[i * LMAXN + l] = ((slot0[i] + p * SL[i] + (int)r) << 5) | (sb[i] + p);
         }
         __syncthreads();
-        c = tm_wait_prev(st, &s_c);
-        const int maxlen = tm_div45(N32 + L - 1, L);
+        c = tm_wait_prev(st, s_c, rC, rS);
+        const int maxlen = tm_divc(N32 + L - 1, L);
         const int ntiles = (maxlen + T - 1) / T;
 
         if (warp >= TM_CONS_WARPS) {
@@ -328,7 +378,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
             uint32_t sp_doff = 0;
             const float *sp_row = src;
             if (owner) {
-                sp_i = (sp >= sb[1]) + (sp >= sb[2]) + (sp >= sb[3]);
+                sp_i = tm_sub<NSUB>(sp, sb);
                 const int sp_p = sp - sb[sp_i];
                 sp_alpha = alpha[sp_i];
                 sp_gam = gam[sp_i];
@@ -420,10 +470,10 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
                     atomicOr(&st->status, WL_ETIMEOUT);
         } else {
             // ---------------- consumer warps ----------------
-            float *dstk[4], *outk[4];
-            int mode[4];   // 0: none of sub-vector k is returned, 1: all, 2: check each value
+            float *dstk[NSUB], *outk[NSUB];
+            int mode[NSUB];   // 0: none of sub-vector k is returned, 1: all, 2: check each value
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
+            for (int k = 0; k < NSUB; k++) {
                 const int64_t q0 = k * N, q1 = q0 + N;
                 mode[k] = (q1 <= w0 || q0 >= w1) ? 0 : ((q0 >= w0 && q1 <= w1) ? 1 : 2);
                 dstk[k] = dst + k * Np;
@@ -447,14 +497,65 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
                 const int Tt = min(T, maxlen - t0);
                 const float *sdata = stage0 + s * tm_stage_words();
                 const int *lead = (const int *)(sdata + tm_stage_data_words());
-                uint64_t tl = 0;   // this tile's terms: at most 24 per thread, each below 2^48
+                uint64_t tl = 0;   // this tile's terms: at most 32 per thread, each below 2^48
+                if constexpr (NSUB == 2) {
+                    // lanes x 64-time chunks dealt round-robin over the
+                    // consumer warps (21 to 55 lanes do not split evenly)
+                    // item = l nch + ch, stepped by the warp count without a division
+                    const int nch = T >> 6, nitems = L * nch;
+                    const int dq = tm_divc(TM_CONS_WARPS, nch), dr = TM_CONS_WARPS - dq * nch;
+                    int l = tm_divc(warp, nch), ch = warp - l * nch;
+                    for (int item = warp; item < nitems;
+                         item += TM_CONS_WARPS, l += dq + (ch + dr >= nch ? 1 : 0),
+                         ch = ch + dr >= nch ? ch + dr - nch : ch + dr) {
+                        const int jl = J[l];
+                        const int tmax = min(Tt, J[l + 1] - jl - t0);
+                        const int t = (ch << 6) + lane;
+                        if (t >= tmax)
+                            continue;
+                        const float *gp[2];
+#pragma unroll
+                        for (int i = 0; i < 2; i++) {
+                            const int lb = lanebase[i * LMAXN + l];
+                            gp[i] = sdata + (lb >> 5) + lead[lb & 31];
+                        }
+                        const bool v2 = t + 32 < tmax;
+                        float g[2], h[2], y[2], z[2];
+#pragma unroll
+                        for (int i = 0; i < 2; i++) {
+                            g[i] = gp[i][alpha[i] * t];
+                            h[i] = v2 ? gp[i][alpha[i] * (t + 32)] : 0.f;
+                        }
+                        wl_xform2(g, rC, rS, y);
+                        wl_xform2(h, rC, rS, z);
+                        const int64_t j = (int64_t)jl + t0 + t;
+#pragma unroll
+                        for (int kk = 0; kk < 2; kk++) {
+                            dstk[kk][j] = y[kk];
+                            if (v2) dstk[kk][j + 32] = z[kk];
+                            tl += term32(y[kk], emax);
+                            if (v2) tl += term32(z[kk], emax);
+                            if (mode[kk] == 1) {
+                                outk[kk][j] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
+                                if (v2) outk[kk][j + 32] = __fadd_rn(mu, __fmul_rn(sigma, z[kk]));
+                            } else if (mode[kk] == 2) {
+                                int64_t q = kk * N + j;
+                                if (q >= w0 && q < w1)
+                                    out[q - w0] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
+                                q += 32;
+                                if (v2 && q >= w0 && q < w1)
+                                    out[q - w0] = __fadd_rn(mu, __fmul_rn(sigma, z[kk]));
+                            }
+                        }
+                    }
+                } else
                 for (int l = warp; l < L; l += TM_CONS_WARPS) {
                     const int jl = J[l];
                     const int tmax = min(Tt, J[l + 1] - jl - t0);   // lane times of lane l in this tile
                     const float *gp[4];
 #pragma unroll
                     for (int i = 0; i < 4; i++) {
-                        const int lb = lanebase[i * TM_LMAX + l];
+                        const int lb = lanebase[i * LMAXN + l];
                         gp[i] = sdata + (lb >> 5) + lead[lb & 31];
                     }
                     const int64_t jb = (int64_t)jl + t0;
@@ -506,10 +607,10 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
 
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st))
-        wl_finalise_cta(st, 4, N, a.nu, rnu, &dst[wl_phys(a.nu - 1, N, Np)], SG ? 1 : 0);
+        wl_finalise_cta(st, NSUB, N, a.nu, rnu, &dst[wl_phys(a.nu - 1, N, Np)], SG ? 1 : 0);
 }
 
-bool g_tma_configured[2] = {false, false};
+bool g_tma_configured[3] = {false, false, false};
 
 } // namespace
 
@@ -517,18 +618,19 @@ bool wl_tma_supported(int n, int64_t N, int fp64, int sm_count)
 {
     // lane starts, span starts and slot offsets are held in 32-bit integers
     (void)sm_count;
-    return n == 4 && !fp64 && N >= TM_MIN_N && (N & 3) == 0 && N <= ((int64_t)1 << 28);
+    return (n == 4 || n == 2) && !fp64 && N >= TM_MIN_N && (N & 3) == 0 && N <= ((int64_t)1 << 28);
 }
 
 cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream)
 {
     const size_t smem = tm_smem_bytes();
-    auto kern = signs ? tma_kernel<true> : tma_kernel<false>;
-    if (!g_tma_configured[signs ? 1 : 0]) {
+    const int which = a.n == 2 ? 2 : (signs ? 1 : 0);
+    auto kern = which == 2 ? tma_kernel<false, 2> : (which == 1 ? tma_kernel<true, 4> : tma_kernel<false, 4>);
+    if (!g_tma_configured[which]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        g_tma_configured[signs ? 1 : 0] = true;
+        g_tma_configured[which] = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(sm_count);

@@ -341,6 +341,12 @@ def test_sign_patterns_bit_exact(orc, n, N, variant, mode):
     (15 * 64, 1.0, W.VARIANT_GATHER, W.FP32),      # 15 | N: coprimality fallback
     (1 << 12, 1 / 3, W.VARIANT_AUTO, W.FP64POOL),
     (4096, 1 / 3, W.VARIANT_FUSED, W.FP32 | W.CHI_WH),
+    (1 << 17, 1 / 3, W.VARIANT_TILED_TMA, W.FP32),  # bulk-copy lane-tiled pass, n = 2
+    (100004, 0.5, W.VARIANT_TILED_TMA, W.FP32),
+    (16388, 1 / 3, W.VARIANT_AUTO, W.FP32),
+    (3 * 16384, 1 / 3, W.VARIANT_TILED_TMA, W.FP32),   # alpha = 5: L = 35 or 55
+    (15 * 2048, 1 / 3, W.VARIANT_TILED_TMA, W.FP32),   # strides 7, 11: in-kernel gather
+    (1 << 17, 1 / 3, W.VARIANT_TILED_TMA, W.FP32 | W.CHI_WH),
 ])
 def test_rann4_bit_exact(orc, N, frac, variant, mode):
     """RANN4 itself (n = 2, Section 8): strides from {3,5} and {7,11} and a
@@ -367,3 +373,14 @@ def test_rann4_bit_exact(orc, N, frac, variant, mode):
 def test_rann4_rejects_sign_patterns():
     with pytest.raises(W.WallaceError):
         W.Wallace(2, 256, 1, 1.0, mode=W.FP32 | W.MATRIX_SIGNS)
+
+
+def test_rann4_full_size(orc):
+    """RANN4 at its benchmark size (n = 2, N = 2^25, frac = 1/3): three passes
+    element by element through the bulk-copy pass."""
+    g = W.Wallace(2, 1 << 25, 7, 1 / 3)
+    o = orc.Generator(2, 1 << 25, 7, 1 / 3)
+    for k in range(3):
+        assert_same(fill_dev(g, g.R), o.fill(g.R), f"pass {k + 1} output")
+        assert_stats_equal(g, o, f"pass {k + 1}")
+    assert_same(g.pool(), o.pool32(), "pool")
