@@ -281,7 +281,11 @@ int wallace_batch_get_pool(wallace_batch_t *b, int s, float *host_out);
  * wallace_batch_set_tuning / wallace_batch_get_tuning -- launch shape: CTAs
  * per SM (capped by occupancy), lane-times per tile of the tiled gather
  * (4 <= etarget <= 2560), and the largest pool (n*N values) kept in shared
- * memory across passes (at most ~8400 values fit).
+ * memory across passes (at most ~8400 values fit).  ctas_per_sm = 0 selects
+ * the bulk-copy runner instead: one CTA of 608 threads per SM, pools with
+ * n = 4, N % 4 == 0 and N >= 16384 regenerated through a warp-specialised
+ * stage ring fed by bulk (TMA) copies, the others as before (etarget and
+ * fused_max apply to them).
  */
 int wallace_batch_set_tuning(wallace_batch_t *b, int ctas_per_sm, int etarget, int64_t fused_max);
 int wallace_batch_get_tuning(const wallace_batch_t *b, int *ctas_per_sm, int *etarget,
@@ -291,8 +295,8 @@ int wallace_batch_get_tuning(const wallace_batch_t *b, int *ctas_per_sm, int *et
  * wallace_batch_autotune -- pick the launch shape.  If `cache_path` (may be
  * NULL) holds an entry for this device and batch shape (count, n, frac and
  * the histogram of pool sizes), use it.  Otherwise time `trial_passes`
- * passes for each candidate (CTAs/SM in {1,2,3}, tile in {1280,1920,2560},
- * shared-memory pool limit in {2048,4096,8192}) on a snapshot of the
+ * passes for each candidate (CTAs/SM in {1,2,3} or the bulk-copy runner,
+ * tile in {1280,1920,2560}, shared-memory pool limit in {2048,4096,8192}) on a snapshot of the
  * generators -- the generators themselves do not advance -- keep the fastest
  * and append it to `cache_path` as one JSON object per line.  Synchronous.
  */

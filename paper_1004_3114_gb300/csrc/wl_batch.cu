@@ -29,6 +29,7 @@
 #include "wallace.h"
 #include "wl_launch.h"
 #include "wl_run_body.cuh"
+#include "wl_tma_run.cuh"
 
 #define BT_THREADS 256
 
@@ -93,10 +94,65 @@ __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
     }
 }
 
+// The same work with the CTA-local bulk-copy runner for pools the
+// single-generator pass would tile with bulk copies (n = 4, N % 4 == 0,
+// N >= TM_MIN_N): one CTA of TM_THREADS threads per SM.
+__global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
+{
+    extern __shared__ __align__(128) float smem[];
+    __shared__ uint64_t red[3 * (TM_THREADS / 32 + 1)];
+    __shared__ int32_t s_prm[20];
+    __shared__ int s_k;
+    __shared__ __align__(8) uint64_t bar_full[TM_STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[TM_STAGES];
+    __shared__ volatile int s_abort;
+    WlTmaRing ring;
+    ring.full = bar_full;
+    ring.empty = bar_empty;
+    ring.abort_flag = &s_abort;
+    wl_tma_ring_init(ring);
+    const int tid = threadIdx.x;
+    const int64_t smem_values = (int64_t)(wl_tma::tm_smem_bytes() / sizeof(float));
+    while (true) {
+        __syncthreads();
+        if (tid == 0)
+            s_k = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int k = s_k;
+        if (k >= a.count)
+            break;
+        const BatchStream d = a.streams[a.order[k]];
+        WlRunSpec r;
+        r.buf[0] = d.pool[0];
+        r.buf[1] = d.pool[1];
+        r.cur = d.cur;
+        r.st = d.st;
+        r.N = d.N;
+        r.Np = d.Np;
+        r.R = d.R;
+        r.n = d.n;
+        r.passes = a.passes;
+        r.out = a.out ? a.out + a.passes * d.out_pref : nullptr;
+        r.last_take = d.R;
+        r.mu = a.mu;
+        r.sigma = a.sigma;
+        r.etarget = a.etarget;
+        int cur;
+        if (d.n == 4 && !wl_run_is_fused(4, d.N, a.fused_max, smem_values) && d.N >= TM_MIN_N &&
+            (d.N & 3) == 0 && d.N <= ((int64_t)1 << 28))
+            cur = wl_run_tma(r, smem, red, s_prm, ring);
+        else
+            cur = wl_run_spec(r, a.fused_max, smem_values, smem, red, s_prm);
+        if (tid == 0)
+            a.streams[a.order[k]].cur = cur;
+    }
+}
+
 struct Tuning {
     int ctas_per_sm = 2;
     int etarget = TL_EMAX;
     int64_t fused_max = 4096;
+    int runner = 0;   // 0: per-thread async-copy runner; 1: bulk-copy runner (batch_tma_kernel)
 };
 
 } // namespace
@@ -120,6 +176,7 @@ struct wallace_batch {
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t knode = nullptr;
     int graph_ctas = 0;
+    int graph_runner = -1;
     int status = 0;
     double last_run_ms = 0.0;
 };
@@ -159,6 +216,9 @@ cudaError_t ensure_configured()
     cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tl_smem_bytes());
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)wl_tma::tm_smem_bytes());
+    if (e == cudaSuccess)
         done = true;
     return e;
 }
@@ -170,16 +230,17 @@ cudaError_t launch_graph(wallace_batch_t *b, const BatchArgs &args)
     cudaError_t e = ensure_configured();
     if (e != cudaSuccess)
         return e;
-    const int ctas = b->sm_count * std::min(b->tune.ctas_per_sm, b->max_ctas_per_sm);
+    const bool tma = b->tune.runner == 1;
+    const int ctas = tma ? b->sm_count : b->sm_count * std::min(b->tune.ctas_per_sm, b->max_ctas_per_sm);
     BatchArgs a = args;
     void *params[] = {&a};
     cudaKernelNodeParams kp = {};
-    kp.func = (void *)batch_kernel;
+    kp.func = tma ? (void *)batch_tma_kernel : (void *)batch_kernel;
     kp.gridDim = dim3(ctas);
-    kp.blockDim = dim3(BT_THREADS);
-    kp.sharedMemBytes = (unsigned)tl_smem_bytes();
+    kp.blockDim = dim3(tma ? TM_THREADS : BT_THREADS);
+    kp.sharedMemBytes = (unsigned)(tma ? wl_tma::tm_smem_bytes() : tl_smem_bytes());
     kp.kernelParams = params;
-    if (!b->exec || b->graph_ctas != ctas) {
+    if (!b->exec || b->graph_ctas != ctas || b->graph_runner != b->tune.runner) {
         if (b->exec)
             cudaGraphExecDestroy(b->exec);
         if (b->graph)
@@ -204,6 +265,7 @@ cudaError_t launch_graph(wallace_batch_t *b, const BatchArgs &args)
         if (e != cudaSuccess)
             return e;
         b->graph_ctas = ctas;
+        b->graph_runner = b->tune.runner;
     } else {
         e = cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp);
         if (e != cudaSuccess)
@@ -248,16 +310,19 @@ bool read_cached(const char *path, const std::string &key, Tuning *t)
     while (fgets(line, sizeof line, f)) {
         if (!strstr(line, needle.c_str()))
             continue;
-        int ctas = 0, et = 0;
+        int ctas = 0, et = 0, runner = 0;
         long long fm = 0;
         const char *pc = strstr(line, "\"ctas_per_sm\": ");
         const char *pe = strstr(line, "\"etarget\": ");
         const char *pf = strstr(line, "\"fused_max\": ");
-        if (pc && pe && pf && sscanf(pc, "\"ctas_per_sm\": %d", &ctas) == 1 &&
-            sscanf(pe, "\"etarget\": %d", &et) == 1 && sscanf(pf, "\"fused_max\": %lld", &fm) == 1) {
+        const char *pr = strstr(line, "\"runner\": ");
+        if (pc && pe && pf && pr && sscanf(pc, "\"ctas_per_sm\": %d", &ctas) == 1 &&
+            sscanf(pe, "\"etarget\": %d", &et) == 1 && sscanf(pf, "\"fused_max\": %lld", &fm) == 1 &&
+            sscanf(pr, "\"runner\": %d", &runner) == 1) {
             t->ctas_per_sm = ctas;
             t->etarget = et;
             t->fused_max = fm;
+            t->runner = runner;
             found = true;   // the last matching line wins
         }
     }
@@ -486,9 +551,10 @@ int wallace_batch_get_pool(wallace_batch_t *b, int s, float *host_out)
 
 int wallace_batch_set_tuning(wallace_batch_t *b, int ctas_per_sm, int etarget, int64_t fused_max)
 {
-    if (!b || ctas_per_sm < 1 || etarget < 4 || etarget > TL_EMAX || fused_max < 0)
+    if (!b || ctas_per_sm < 0 || etarget < 4 || etarget > TL_EMAX || fused_max < 0)
         return WALLACE_EINVAL;
-    b->tune.ctas_per_sm = ctas_per_sm;
+    b->tune.runner = ctas_per_sm == 0 ? 1 : 0;
+    b->tune.ctas_per_sm = ctas_per_sm == 0 ? 1 : ctas_per_sm;
     b->tune.etarget = etarget;
     b->tune.fused_max = fused_max;
     return WALLACE_OK;
@@ -499,7 +565,7 @@ int wallace_batch_get_tuning(const wallace_batch_t *b, int *ctas_per_sm, int *et
     if (!b)
         return WALLACE_EINVAL;
     if (ctas_per_sm)
-        *ctas_per_sm = std::min(b->tune.ctas_per_sm, b->max_ctas_per_sm);
+        *ctas_per_sm = b->tune.runner == 1 ? 0 : std::min(b->tune.ctas_per_sm, b->max_ctas_per_sm);
     if (etarget)
         *etarget = b->tune.etarget;
     if (fused_max)
@@ -542,15 +608,20 @@ int wallace_batch_autotune(wallace_batch_t *b, const char *cache_path, int trial
         e = cudaEventCreate(&t1);
     Tuning best = b->tune;
     float best_ms = 1e30f;
-    const int ctas_list[] = {1, 2, 3};
+    // async-copy runner: CTAs per SM x tile size x shared-memory pool limit;
+    // bulk-copy runner (one CTA per SM): shared-memory pool limit x the async
+    // tile size its smaller global pools use
+    const int ctas_list[] = {1, 2, 3, 0};
     const int et_list[] = {1280, 1920, TL_EMAX};
     const int64_t fm_list[] = {2048, 4096, 8192};
-    for (int ci = 0; ci < 3 && e == cudaSuccess; ci++) {
-        if (ctas_list[ci] > b->max_ctas_per_sm)
+    for (int ci = 0; ci < 4 && e == cudaSuccess; ci++) {
+        const bool tma = ctas_list[ci] == 0;
+        if (!tma && ctas_list[ci] > b->max_ctas_per_sm)
             continue;
         for (int ei = 0; ei < 3 && e == cudaSuccess; ei++)
             for (int fi = 0; fi < 3 && e == cudaSuccess; fi++) {
-                b->tune.ctas_per_sm = ctas_list[ci];
+                b->tune.runner = tma ? 1 : 0;
+                b->tune.ctas_per_sm = tma ? 1 : ctas_list[ci];
                 b->tune.etarget = et_list[ei];
                 b->tune.fused_max = fm_list[fi];
                 e = cudaEventRecord(t0, b->stream);
@@ -596,9 +667,9 @@ int wallace_batch_autotune(wallace_batch_t *b, const char *cache_path, int trial
         if (f) {
             fprintf(f,
                     "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"etarget\": %d, \"fused_max\": %lld, "
-                    "\"trial_passes\": %d, \"ms\": %.4f}\n",
+                    "\"runner\": %d, \"trial_passes\": %d, \"ms\": %.4f}\n",
                     key.c_str(), best.ctas_per_sm, best.etarget, (long long)best.fused_max,
-                    trial_passes, best_ms);
+                    best.runner, trial_passes, best_ms);
             fclose(f);
         }
     }

@@ -41,16 +41,23 @@ def _check_batch(orc, b, Ns, seeds, frac, n, runs, mu=0.0, sigma=1.0):
     assert b.sync() == 0
 
 
-def test_batch_n4_mixed_sizes_matches_oracle(orc):
+@pytest.mark.parametrize("bulk", [False, True])
+def test_batch_n4_mixed_sizes_matches_oracle(orc, bulk):
     seeds = list(range(100, 100 + len(NS4)))
     b = W.Batch(4, NS4, seeds, 1.0)
+    if bulk:
+        b.set_tuning(0, 2560, 4096)      # the bulk-copy runner
     _check_batch(orc, b, NS4, seeds, 1.0, 4, runs=[3, 2, 1], mu=0.5, sigma=2.0)
 
 
-@pytest.mark.parametrize("tuning", [(1, 1280, 0), (3, 2560, 8192), (2, 640, 2048)])
+@pytest.mark.parametrize("tuning", [(1, 1280, 0), (3, 2560, 8192), (2, 640, 2048), (0, 2560, 4096),
+                                    (0, 1280, 0)])
 def test_batch_tunings_give_identical_streams(orc, tuning):
-    Ns = [300, 2000, 9000, 30000, 65536, 5001]
-    seeds = [5, 6, 7, 8, 9, 10]
+    """ctas_per_sm = 0: the bulk-copy runner (pools 30000, 65536, 100004 and
+    16384 take the stage ring; 45060 = 2^2 3 5 751 has fallback strides and
+    takes the plain gather inside it)."""
+    Ns = [300, 2000, 9000, 30000, 65536, 5001, 100004, 16384, 45060]
+    seeds = [5, 6, 7, 8, 9, 10, 11, 12, 13]
     b = W.Batch(4, Ns, seeds, 0.5)
     b.set_tuning(*tuning)
     _check_batch(orc, b, Ns, seeds, 0.5, 4, runs=[2, 3])
