@@ -659,7 +659,7 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
 
 
 def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float = 50_000.0,
-                budget_gb: float = 40.0, passes_per_tick: int = 2):
+                budget_gb: float = 40.0, passes_per_tick: int = 2, ctas_per_sm: int = 0):
     """Serving loop: n_clients generators (n = 4, N log-uniform on
     [2^10, 2^20], frac = 1/3), Poisson arrivals at `rate`, counts log-uniform
     on [2^10, 2^24], mu ~ U[-10, 10], sigma ~ U[0.1, 10], admitted against a
@@ -674,7 +674,7 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
     t0 = time.perf_counter()
     srv = W.Server(4, Ns, seeds, 1 / 3, int(budget_gb * (1 << 30)), stream=stream)
     create_s = time.perf_counter() - t0
-    srv.set_tuning(passes_per_tick, 4096, 3)
+    srv.set_tuning(passes_per_tick, 4096, ctas_per_sm)
     tr = serving_requests(n_requests, n_clients, rate)
     t0 = time.perf_counter()
     lat = srv.run_trace(tr["arrival_s"], tr["client"], tr["count"], tr["mu"], tr["sigma"])
@@ -698,7 +698,9 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
         "roofline": {"bound": "hbm", "achieved": bytes_moved / st.elapsed_s / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": bytes_moved / st.elapsed_s / 1e9 / peak, "peak_kind": kind,
                      "bytes_per_value": 28},
-        "passes_per_tick": passes_per_tick, "create_s": create_s, "status": int(st.status)}), flush=True)
+        "passes_per_tick": passes_per_tick, "ctas_per_sm": ctas_per_sm,
+        "runner": "bulk-copy for one-CTA requests on 16384 <= N (n=4, N % 4 == 0)" if ctas_per_sm == 0
+                  else "async-copy", "create_s": create_s, "status": int(st.status)}), flush=True)
 
 
 def main():
@@ -726,6 +728,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=20_000)
     ap.add_argument("--serve-rate", type=float, default=50_000.0)
     ap.add_argument("--serve-ppt", type=int, default=2)
+    ap.add_argument("--serve-ctas", type=int, default=0,
+                    help="CTAs per SM of the one-CTA requests; 0: bulk-copy runner where it applies")
     ap.add_argument("--precision-study", action="store_true",
                     help="binary32 vs binary64 pool study (N=2^22, n=4 and 8, 1000 passes) instead of the benchmark")
     args = ap.parse_args()
@@ -746,7 +750,7 @@ def main():
         return
     if args.serve:
         serve_bench(n_requests=args.serve_requests, rate=args.serve_rate,
-                    passes_per_tick=args.serve_ppt)
+                    passes_per_tick=args.serve_ppt, ctas_per_sm=args.serve_ctas)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -342,8 +342,11 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
 void wallace_server_destroy(wallace_server_t *s);
 
 /* wallace_server_set_tuning -- passes per request per tick (>= 1), the
- * largest pool kept in shared memory across passes, CTAs per SM.  Only
- * while idle. */
+ * largest pool kept in shared memory across passes, CTAs per SM.
+ * ctas_per_sm = 0: three CTAs per SM as before, and the requests one CTA
+ * serves whose pools have n = 4, N % 4 == 0, N >= 16384 run the bulk-copy
+ * (TMA) runner instead, one 608-thread CTA per SM on a second stream beside
+ * the others.  Only while idle. */
 int wallace_server_set_tuning(wallace_server_t *s, int passes_per_tick, int64_t fused_max,
                               int ctas_per_sm);
 

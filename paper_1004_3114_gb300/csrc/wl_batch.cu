@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
     __shared__ uint64_t red[3 * (BT_THREADS / 32)];
     __shared__ int32_t s_prm[20];
     __shared__ int s_k;
+    __shared__ WlDevState sst;   // the running generator's state
     const int tid = threadIdx.x;
     const int64_t smem_values = (int64_t)(tl_smem_bytes() / sizeof(float));
     while (true) {
@@ -88,7 +89,10 @@ __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
         r.mu = a.mu;
         r.sigma = a.sigma;
         r.etarget = a.etarget;
+        wl_state_load(&sst, d.st);
+        r.st = &sst;
         const int cur = wl_run_spec(r, a.fused_max, smem_values, smem, red, s_prm);
+        wl_state_store(d.st, &sst);
         if (tid == 0)
             a.streams[a.order[k]].cur = cur;
     }
@@ -106,6 +110,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
     __shared__ __align__(8) uint64_t bar_full[TM_STAGES];
     __shared__ __align__(8) uint64_t bar_empty[TM_STAGES];
     __shared__ volatile int s_abort;
+    __shared__ WlDevState sst;   // the running generator's state
     WlTmaRing ring;
     ring.full = bar_full;
     ring.empty = bar_empty;
@@ -138,11 +143,14 @@ __global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
         r.sigma = a.sigma;
         r.etarget = a.etarget;
         int cur;
+        wl_state_load(&sst, d.st);
+        r.st = &sst;
         if (d.n == 4 && !wl_run_is_fused(4, d.N, a.fused_max, smem_values) && d.N >= TM_MIN_N &&
             (d.N & 3) == 0 && d.N <= ((int64_t)1 << 28))
             cur = wl_run_tma(r, smem, red, s_prm, ring);
         else
             cur = wl_run_spec(r, a.fused_max, smem_values, smem, red, s_prm);
+        wl_state_store(d.st, &sst);
         if (tid == 0)
             a.streams[a.order[k]].cur = cur;
     }

@@ -441,11 +441,17 @@ __device__ __forceinline__ double wl_chi_sample(int chi, int64_t nu, double x)
 #define WL_FIN_INIT 0
 #define WL_FIN_PASS 1
 #define WL_FIN_RESTART 2
+// local: st is a CTA's shared-memory copy of the state (a run of many passes
+// on one CTA), so no device-scope fence is needed; rnu > 0: sqrt(2 nu - 1)
+// precomputed by the caller (Eq. 3's sample).
 __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu, double x,
-                                   bool fp64, int kind)
+                                   bool fp64, int kind, bool local = false, double rnu = 0.0)
 {
     volatile WlDevState *vs = st;
-    __threadfence();
+    if (local)
+        __threadfence_block();
+    else
+        __threadfence();
     uint64_t lo, hi;
     wl_acc_read(st, lo, hi);
     uint32_t bad = vs->acc_bad;
@@ -457,7 +463,13 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
     } else {
         q = __dadd_rn(__ull2double_rn(hi), __dmul_rn(__ull2double_rn(lo), 1.0 / 18446744073709551616.0));
     }
-    const double S = wl_chi_sample(st->chi, nu, x);
+    double S;
+    if (rnu > 0.0 && !st->chi) {
+        const double xr = __dadd_rn(x, rnu);
+        S = __dmul_rn(__dmul_rn(xr, xr), 0.5);
+    } else {
+        S = wl_chi_sample(st->chi, nu, x);
+    }
     double c = 1.0;
     int32_t status = st->status;
     if (bad || (st->chi && !(S > 0.0)) || !(q > 0.0))
@@ -594,6 +606,34 @@ __device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, int64_t
         st->tile_ctr = 0;
         st->ticket = 0;
     }
+}
+
+// A generator's state kept in shared memory while one CTA runs its passes:
+// the finaliser's reads and writes and the sum-of-squares atomics stay on
+// chip.  Every thread of the CTA calls both; nothing else touches the
+// device copy meanwhile.
+__device__ inline void wl_state_load(WlDevState *sh, const WlDevState *g)
+{
+    const uint32_t *src = (const uint32_t *)g;
+    uint32_t *dst = (uint32_t *)sh;
+    for (int w = threadIdx.x; w < (int)(sizeof(WlDevState) / 4); w += blockDim.x)
+        dst[w] = src[w];
+    __syncthreads();
+}
+
+__device__ inline void wl_state_store(WlDevState *g, const WlDevState *sh)
+{
+    __syncthreads();
+    const uint32_t *src = (const uint32_t *)sh;
+    uint32_t *dst = (uint32_t *)g;
+    for (int w = threadIdx.x; w < (int)(sizeof(WlDevState) / 4); w += blockDim.x)
+        dst[w] = src[w];
+}
+
+// sqrt(2 nu - 1) of Eq. 3, as the finaliser would compute it
+__device__ __forceinline__ double wl_rnu(int64_t nu)
+{
+    return __dsqrt_rn(__dsub_rn(__dmul_rn(2.0, (double)nu), 1.0));
 }
 
 // Last-CTA detection: after a CTA barrier one thread takes a ticket with an

@@ -19,7 +19,7 @@ namespace {
 
 template <int NSUB, typename T>
 __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout, int64_t N,
-                                                          int64_t Np, WlDevState *st,
+                                                          int64_t Np, WlDevState *st_g,
                                                           int64_t passes, int64_t R,
                                                           int64_t last_take, T *__restrict__ out,
                                                           double mu_d, double sigma_d)
@@ -30,8 +30,12 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
     __shared__ int32_t s_gamma[NSUB];
     __shared__ T s_c, s_rC, s_rS;
     __shared__ uint32_t s_signs;
+    __shared__ WlDevState sst;   // the state, on chip for the whole run
+    wl_state_load(&sst, st_g);
+    WlDevState *st = &sst;
     const int tid = threadIdx.x;
     const int nu = NSUB * (int)N;
+    const double rnu = wl_rnu(nu);
     T *buf0 = (T *)fsm;
     T *buf1 = buf0 + nu;
     for (int q = tid; q < nu; q += FU_THREADS) {
@@ -113,10 +117,9 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
         }
         wl_cta_reduce_to_state(lo, hi, bad, st, red);
         __syncthreads();
-        if (tid == 0) {
-            __threadfence_block();
-            wl_finalise(st, NSUB, N, (int64_t)nu, (double)dst[nu - 1], sizeof(T) == 8, WL_FIN_PASS);
-        }
+        if (tid == 0)
+            wl_finalise(st, NSUB, N, (int64_t)nu, (double)dst[nu - 1], sizeof(T) == 8, WL_FIN_PASS, true,
+                        rnu);
         __syncthreads();
         T *t = src;
         src = dst;
@@ -126,6 +129,7 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
         int i = q / (int)N;
         gout[(int64_t)i * Np + (q - i * (int)N)] = src[q];
     }
+    wl_state_store(st_g, &sst);
 }
 
 template <int NSUB, typename T>

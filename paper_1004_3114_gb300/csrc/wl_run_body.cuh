@@ -68,6 +68,7 @@ __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red, int32
 {
     const int tid = threadIdx.x, nth = blockDim.x;
     const int N = (int)d.N, nu = NSUB * N;
+    const double rnu = wl_rnu(nu);
     float *src = sm, *dst = sm + nu;
     const float *g0 = d.buf[d.cur];
     for (int q = tid; q < nu; q += nth) {
@@ -120,7 +121,7 @@ __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red, int32
         wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
         __syncthreads();
         if (tid == 0)
-            wl_finalise(d.st, NSUB, N, nu, (double)dst[nu - 1], false, WL_FIN_PASS);
+            wl_finalise(d.st, NSUB, N, nu, (double)dst[nu - 1], false, WL_FIN_PASS, true, rnu);
         float *t = src;
         src = dst;
         dst = t;
@@ -140,6 +141,7 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
 {
     const int tid = threadIdx.x;
     const int64_t N = d.N, nu = NSUB * N;
+    const double rnu = wl_rnu(nu);
     int cur = d.cur;
     for (int64_t p = 0; p < d.passes; p++) {
         __syncthreads();   // the previous pass's parameters are written
@@ -185,7 +187,8 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
         wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
         __syncthreads();
         if (tid == 0)
-            wl_finalise(d.st, NSUB, N, nu, (double)__ldcg(&dst[wl_phys(nu - 1, N, d.Np)]), false, WL_FIN_PASS);
+            wl_finalise(d.st, NSUB, N, nu, (double)__ldcg(&dst[wl_phys(nu - 1, N, d.Np)]), false, WL_FIN_PASS,
+                        true, rnu);
         cur = 1 - cur;
     }
     return cur;

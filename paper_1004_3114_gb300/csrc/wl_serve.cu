@@ -38,6 +38,7 @@
 #include "wallace.h"
 #include "wl_launch.h"
 #include "wl_run_body.cuh"
+#include "wl_tma_run.cuh"
 
 #define SV_THREADS 256
 #define SV_MAX_PPT 14                /* passes per tick of a large pool (queue counters per slot - 1) */
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(SV_THREADS, 3) serve_kernel(const ServeItem *i
     __shared__ uint64_t red[3 * (SV_THREADS / 32)];
     __shared__ int32_t s_prm[20];
     __shared__ int s_k;
+    __shared__ WlDevState sst;   // the running request's generator state
     const int tid = threadIdx.x;
     const int64_t smem_values = (int64_t)(tl_smem_bytes() / sizeof(float));
     while (true) {
@@ -75,8 +77,67 @@ __global__ void __launch_bounds__(SV_THREADS, 3) serve_kernel(const ServeItem *i
             const float y = it.drain_src[wl_phys(it.drain_pos + q, it.spec.N, it.spec.Np)];
             it.drain_out[q] = __fadd_rn(it.spec.mu, __fmul_rn(it.spec.sigma, y));
         }
-        if (it.spec.passes > 0)
-            wl_run_spec(it.spec, fused_max, smem_values, smem, red, s_prm);
+        if (it.spec.passes > 0) {
+            WlRunSpec r = it.spec;
+            wl_state_load(&sst, it.spec.st);
+            r.st = &sst;
+            wl_run_spec(r, fused_max, smem_values, smem, red, s_prm);
+            wl_state_store(it.spec.st, &sst);
+        }
+    }
+}
+
+// Whether a one-CTA request's pool takes the bulk-copy runner (wl_tma_run.cuh).
+__host__ __device__ inline bool sv_bulk_eligible(int n, int64_t N, int64_t passes, int64_t fused_max,
+                                                 int64_t smem_values)
+{
+    return n == 4 && passes > 0 && N >= TM_MIN_N && (N & 3) == 0 && N <= ((int64_t)1 << 28) &&
+           !wl_run_is_fused(n, N, fused_max, smem_values);
+}
+
+// The same items with the CTA-local bulk-copy runner: one 608-thread CTA per
+// SM, running beside serve_kernel's CTAs on another stream.
+__global__ void __launch_bounds__(TM_THREADS, 1) serve_tma_kernel(const ServeItem *items, int count,
+                                                                  int *queue, int64_t fused_max)
+{
+    extern __shared__ __align__(128) float smem[];
+    __shared__ uint64_t red[3 * (TM_THREADS / 32 + 1)];
+    __shared__ int32_t s_prm[20];
+    __shared__ int s_k;
+    __shared__ __align__(8) uint64_t bar_full[TM_STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[TM_STAGES];
+    __shared__ volatile int s_abort;
+    __shared__ WlDevState sst;   // the running request's generator state
+    WlTmaRing ring;
+    ring.full = bar_full;
+    ring.empty = bar_empty;
+    ring.abort_flag = &s_abort;
+    wl_tma_ring_init(ring);
+    const int tid = threadIdx.x;
+    const int64_t smem_values = (int64_t)(wl_tma::tm_smem_bytes() / sizeof(float));
+    while (true) {
+        __syncthreads();
+        if (tid == 0)
+            s_k = atomicAdd(queue, 1);
+        __syncthreads();
+        const int k = s_k;
+        if (k >= count)
+            break;
+        const ServeItem it = items[k];
+        for (int64_t q = tid; q < it.drain_take; q += blockDim.x) {
+            const float y = it.drain_src[wl_phys(it.drain_pos + q, it.spec.N, it.spec.Np)];
+            it.drain_out[q] = __fadd_rn(it.spec.mu, __fmul_rn(it.spec.sigma, y));
+        }
+        if (it.spec.passes > 0) {
+            WlRunSpec r = it.spec;
+            wl_state_load(&sst, it.spec.st);
+            r.st = &sst;
+            if (sv_bulk_eligible(it.spec.n, it.spec.N, it.spec.passes, fused_max, smem_values))
+                wl_run_tma(r, smem, red, s_prm, ring);
+            else
+                wl_run_spec(r, fused_max, smem_values, smem, red, s_prm);
+            wl_state_store(it.spec.st, &sst);
+        }
     }
 }
 
@@ -310,6 +371,9 @@ struct wallace_server {
     int n = 4, nclients = 0;
     double frac = 1.0;
     cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr;             // the bulk-copy runner's stream (forked per tick)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool bulk = false;                      // one-CTA requests of large enough pools use the bulk-copy runner
     int sm_count = 1, max_ctas_per_sm = 1;
     char *pool_mem = nullptr;
     size_t budget = 0;
@@ -567,10 +631,18 @@ int enqueue_tick(wallace_server_t *s)
         }
     }
     s->active.swap(still);
-    // largest work first
+    // largest work first; with the bulk-copy runner on, its items go last
     std::sort(small.begin(), small.end(), [](const ServeItem &a, const ServeItem &b) {
         return a.spec.N * (a.spec.passes + 1) > b.spec.N * (b.spec.passes + 1);
     });
+    int nrest = (int)small.size();
+    if (s->bulk) {
+        const int64_t tma_values = (int64_t)(wl_tma::tm_smem_bytes() / sizeof(float));
+        auto mid = std::stable_partition(small.begin(), small.end(), [&](const ServeItem &it) {
+            return !sv_bulk_eligible(it.spec.n, it.spec.N, it.spec.passes, s->fused_max, tma_values);
+        });
+        nrest = (int)(mid - small.begin());
+    }
     // one device buffer per slot: [small items][pass items...][pass units...]
     size_t bytes = sizeof(ServeItem) * small.size();
     std::vector<size_t> off_items(s->passes_per_tick), off_units(s->passes_per_tick);
@@ -608,10 +680,24 @@ int enqueue_tick(wallace_server_t *s)
     if (e == cudaSuccess)
         e = cudaMemsetAsync(dq, 0, sizeof(int) * SV_QUEUES_PER_SLOT, s->stream);
     const int ctas = s->sm_count * std::min(s->ctas_per_sm, s->max_ctas_per_sm);
-    if (e == cudaSuccess && !small.empty()) {
-        const int grid = std::min(ctas, (int)small.size());
-        serve_kernel<<<grid, SV_THREADS, tl_smem_bytes(), s->stream>>>((const ServeItem *)dw, (int)small.size(),
-                                                                    dq, s->fused_max);
+    // bulk-copy items (placed after the others) run on the aux stream, beside the rest
+    const int nbulk = (int)small.size() - nrest;
+    if (e == cudaSuccess && nbulk > 0) {
+        e = cudaEventRecord(s->ev_fork, s->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(s->aux, s->ev_fork, 0);
+        if (e == cudaSuccess) {
+            serve_tma_kernel<<<std::min(s->sm_count, nbulk), TM_THREADS, wl_tma::tm_smem_bytes(), s->aux>>>(
+                (const ServeItem *)dw + nrest, nbulk, dq + SV_MAX_PPT + 1, s->fused_max);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaEventRecord(s->ev_join, s->aux);
+    }
+    if (e == cudaSuccess && nrest > 0) {
+        const int grid = std::min(ctas, nrest);
+        serve_kernel<<<grid, SV_THREADS, tl_smem_bytes(), s->stream>>>((const ServeItem *)dw, nrest, dq,
+                                                                    s->fused_max);
         e = cudaGetLastError();
     }
     for (int p = 0; p < s->passes_per_tick && e == cudaSuccess; p++) {
@@ -623,6 +709,8 @@ int enqueue_tick(wallace_server_t *s)
             (int)punits[p].size(), dq + 1 + p);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && nbulk > 0)
+        e = cudaStreamWaitEvent(s->stream, s->ev_join, 0);
     for (size_t k = 0; k < t.copies.size() && e == cudaSuccess; k++)
         e = cudaMemcpyAsync(t.copies[k].dst, t.copies[k].src, t.copies[k].bytes, cudaMemcpyDeviceToDevice,
                             s->stream);
@@ -710,6 +798,15 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(pass_units_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tl_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(serve_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)wl_tma::tm_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         int per = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, serve_kernel, SV_THREADS, tl_smem_bytes());
@@ -758,6 +855,14 @@ void wallace_server_destroy(wallace_server_t *s)
     if (!s)
         return;
     cudaStreamSynchronize(s->stream);
+    if (s->aux) {
+        cudaStreamSynchronize(s->aux);
+        cudaStreamDestroy(s->aux);
+    }
+    if (s->ev_fork)
+        cudaEventDestroy(s->ev_fork);
+    if (s->ev_join)
+        cudaEventDestroy(s->ev_join);
     for (auto &t : s->inflight)
         cudaEventDestroy(t.ev);
     for (auto *p : s->d_work)
@@ -770,12 +875,13 @@ void wallace_server_destroy(wallace_server_t *s)
 
 int wallace_server_set_tuning(wallace_server_t *s, int passes_per_tick, int64_t fused_max, int ctas_per_sm)
 {
-    if (!s || passes_per_tick < 1 || passes_per_tick > SV_MAX_PPT || fused_max < 0 || ctas_per_sm < 1 ||
+    if (!s || passes_per_tick < 1 || passes_per_tick > SV_MAX_PPT || fused_max < 0 || ctas_per_sm < 0 ||
         !s->active.empty() || !s->inflight.empty())
         return WALLACE_EINVAL;
     s->passes_per_tick = passes_per_tick;
     s->fused_max = fused_max;
-    s->ctas_per_sm = ctas_per_sm;
+    s->bulk = ctas_per_sm == 0;
+    s->ctas_per_sm = ctas_per_sm == 0 ? 3 : ctas_per_sm;
     return WALLACE_OK;
 }
 

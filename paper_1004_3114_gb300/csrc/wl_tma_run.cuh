@@ -280,6 +280,7 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
 {
     const int tid = threadIdx.x;
     const int64_t N = d.N, nu = 4 * N;
+    const double rnu = wl_rnu(nu);
     int cur = d.cur;
     for (int64_t p = 0; p < d.passes; p++) {
         __syncthreads();   // the previous pass's finaliser has written the parameters
@@ -331,7 +332,8 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
         wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
         __syncthreads();
         if (tid == 0)
-            wl_finalise(d.st, 4, N, nu, (double)__ldcg(&dst[wl_phys(nu - 1, N, d.Np)]), false, WL_FIN_PASS);
+            wl_finalise(d.st, 4, N, nu, (double)__ldcg(&dst[wl_phys(nu - 1, N, d.Np)]), false, WL_FIN_PASS,
+                        true, rnu);
         cur = 1 - cur;
     }
     return cur;

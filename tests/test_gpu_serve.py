@@ -45,7 +45,8 @@ def _serve(Ns, seeds, reqs, frac, budget, tuning=None, interleave=True):
     return outs, st
 
 
-@pytest.mark.parametrize("frac,tuning", [(1 / 3, None), (1.0, (1, 2048, 2)), (0.5, (3, 0, 1))])
+@pytest.mark.parametrize("frac,tuning", [(1 / 3, None), (1.0, (1, 2048, 2)), (0.5, (3, 0, 1)),
+                                         (1 / 3, (2, 4096, 0))])
 def test_server_outputs_match_oracle(orc, frac, tuning):
     Ns, seeds, reqs = _mix(7, 24, 160, 40000)
     outs, st = _serve(Ns, seeds, reqs, frac, 256 << 20, tuning)
@@ -140,3 +141,29 @@ def test_server_large_pools_split_into_units(orc, ppt):
     for rid, (c, cnt, mu, sg) in zip(ids, reqs):
         ref = oracles[c].fill(cnt, np.float32(mu), np.float32(sg))
         assert np.array_equal(srv.result_host(rid).view(np.uint32), ref.view(np.uint32)), (c, cnt)
+
+
+@pytest.mark.parametrize("ppt", [1, 2])
+def test_server_bulk_copy_runner(orc, ppt):
+    """ctas_per_sm = 0: requests on pools of 16384..65536 (N % 4 == 0) run the
+    bulk-copy runner on the second stream, beside shared-memory pools,
+    fallback strides (45060 = 2^2 3 5 751), ragged N and a pool split into
+    work units; every value exact."""
+    Ns = np.array([16384, 20000, 32768, 65536, 16388, 45060, 300, 3001, 16387, 70000], dtype=np.int64)
+    seeds = np.arange(31, 31 + Ns.size, dtype=np.uint32)
+    srv = W.Server(4, Ns, seeds, 1 / 3, 1 << 30)
+    srv.set_tuning(ppt, 4096, 0)
+    rng = np.random.default_rng(12)
+    reqs = [(int(rng.integers(0, Ns.size)), int(rng.integers(1, 300000)), float(rng.uniform(-2, 2)),
+             float(rng.uniform(0.5, 2))) for _ in range(60)]
+    ids = []
+    for k, (c, cnt, mu, sg) in enumerate(reqs):
+        ids.append(srv.submit(c, cnt, mu, sg))
+        if k % 4 == 3:
+            srv.progress()
+    srv.drain()
+    oracles = [orc.Generator(4, int(N), int(sd), 1 / 3) for N, sd in zip(Ns, seeds)]
+    for rid, (c, cnt, mu, sg) in zip(ids, reqs):
+        ref = oracles[c].fill(cnt, np.float32(mu), np.float32(sg))
+        got = srv.result_host(rid)
+        assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (c, int(Ns[c]), cnt)
