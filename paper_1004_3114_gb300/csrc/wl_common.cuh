@@ -522,35 +522,40 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
     st->ticket = 0;
 }
 
-// The same end-of-pass update as wl_finalise for a pass over a binary32 pool,
-// run by the whole last CTA: its three independent chains go to three warps
-// -- the scale (S and c, Eq. 3), the drift ratio (Section 8) and the next
-// pass's parameters -- so their binary64 divisions and square roots and the
-// parameter draw overlap.  rnu = sqrt(2 nu - 1), correctly rounded; xp points
-// at the withheld last value of the new pool.  Every thread of the CTA calls.
-__device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, int64_t nu, double rnu,
-                                       const float *xp, int msigns)
+// The same end-of-pass update as wl_finalise (a pass), run by the whole CTA:
+// its three independent chains go to three warps -- the scale (S and c,
+// Eq. 3), the drift ratio (Section 8) and the next pass's strides -- so their
+// binary64 divisions and square roots and the stride draw overlap.  xf()
+// returns the withheld last value of the new pool; rnu = sqrt(2 nu - 1),
+// correctly rounded (0: computed here); msigns: the generator draws sign
+// patterns.  Every thread of the CTA calls.  st may be the device state
+// (after the last-CTA ticket, whose acquire and CTA barrier order every
+// other CTA's writes before these reads) or a CTA's shared-memory copy.
+template <typename XF>
+__device__ inline void wl_finalise_par(WlDevState *st, int n, int64_t N, int64_t nu, double rnu, XF xf,
+                                       int msigns, bool fp64)
 {
     __shared__ double s_S, s_c;
     __shared__ int32_t s_flag[2];
     volatile WlDevState *vs = st;
     const int warp = threadIdx.x >> 5;
-    // The caller's last-CTA ticket (acquire by thread 0, then a CTA barrier)
-    // already orders every other CTA's writes before these reads.
     if ((threadIdx.x & 31) == 0 && warp < 3) {
         if (warp < 2) {
             uint64_t lo, hi;
             wl_acc_read(st, lo, hi);
-            const double q = __dmul_rn(__ull2double_rn(lo), 1.0 / 4294967296.0);
+            const double q = fp64 ? __dadd_rn(__ull2double_rn(hi),
+                                              __dmul_rn(__ull2double_rn(lo), 1.0 / 18446744073709551616.0))
+                                  : __dmul_rn(__ull2double_rn(lo), 1.0 / 4294967296.0);
             if (warp == 0) {
-                const uint32_t bad = (vs->acc_bad != 0u || hi != 0) ? 1u : 0u;
+                const uint32_t bad = (vs->acc_bad != 0u || (!fp64 && hi != 0)) ? 1u : 0u;
                 const int chi = vs->chi;
+                const double x = xf();
                 double S;
-                if (!chi) {
-                    const double xr = __dadd_rn((double)__ldcg(xp), rnu);
+                if (!chi && rnu > 0.0) {
+                    const double xr = __dadd_rn(x, rnu);
                     S = __dmul_rn(__dmul_rn(xr, xr), 0.5);
                 } else {
-                    S = wl_chi_sample(1, nu, (double)__ldcg(xp));
+                    S = wl_chi_sample(chi, nu, x);
                 }
                 double c = 1.0;
                 int32_t f = 0;
@@ -598,7 +603,7 @@ __device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, int64_t
         st->S_prev = s_S;
         st->have_prev = 1;
         st->status = vs->status | s_flag[0] | s_flag[1];
-        // the next pass reads these after this grid completes: no fence
+        // the next pass (another grid, or this CTA after a barrier) reads these
         st->acc0 = 0;
         st->acc1 = 0;
         st->acc2 = 0;
@@ -606,6 +611,14 @@ __device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, int64_t
         st->tile_ctr = 0;
         st->ticket = 0;
     }
+}
+
+// The grid-wide bulk-copy pass's form: binary32 pool, x read from the new
+// pool in device memory.
+__device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, int64_t nu, double rnu,
+                                       const float *xp, int msigns)
+{
+    wl_finalise_par(st, n, N, nu, rnu, [xp]() { return (double)__ldcg(xp); }, msigns, false);
 }
 
 // A generator's state kept in shared memory while one CTA runs its passes:

@@ -117,9 +117,9 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
         }
         wl_cta_reduce_to_state(lo, hi, bad, st, red);
         __syncthreads();
-        if (tid == 0)
-            wl_finalise(st, NSUB, N, (int64_t)nu, (double)dst[nu - 1], sizeof(T) == 8, WL_FIN_PASS, true,
-                        rnu);
+        const double xlast = (double)dst[nu - 1];
+        wl_finalise_par(st, NSUB, N, (int64_t)nu, rnu, [xlast]() { return xlast; }, st->msigns,
+                        sizeof(T) == 8);
         __syncthreads();
         T *t = src;
         src = dst;

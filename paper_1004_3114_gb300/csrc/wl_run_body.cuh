@@ -120,8 +120,8 @@ __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red, int32
         }
         wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
         __syncthreads();
-        if (tid == 0)
-            wl_finalise(d.st, NSUB, N, nu, (double)dst[nu - 1], false, WL_FIN_PASS, true, rnu);
+        const double xlast = (double)dst[nu - 1];
+        wl_finalise_par(d.st, NSUB, N, nu, rnu, [xlast]() { return xlast; }, d.st->msigns, false);
         float *t = src;
         src = dst;
         dst = t;
@@ -186,9 +186,8 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
         }
         wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
         __syncthreads();
-        if (tid == 0)
-            wl_finalise(d.st, NSUB, N, nu, (double)__ldcg(&dst[wl_phys(nu - 1, N, d.Np)]), false, WL_FIN_PASS,
-                        true, rnu);
+        const float *xp = &dst[wl_phys(nu - 1, N, d.Np)];
+        wl_finalise_par(d.st, NSUB, N, nu, rnu, [xp]() { return (double)__ldcg(xp); }, d.st->msigns, false);
         cur = 1 - cur;
     }
     return cur;

@@ -331,9 +331,8 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
         }
         wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
         __syncthreads();
-        if (tid == 0)
-            wl_finalise(d.st, 4, N, nu, (double)__ldcg(&dst[wl_phys(nu - 1, N, d.Np)]), false, WL_FIN_PASS,
-                        true, rnu);
+        const float *xp = &dst[wl_phys(nu - 1, N, d.Np)];
+        wl_finalise_par(d.st, 4, N, nu, rnu, [xp]() { return (double)__ldcg(xp); }, d.st->msigns, false);
         cur = 1 - cur;
     }
     return cur;
