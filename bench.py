@@ -36,7 +36,8 @@ BYTES_PER_PASS = 8 * NU + 4 * R          # pool read + pool write + returned out
 WORKLOAD = (f"Wallace pass, n=4, N=2^24 (2^26-value FP32 pool), A=J/2-I, seed {SEED}, "
             f"frac=1/2 (R=2^25 returned per pass, mu=0 sigma=1, written to HBM)")
 PROFILE = os.path.join(ROOT, "profiles", "wl_tma_pass_n4_N2p24.txt")
-KERNEL_SOURCES = ["paper_1004_3114_gb300/csrc/wl_tiled_tma.cu", "paper_1004_3114_gb300/csrc/wl_common.cuh"]
+KERNEL_SOURCES = ["paper_1004_3114_gb300/csrc/wl_tiled_tma.cu", "paper_1004_3114_gb300/csrc/wl_common.cuh",
+                  "paper_1004_3114_gb300/csrc/wl_tma_common.cuh"]
 
 
 def kernel_hash() -> str:
@@ -587,7 +588,7 @@ def variant_bench(steps: int = 2000, warmup: int = 5):
 
 
 def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
-                  power_of_two: bool = False):
+                  power_of_two: bool = False, count: int = 4096):
     """4096 generators, n = 4, N log-uniform on [2^8, 2^18], seeds 0..4095,
     frac = 1: `runs` batched launches of `passes_per_run` passes (autotuned,
     CUDA graph), against the same generators run one after another through
@@ -596,7 +597,7 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
     import torch
     from paper_1004_3114_gb300 import wallace as W
     from paper_1004_3114_gb300.workloads import batch_sizes
-    Ns = batch_sizes(power_of_two=power_of_two)
+    Ns = batch_sizes(count=count, power_of_two=power_of_two)
     seeds = np.arange(len(Ns), dtype=np.uint32)
     stream = torch.cuda.Stream()
     b = W.Batch(4, Ns, seeds, 1.0, stream=stream)
@@ -645,8 +646,8 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
     print(json.dumps({
         "metric": "batched generators: N(0,1) variates/s", "value": value, "unit": UNIT,
         "cpu_baseline": cpu,
-        "workload": f"4096 generators, n=4, N log-uniform on [2^8, 2^18]"
-                    f"{' (powers of two)' if power_of_two else ''}, seeds 0..4095, frac=1",
+        "workload": f"{count} generators, n=4, N log-uniform on [2^8, 2^18]"
+                    f"{' (powers of two)' if power_of_two else ''}, seeds 0..{count - 1}, frac=1",
         "sum_nu": nu_total, "passes": passes, "runs": runs, "ms": ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": kind,
@@ -717,6 +718,9 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="4096 uneven generators in one persistent launch vs one handle each")
     ap.add_argument("--pow2", action="store_true", help="with --batched: power-of-two pool sizes")
+    ap.add_argument("--batched-count", type=int, default=4096, help="with --batched: generators")
+    ap.add_argument("--batched-runs", type=int, default=10, help="with --batched: timed runs of 10 passes")
+    ap.add_argument("--variants-steps", type=int, default=2000, help="with --variants: passes per case")
     ap.add_argument("--variants", action="store_true",
                     help="RANN4 (n=2), per-pass sign patterns, Wilson-Hilferty and restarts on the default pool size")
     ap.add_argument("--boxmuller", action="store_true",
@@ -737,7 +741,7 @@ def main():
         precision_study()
         return
     if args.batched:
-        batched_bench(power_of_two=args.pow2)
+        batched_bench(power_of_two=args.pow2, count=args.batched_count, runs=args.batched_runs)
         return
     if args.small:
         small_config_bench()
@@ -746,7 +750,7 @@ def main():
         boxmuller_bench()
         return
     if args.variants:
-        variant_bench()
+        variant_bench(steps=args.variants_steps)
         return
     if args.serve:
         serve_bench(n_requests=args.serve_requests, rate=args.serve_rate,
