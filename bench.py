@@ -60,7 +60,7 @@ def profiled_traffic():
                     kv[k.strip()] = v.strip()
         if kv.get("kernel_source_sha256_16") != kernel_hash():
             return None
-        return float(kv["dram_bytes_per_launch_full_size"])
+        return float(kv["dram_bytes_per_launch_full_size"].split("#")[0])
     except (OSError, KeyError, ValueError):
         return None
 
