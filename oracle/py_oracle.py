@@ -81,6 +81,7 @@ def lib():
             "orc_restart_pool": (None, [C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, f32p]),
             "orc_boxmuller_stream": (None, [C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, C.c_float,
                                             C.c_float, f32p]),
+            "orc_stride_candidates": (C.c_int, [C.c_int, C.c_int64, i32p]),
             "orc_draw_params": (None, [C.c_int, C.c_int64, C.POINTER(C.c_uint64), i32p, i64p]),
             "orc_transform32": (None, [C.c_int, f32p, C.c_float, f32p]),
             "orc_transform64": (None, [C.c_int, f64p, C.c_double, f64p]),
@@ -157,6 +158,13 @@ def boxmuller_stream(seed: int, stream: int, offset: int, count: int, mu: float 
     out = np.empty(count, dtype=np.float32)
     lib().orc_boxmuller_stream(seed, stream, offset, count, np.float32(mu), np.float32(sigma), out)
     return out
+
+
+def stride_candidates(n: int, N: int) -> list[int]:
+    """Candidate strides of a pass for n = 4 or 8 (Sections 3 and 7), increasing."""
+    cand = np.zeros(11, dtype=np.int32)
+    k = lib().orc_stride_candidates(n, N, cand)
+    return [int(v) for v in cand[:k]]
 
 
 def draw_params(n: int, N: int, state: int) -> tuple[np.ndarray, np.ndarray, int]:

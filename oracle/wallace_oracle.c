@@ -204,20 +204,22 @@ void orc_boxmuller_stream(uint32_t seed, uint32_t stream, int64_t offset, int64_
  * Per-pass parameters (Eq. 1 and Eq. 2; Sections 3, 7 and 8).  The paper asks
  * for strides that are distinct, greater than one, odd, and coprime to N, and
  * offsets uniform on {0..N-1}, all redrawn every pass; RANN4 picks its two
- * strides from {3,5} and {7,11}.  Reading for n = 4 and n = 8 (the paper
- * gives only n = 2): the candidate strides are the odd divisors > 1 of 45
- * (n = 4: 3, 5, 9, 15, 45) or of 315 (n = 8: eleven values), so the lcm of
- * any pass's strides divides 45 or 315.  Sub-vector i draws one uniform U and
- * takes entry floor(U * k / 2^32) of the k candidates still available --
- * coprime to N and not yet used this pass, in table order -- so for N coprime
- * to the table every ordered choice of distinct strides is equally likely
- * (120 for n = 4).  If none is available, it takes the smallest odd number
- * > 1 coprime to N and not in use.  Then one uniform U gives the offset
+ * strides from {3,5} and {7,11}, and Section 7's vector gather wants strides
+ * whose common multiple is small.  Reading for n = 4 and n = 8 (the paper
+ * gives only n = 2): with p < q < r the three smallest odd primes that do not
+ * divide N, the candidate strides are the odd divisors > 1 of p^2 q (n = 4:
+ * five values) or of p^2 q r (n = 8: eleven values), in increasing order.
+ * Every candidate is then coprime to N and the lcm of any pass's strides
+ * divides p^2 q or p^2 q r; for N coprime to 15 the n = 4 set is
+ * {3, 5, 9, 15, 45}, and for N coprime to 105 the n = 8 set is the odd
+ * divisors of 315.  Sub-vector i draws one uniform U and takes entry
+ * floor(U * k / 2^32) of the k candidates not yet used this pass, in order,
+ * so every ordered choice of distinct strides is equally likely (120 for
+ * n = 4).  For n = 2 the candidates are RANN4's pair for the sub-vector,
+ * those coprime to N; if neither is, it takes the smallest odd number > 1
+ * coprime to N and not in use.  Then one uniform U gives the offset
  * floor(U * N / 2^32).
  * ------------------------------------------------------------------------ */
-static const int32_t ORC_CAND4[5] = {3, 5, 9, 15, 45};
-static const int32_t ORC_CAND8[11] = {3, 5, 7, 9, 15, 21, 35, 45, 63, 105, 315};
-
 static int64_t orc_gcd(int64_t a, int64_t b)
 {
     while (b != 0) {
@@ -238,15 +240,62 @@ static int orc_stride_ok(int32_t a, int64_t N, const int32_t *used, int nused)
     return 1;
 }
 
+/* The odd primes below 64.  The product of the first fifteen exceeds 2^63,
+ * so at most fourteen of them divide an N < 2^63 and at least three do not. */
+static const int32_t ORC_ODD_PRIMES[17] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61};
+
+/* Candidate strides of the reading above for n = 4 or 8, increasing; returns
+ * how many (5 or 11). */
+int orc_stride_candidates(int n, int64_t N, int32_t *cand)
+{
+    int32_t pr[3];
+    int np = 0;
+    const int need = n == 8 ? 3 : 2;
+    for (int k = 0; k < 17 && np < need; k++)
+        if (N % ORC_ODD_PRIMES[k] != 0)
+            pr[np++] = ORC_ODD_PRIMES[k];
+    /* odd divisors of p^2 q (r): p^e1 q^e2 r^e3, e1 <= 2, e2 <= 1, e3 <= 1 */
+    int nc = 0;
+    const int e3max = n == 8 ? 1 : 0;
+    for (int e1 = 0; e1 <= 2; e1++)
+        for (int e2 = 0; e2 <= 1; e2++)
+            for (int e3 = 0; e3 <= e3max; e3++) {
+                int32_t d = 1;
+                for (int t = 0; t < e1; t++)
+                    d *= pr[0];
+                if (e2)
+                    d *= pr[1];
+                if (e3)
+                    d *= pr[2];
+                if (d > 1)
+                    cand[nc++] = d;
+            }
+    /* insertion sort: increasing order */
+    for (int a = 1; a < nc; a++) {
+        int32_t v = cand[a];
+        int b = a - 1;
+        while (b >= 0 && cand[b] > v) {
+            cand[b + 1] = cand[b];
+            b--;
+        }
+        cand[b + 1] = v;
+    }
+    return nc;
+}
+
 /* n = 2 is RANN4 itself (Section 8): alpha from {3, 5} for x and beta from
  * {7, 11} for y, each drawn as above among the candidates still available. */
 static const int32_t ORC_CAND2[2][2] = {{3, 5}, {7, 11}};
 
 void orc_draw_params(int n, int64_t N, uint64_t *state, int32_t *alpha, int64_t *gamma)
 {
+    int32_t table[11];
+    int ntable = 0;
+    if (n != 2)
+        ntable = orc_stride_candidates(n, N, table);
     for (int i = 0; i < n; i++) {
-        const int32_t *cand = n == 4 ? ORC_CAND4 : (n == 8 ? ORC_CAND8 : ORC_CAND2[i]);
-        const int ncand = n == 4 ? 5 : (n == 8 ? 11 : 2);
+        const int32_t *cand = n == 2 ? ORC_CAND2[i] : table;
+        const int ncand = n == 2 ? 2 : ntable;
         uint32_t us = orc_lcg_next(state);
         int32_t avail[11];
         int na = 0;

@@ -72,6 +72,7 @@ void orc_box_muller(uint32_t u1, uint32_t u2, float *a, float *b);
 uint64_t orc_lcg_jump(uint64_t state, uint64_t steps);
 void orc_boxmuller_stream(uint32_t seed, uint32_t stream, int64_t offset, int64_t count,
                           float mu, float sigma, float *out);
+int orc_stride_candidates(int n, int64_t N, int32_t *cand);
 void orc_draw_params(int n, int64_t N, uint64_t *state, int32_t *alpha, int64_t *gamma);
 void orc_transform32(int n, const float *g, float c, float *y);
 void orc_transform64(int n, const double *g, double c, double *y);
