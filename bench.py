@@ -700,7 +700,7 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
                      "unit": "GB/s", "frac": bytes_moved / st.elapsed_s / 1e9 / peak, "peak_kind": kind,
                      "bytes_per_value": 28},
         "passes_per_tick": passes_per_tick, "ctas_per_sm": ctas_per_sm,
-        "runner": "bulk-copy for one-CTA requests on 16384 <= N (n=4, N % 4 == 0)" if ctas_per_sm == 0
+        "runner": "bulk-copy for one-CTA requests on 16384 <= N (n=4)" if ctas_per_sm == 0
                   else "async-copy", "create_s": create_s, "status": int(st.status)}), flush=True)
 
 

@@ -72,13 +72,15 @@ typedef struct wallace wallace_t;
 #define WALLACE_VARIANT_AUTO    0  /* pick by pool size                                 */
 #define WALLACE_VARIANT_GATHER  1  /* direct strided gather from HBM, one pass/launch   */
 #define WALLACE_VARIANT_TILED   2  /* lane-tiled gather staged in shared memory: the
-                                      bulk-copy (TMA) pipeline when N % 4 == 0, else
-                                      per-thread 16-byte async copies                 */
+                                      bulk-copy (TMA) pipeline when N % 4 == 0 and
+                                      (n = 4) N is coprime to 15, else per-thread
+                                      16-byte async copies                           */
 #define WALLACE_VARIANT_FUSED   3  /* whole pool in shared memory, many passes/launch   */
 #define WALLACE_VARIANT_TILED_ASYNC 4 /* lane-tiled, per-thread 16-byte async copies      */
 #define WALLACE_VARIANT_TILED_TMA   5 /* lane-tiled, warp-specialised bulk (TMA) copies
-                                         into a stage ring; needs N % 4 == 0 (else the
-                                         per-thread-copy kernel runs)                   */
+                                         into a stage ring; needs N % 4 == 0 and, for
+                                         n = 4, N coprime to 15 (else the per-thread-copy
+                                         kernel runs)                                   */
 
 /* Scalars of the most recent pass (or of the initial pool after create). */
 typedef struct {
@@ -283,9 +285,9 @@ int wallace_batch_get_pool(wallace_batch_t *b, int s, float *host_out);
  * (4 <= etarget <= 2560), and the largest pool (n*N values) kept in shared
  * memory across passes (at most ~8400 values fit).  ctas_per_sm = 0 selects
  * the bulk-copy runner instead: one CTA of 608 threads per SM, pools with
- * n = 4, N % 4 == 0 and N >= 16384 regenerated through a warp-specialised
- * stage ring fed by bulk (TMA) copies, the others as before (etarget and
- * fused_max apply to them).
+ * n = 4 and 16384 <= N <= 2^28 regenerated through a warp-specialised stage
+ * ring fed by bulk (TMA) copies, the others as before (etarget and fused_max
+ * apply to them).
  */
 int wallace_batch_set_tuning(wallace_batch_t *b, int ctas_per_sm, int etarget, int64_t fused_max);
 int wallace_batch_get_tuning(const wallace_batch_t *b, int *ctas_per_sm, int *etarget,
@@ -344,7 +346,7 @@ void wallace_server_destroy(wallace_server_t *s);
 /* wallace_server_set_tuning -- passes per request per tick (>= 1), the
  * largest pool kept in shared memory across passes, CTAs per SM.
  * ctas_per_sm = 0: three CTAs per SM as before, and the requests one CTA
- * serves whose pools have n = 4, N % 4 == 0, N >= 16384 run the bulk-copy
+ * serves whose pools have n = 4 and 16384 <= N <= 2^28 run the bulk-copy
  * (TMA) runner instead, one 608-thread CTA per SM on a second stream beside
  * the others.  Only while idle. */
 int wallace_server_set_tuning(wallace_server_t *s, int passes_per_tick, int64_t fused_max,

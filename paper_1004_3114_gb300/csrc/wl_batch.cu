@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
     ring.abort_flag = &s_abort;
     wl_tma_ring_init(ring);
     const int tid = threadIdx.x;
-    const int64_t smem_values = (int64_t)(wl_tma::tm_smem_bytes() / sizeof(float));
+    const int64_t smem_values = (int64_t)(wl_tma::tr_smem_bytes() / sizeof(float));
     while (true) {
         __syncthreads();
         if (tid == 0)
@@ -145,8 +145,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
         int cur;
         wl_state_load(&sst, d.st);
         r.st = &sst;
-        if (d.n == 4 && !wl_run_is_fused(4, d.N, a.fused_max, smem_values) && d.N >= TM_MIN_N &&
-            (d.N & 3) == 0 && d.N <= ((int64_t)1 << 28))
+        if (wl_tma_run_eligible(d.n, d.N) && !wl_run_is_fused(4, d.N, a.fused_max, smem_values))
             cur = wl_run_tma(r, smem, red, s_prm, ring);
         else
             cur = wl_run_spec(r, a.fused_max, smem_values, smem, red, s_prm);
@@ -225,7 +224,7 @@ cudaError_t ensure_configured()
                                          (int)tl_smem_bytes());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(batch_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)wl_tma::tm_smem_bytes());
+                                 (int)wl_tma::tr_smem_bytes());
     if (e == cudaSuccess)
         done = true;
     return e;
@@ -246,7 +245,7 @@ cudaError_t launch_graph(wallace_batch_t *b, const BatchArgs &args)
     kp.func = tma ? (void *)batch_tma_kernel : (void *)batch_kernel;
     kp.gridDim = dim3(ctas);
     kp.blockDim = dim3(tma ? TM_THREADS : BT_THREADS);
-    kp.sharedMemBytes = (unsigned)(tma ? wl_tma::tm_smem_bytes() : tl_smem_bytes());
+    kp.sharedMemBytes = (unsigned)(tma ? wl_tma::tr_smem_bytes() : tl_smem_bytes());
     kp.kernelParams = params;
     if (!b->exec || b->graph_ctas != ctas || b->graph_runner != b->tune.runner) {
         if (b->exec)

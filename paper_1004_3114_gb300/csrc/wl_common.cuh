@@ -68,6 +68,8 @@ struct WlDevState {
     int32_t msigns;         // 1: a random sign pattern per pass, matrix A D_k (set at creation)
     int32_t pad3_;
     int64_t passes;
+    int32_t cand[11];       // n = 4, 8: the stride candidates for this N, increasing (set at creation)
+    int32_t ncand;
     // next tile of the pass in flight (dynamically scheduled kernels): every
     // CTA takes tiles from it all pass long, so it has a cache line to itself
     alignas(128) uint32_t tile_ctr;
@@ -113,12 +115,15 @@ __device__ __forceinline__ uint64_t wl_lcg_jump(uint64_t s, uint64_t m)
 
 // ---- per-pass parameters ---------------------------------------------------
 // Strides are distinct, odd, > 1 and coprime to N (Eq. 2, Sections 3 and 7).
-// Candidates: the odd divisors > 1 of 45 (n = 4) or of 315 (n = 8), so one
-// pass's strides have lcm dividing 45 (315): the lane count of the tiled
-// kernels.  One uniform per sub-vector picks, by multiply-shift, among the
-// candidates still free (coprime to N, not yet used) in table order; with
-// none free, the smallest free odd number > 1 coprime to N.  The offset is
-// floor(U N / 2^32), uniform on {0..N-1}.
+// For n = 4 and 8 the candidates are the odd divisors > 1 of p^2 q (n = 4) or
+// p^2 q r (n = 8), p < q < r the smallest odd primes not dividing N: all
+// coprime to N, and one pass's strides have an lcm dividing p^2 q (p^2 q r),
+// the lane count of the tiled kernels -- 45 (315) when N is coprime to 15
+// (105).  One uniform per sub-vector picks, by multiply-shift, among the
+// candidates not yet used, in increasing order.  n = 2 is RANN4 itself
+// (Section 8): alpha from {3, 5} for x and beta from {7, 11} for y, those
+// coprime to N; with none free, the smallest free odd number > 1 coprime to
+// N.  The offset is floor(U N / 2^32), uniform on {0..N-1}.
 __device__ __forceinline__ int64_t wl_gcd(int64_t a, int64_t b)
 {
     while (b) {
@@ -139,32 +144,129 @@ __device__ __forceinline__ bool wl_stride_free(int32_t a, int64_t N, const int32
     return true;
 }
 
-// Every candidate divides 45 (315), so it is coprime to N exactly when N
-// shares none of its prime factors among 3, 5, 7: one bit per prime.  This
-// keeps the finaliser (one thread, between two passes) free of Euclid's
-// algorithm except in the rare fallback.
-//
-// n = 2 is RANN4 itself (Section 8): alpha from {3, 5} for x and beta from
-// {7, 11} for y, drawn the same way; 11's factor is not among the three bits,
-// so those tables are checked against N by Euclid.
-__device__ inline void wl_draw_params(int n, int64_t N, uint64_t &s, int32_t *alpha, int64_t *gamma)
+// The `need` smallest odd primes that do not divide N, from the odd primes
+// below 64 (at most fourteen of them divide an N < 2^63).  N mod P in 32-bit
+// arithmetic from N's halves (N = hi 2^32 + lo); N coprime to 15 takes two
+// tests.  A rolled loop: the finaliser runs inside kernels that keep many
+// registers live.
+__device__ __forceinline__ void wl_free_primes(uint64_t uN, int need, uint32_t &p, uint32_t &q, uint32_t &r)
 {
-    const int32_t div45[5] = {3, 5, 9, 15, 45};
-    const uint8_t fac45[5] = {1, 2, 1, 3, 3};            // bit 0: 3 | a, bit 1: 5 | a, bit 2: 7 | a
-    const int32_t div315[11] = {3, 5, 7, 9, 15, 21, 35, 45, 63, 105, 315};
-    const uint8_t fac315[11] = {1, 2, 4, 1, 3, 5, 6, 3, 5, 7, 7};
-    const int32_t rann4[2][2] = {{3, 5}, {7, 11}};
-    const uint64_t uN = (uint64_t)N;
-    const uint32_t nfac = (uN % 3u == 0 ? 1u : 0u) | (uN % 5u == 0 ? 2u : 0u) | (uN % 7u == 0 ? 4u : 0u);
+    constexpr uint32_t P[17] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61};
+    const uint32_t hi = (uint32_t)(uN >> 32), lo = (uint32_t)uN;
+    p = q = r = 0;
+    int got = 0;
+#pragma unroll 1
+    for (int k = 0; k < 17; k++) {
+        const uint32_t pk = P[k];
+        const uint32_t r32 = (0xffffffffu % pk + 1u) % pk;   // 2^32 mod pk
+        if (((hi % pk) * r32 + lo % pk) % pk != 0) {
+            if (got == 0)
+                p = P[k];
+            else if (got == 1)
+                q = P[k];
+            else
+                r = P[k];
+            if (++got == need)
+                break;
+        }
+    }
+}
+
+// The candidates for n = 4 (5 values) or n = 8 (11 values), increasing.
+__device__ inline int wl_stride_candidates(int n, int64_t N, int32_t *cand)
+{
+    uint32_t p, q, r;
+    wl_free_primes((uint64_t)N, n == 8 ? 3 : 2, p, q, r);
+    int nc = 0;
+    const int e3max = n == 8 ? 1 : 0;
+    for (int e1 = 0; e1 <= 2; e1++) {
+        const int32_t pe = e1 == 0 ? 1 : (e1 == 1 ? (int32_t)p : (int32_t)(p * p));
+        for (int e2 = 0; e2 <= 1; e2++)
+            for (int e3 = 0; e3 <= e3max; e3++) {
+                const int32_t d = pe * (e2 ? (int32_t)q : 1) * (e3 ? (int32_t)r : 1);
+                if (d > 1)
+                    cand[nc++] = d;
+            }
+    }
+    for (int a = 1; a < nc; a++) {
+        const int32_t v = cand[a];
+        int b = a - 1;
+        while (b >= 0 && cand[b] > v) {
+            cand[b + 1] = cand[b];
+            b--;
+        }
+        cand[b + 1] = v;
+    }
+    return nc;
+}
+
+// n = 4 or 8 from NC = 5 or 11 candidates c (increasing) held in registers:
+// a bit per candidate still free; sub-vector i takes the free candidate of
+// rank floor(U k / 2^32) among the k free ones.
+template <int NC>
+__device__ __forceinline__ void wl_pick_strides(int64_t N, uint64_t &s, int32_t *alpha, int64_t *gamma,
+                                                const int32_t (&c)[NC])
+{
+    constexpr int n = NC == 5 ? 4 : 8;
+    uint32_t avail = (1u << NC) - 1u;
+#pragma unroll(NC == 5 ? 4 : 1)
     for (int i = 0; i < n; i++) {
-        const int32_t *cand = n == 4 ? div45 : (n == 8 ? div315 : rann4[i]);
-        const uint8_t *fac = n == 4 ? fac45 : fac315;
-        const int ncand = n == 4 ? 5 : (n == 8 ? 11 : 2);
         const uint32_t u = wl_lcg_step(s);
-        int32_t freec[11];
+        const uint32_t pick = (uint32_t)(((uint64_t)u * (uint64_t)__popc(avail)) >> 32);
+        int32_t a = 0;
+        uint32_t bit = 0, seen = 0;
+#pragma unroll
+        for (int b = 0; b < NC; b++) {
+            const bool on = (avail >> b) & 1u;
+            if (on && seen == pick) {
+                a = c[b];
+                bit = 1u << b;
+            }
+            seen += on ? 1u : 0u;
+        }
+        avail &= ~bit;
+        alpha[i] = a;
+        const uint32_t v = wl_lcg_step(s);
+        gamma[i] = (int64_t)(((uint64_t)v * (uint64_t)N) >> 32);
+    }
+}
+
+// ctab: the generator's candidates (wl_stride_candidates at creation); N
+// coprime to 15 (n = 4) or 105 (n = 8) takes the same values as constants,
+// so the finaliser of such pools reads no memory here.
+__device__ inline void wl_draw_params(int n, int64_t N, uint64_t &s, int32_t *alpha, int64_t *gamma,
+                                      const int32_t *ctab)
+{
+    const uint64_t uN = (uint64_t)N;
+    const bool co15 = uN % 3u != 0 && uN % 5u != 0;
+    if (n == 4) {
+        int32_t c[5] = {3, 5, 9, 15, 45};
+        if (!co15) {
+#pragma unroll
+            for (int k = 0; k < 5; k++)
+                c[k] = ctab[k];
+        }
+        wl_pick_strides<5>(N, s, alpha, gamma, c);
+        return;
+    }
+    if (n == 8) {
+        int32_t c[11] = {3, 5, 7, 9, 15, 21, 35, 45, 63, 105, 315};
+        if (!co15 || uN % 7u == 0) {
+#pragma unroll
+            for (int k = 0; k < 11; k++)
+                c[k] = ctab[k];
+        }
+        wl_pick_strides<11>(N, s, alpha, gamma, c);
+        return;
+    }
+    const int32_t rann4[2][2] = {{3, 5}, {7, 11}};
+    for (int i = 0; i < n; i++) {
+        const int32_t *cand = rann4[i];
+        const uint32_t u = wl_lcg_step(s);
+        int32_t freec[2];
         int nf = 0;
-        for (int k = 0; k < ncand; k++) {
-            if (n == 2 ? wl_gcd(cand[k], N) != 1 : (fac[k] & nfac) != 0)
+        for (int k = 0; k < 2; k++) {
+            if (wl_gcd(cand[k], N) != 1)
                 continue;
             bool used = false;
             for (int t = 0; t < i; t++)
@@ -371,9 +473,9 @@ __device__ inline void wl_draw_rotation(uint64_t &s, double &cs, double &sn)
 }
 
 __device__ __forceinline__ void wl_draw_pass(int n, int64_t N, uint64_t &s, WlStrides &slot,
-                                             int msigns)
+                                             int msigns, const int32_t *ctab)
 {
-    wl_draw_params(n, N, s, slot.alpha, slot.gamma);
+    wl_draw_params(n, N, s, slot.alpha, slot.gamma, ctab);
     slot.signs = msigns ? wl_lcg_step(s) >> (32 - n) : 0u;
     if (n == 2)
         wl_draw_rotation(s, slot.rcos, slot.rsin);
@@ -406,7 +508,7 @@ __device__ inline void wl_advance_strides(WlDevState *st, int n, int64_t N, uint
     st->next.rsin = cur.rsin;
     st->lcg_rep = rep;
     st->lcg_pend = s;
-    wl_draw_pass(n, N, s, st->ahead[(k + 1) & 1], msigns);
+    wl_draw_pass(n, N, s, st->ahead[(k + 1) & 1], msigns, st->cand);
     st->lcg = s;
 }
 
@@ -498,9 +600,12 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
             st->last = st->next;
             st->passes += 1;
         } else {
-            // initial pool: draw the strides of the first pass as well
+            // initial pool: fix the stride candidates for this N, and draw
+            // the strides of the first pass as well
+            if (n != 2)
+                st->ncand = wl_stride_candidates(n, N, st->cand);
             rep = s;
-            wl_draw_pass(n, N, s, st->ahead[st->passes & 1], st->msigns);
+            wl_draw_pass(n, N, s, st->ahead[st->passes & 1], st->msigns, st->cand);
         }
         wl_advance_strides(st, n, N, s, rep, st->msigns);
     }

@@ -91,8 +91,7 @@ __global__ void __launch_bounds__(SV_THREADS, 3) serve_kernel(const ServeItem *i
 __host__ __device__ inline bool sv_bulk_eligible(int n, int64_t N, int64_t passes, int64_t fused_max,
                                                  int64_t smem_values)
 {
-    return n == 4 && passes > 0 && N >= TM_MIN_N && (N & 3) == 0 && N <= ((int64_t)1 << 28) &&
-           !wl_run_is_fused(n, N, fused_max, smem_values);
+    return passes > 0 && wl_tma_run_eligible(n, N) && !wl_run_is_fused(n, N, fused_max, smem_values);
 }
 
 // The same items with the CTA-local bulk-copy runner: one 608-thread CTA per
@@ -114,7 +113,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) serve_tma_kernel(const ServeIte
     ring.abort_flag = &s_abort;
     wl_tma_ring_init(ring);
     const int tid = threadIdx.x;
-    const int64_t smem_values = (int64_t)(wl_tma::tm_smem_bytes() / sizeof(float));
+    const int64_t smem_values = (int64_t)(wl_tma::tr_smem_bytes() / sizeof(float));
     while (true) {
         __syncthreads();
         if (tid == 0)
@@ -637,7 +636,7 @@ int enqueue_tick(wallace_server_t *s)
     });
     int nrest = (int)small.size();
     if (s->bulk) {
-        const int64_t tma_values = (int64_t)(wl_tma::tm_smem_bytes() / sizeof(float));
+        const int64_t tma_values = (int64_t)(wl_tma::tr_smem_bytes() / sizeof(float));
         auto mid = std::stable_partition(small.begin(), small.end(), [&](const ServeItem &it) {
             return !sv_bulk_eligible(it.spec.n, it.spec.N, it.spec.passes, s->fused_max, tma_values);
         });
@@ -687,7 +686,7 @@ int enqueue_tick(wallace_server_t *s)
         if (e == cudaSuccess)
             e = cudaStreamWaitEvent(s->aux, s->ev_fork, 0);
         if (e == cudaSuccess) {
-            serve_tma_kernel<<<std::min(s->sm_count, nbulk), TM_THREADS, wl_tma::tm_smem_bytes(), s->aux>>>(
+            serve_tma_kernel<<<std::min(s->sm_count, nbulk), TM_THREADS, wl_tma::tr_smem_bytes(), s->aux>>>(
                 (const ServeItem *)dw + nrest, nbulk, dq + SV_MAX_PPT + 1, s->fused_max);
             e = cudaGetLastError();
         }
@@ -800,7 +799,7 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
                                  (int)tl_smem_bytes());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(serve_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)wl_tma::tm_smem_bytes());
+                                 (int)wl_tma::tr_smem_bytes());
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking);
     if (e == cudaSuccess)

@@ -16,8 +16,8 @@
 // counterpart of the paper's odd strides for interleaved memory banks.
 //
 // Persistent kernel: CTA b handles tiles b, b + grid, ...  If a pass's
-// strides have L > 315 (fallback strides for N with small odd factors) the
-// same launch runs a plain strided gather.
+// strides have L > 315 (N a multiple of 15: the candidates divide 7^2 11 or a
+// larger p^2 q) the same launch runs a plain strided gather.
 #include "wl_launch.h"
 #include "wl_tiled_body.cuh"
 

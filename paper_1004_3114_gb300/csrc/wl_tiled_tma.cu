@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
 
     // n = 4: L = lcm of the strides when all divide 45 (3^e3 5^e5).  n = 2:
     // L = alpha beta for alpha in {3, 5}, beta in {7, 11}.  Any other stride
-    // (the coprimality fallback) sends the pass to the plain gather below.
+    // sends the pass to the plain gather below (n = 2 with N a multiple of 15
+    // or 77; the host sends n = 4 pools with other strides elsewhere).
     int L;
     bool tileable;
     if constexpr (NSUB == 4) {
@@ -486,7 +487,13 @@ bool wl_tma_supported(int n, int64_t N, int fp64, int sm_count)
 {
     // lane starts, span starts and slot offsets are held in 32-bit integers
     (void)sm_count;
-    return (n == 4 || n == 2) && !fp64 && N >= TM_MIN_N && (N & 3) == 0 && N <= ((int64_t)1 << 28);
+    // n = 4: N coprime to 15, so every stride divides 45 (other N take the
+    // per-thread tiled kernel, whose lanes go up to 315).  n = 2: any N; the
+    // rare N whose RANN4 pair is excluded (a multiple of 15 or 77) runs the
+    // in-kernel plain gather.
+    const bool strides45 = n == 4 ? (N % 3 != 0 && N % 5 != 0) : true;
+    return (n == 4 || n == 2) && !fp64 && strides45 && N >= TM_MIN_N && (N & 3) == 0 &&
+           N <= ((int64_t)1 << 28);
 }
 
 cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream)

@@ -3,7 +3,8 @@
 // wl_batch.cu), with the same lane-tiled geometry and warp-specialised stage
 // ring as the grid-wide kernel (wl_tiled_tma.cu) -- 4 producer warps issue
 // one bulk copy per span into TM_STAGES shared-memory stages, 15 consumer
-// warps own 3 lanes each -- but over all tiles of the pool in order, with the
+// warps own whole lanes (L <= 90) or take (lane, time) pairs -- but over all
+// tiles of the pool in order, for any N >= TM_MIN_N, with the
 // sum of squares and the chi-squared rescale (Eq. 3 of Brent's RANN4 paper)
 // done by the CTA itself, so no CTA waits for another.
 //
@@ -13,6 +14,8 @@
 // timeout the CTA records WALLACE_ETIMEOUT in the generator's state, waits
 // (bounded) for its copies in flight and runs no more bulk-copy passes.
 #pragma once
+
+#include <type_traits>
 
 #include "wl_run_body.cuh"
 #include "wl_tma_common.cuh"
@@ -40,29 +43,51 @@ __device__ inline void wl_tma_ring_init(WlTmaRing &r)
     r.it = 0;
 }
 
-// Lanes of the tiled geometry for these strides (lcm, all dividing 45), or 0
-// when a stride does not divide 45 (the coprimality fallback).
-__device__ __forceinline__ int wl_tma_lanes45(const int32_t *alpha)
+// Geometry limits of the runner.  The strides of a pass have lcm L dividing
+// p^2 q (p < q the smallest odd primes not dividing N): 45, 63, 99, 175, 275
+// or 539 unless 105 or 165 divides N.  With T = TM_ETARGET / L lane times a
+// tile still holds about TM_ETARGET values per sub-vector; the spans per tile
+// are sum_i L / alpha_i <= 77 + 49 + 11 + 7 for L = 539.
+#define TR_LMAX 539
+#define TR_MAXSPANS 144
+#define TR_SPAN_PAD 12   /* slot words per span beyond alpha T: 3 lead + 3 wrap shift, rounded to 4 */
+
+namespace wl_tma {
+
+// stage: span data, then per span its lead and shift, then its wrap threshold
+__host__ __device__ constexpr int tr_stage_data_words() { return 4 * TM_ETARGET + TR_SPAN_PAD * TR_MAXSPANS; }
+__host__ __device__ constexpr int tr_stage_words() { return tr_stage_data_words() + 2 * TR_MAXSPANS; }
+// common area: J[L + 1], lane table (4 rows of TR_LMAX), span starts
+__host__ __device__ constexpr int tr_common_words() { return (TR_LMAX + 1) + 4 * TR_LMAX + TR_MAXSPANS; }
+__host__ __device__ constexpr size_t tr_smem_bytes()
 {
-    int e3 = 0, e5 = 0;
-    for (int i = 0; i < 4; i++) {
-        const int al = alpha[i];
-        if (al != 3 && al != 5 && al != 9 && al != 15 && al != 45)
-            return 0;
-        if (al == 3 || al == 15)
-            e3 = max(e3, 1);
-        if (al == 9 || al == 45)
-            e3 = 2;
-        if (al == 5 || al == 15 || al == 45)
-            e5 = 1;
-    }
-    return (e3 == 2 ? 9 : (e3 == 1 ? 3 : 1)) * (e5 ? 5 : 1);
+    return sizeof(float) * (size_t)(TM_STAGES * tr_stage_words() + tr_common_words());
 }
 
-// One pass src -> dst of an n = 4 pool (N % 4 == 0, N >= TM_MIN_N) whose
-// strides have lcm L <= 45.  Every thread of the CTA calls; the terms of its
-// values are added to (lo, hi) and its bad-value flag to `bad`.  The pass's
-// returned values [0, w1) go to o (o may be null when w1 == 0).
+} // namespace wl_tma
+
+// Pools the bulk-copy runner takes: n = 4 and N in [TM_MIN_N, 2^28] (32-bit
+// lane, span and slot offsets; a span of at most TM_ETARGET values wraps at
+// most once).  A pass whose strides have lcm above TR_LMAX runs the plain
+// gather instead.  Other pools take the per-thread runners.
+__host__ __device__ inline bool wl_tma_run_eligible(int n, int64_t N)
+{
+    return n == 4 && N >= TM_MIN_N && N <= ((int64_t)1 << 28);
+}
+
+// One pass src -> dst of an n = 4 pool (a pool wl_tma_run_eligible accepts)
+// whose strides have lcm L <= TR_LMAX.  Every thread of the CTA calls; the
+// terms of its values are added to (lo, hi) and its bad-value flag to `bad`.
+// The pass's returned values [0, w1) go to o (o may be null when w1 == 0).
+//
+// Spans: each bulk copy starts at the 16-byte boundary at or below the span's
+// first address (its lead, 0..3 values, is recorded per stage).  A span that
+// runs past the end of its row is copied in two parts: [as, N4) with N4 = N
+// rounded up to a multiple of 4 (the row pitch leaves room past N), then the
+// wrapped part from the row start, placed right after it.  Values of the span
+// at slot positions from N - as on therefore sit N4 - N further on: each span
+// records that threshold and shift, and the consumers add the shift to
+// positions at or past the threshold (the shift is 0 when 4 divides N).
 __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, int64_t Np, int L,
                                        const int32_t *alpha, const int64_t *gam, float c, float *o,
                                        int64_t w1, float mu, float sigma, float *smem, WlTmaRing &ring,
@@ -83,15 +108,15 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
     slot0[0] = 0;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        SL[i] = (alpha[i] * T + 8 + 3) & ~3;   // 16-byte aligned slots; wrap copies need +6
+        SL[i] = (alpha[i] * T + TR_SPAN_PAD) & ~3;   // 16-byte aligned slots
         if (i < 3)
             slot0[i + 1] = slot0[i] + m[i] * SL[i];
     }
     float *stage0 = smem;
-    int *common = (int *)(smem + TM_STAGES * tm_stage_words());
+    int *common = (int *)(smem + TM_STAGES * tr_stage_words());
     int *J = common;
-    int *lanebase = J + (TM_LMAX2 + 1);
-    int *spanC = lanebase + 4 * TM_LMAX;
+    int *lanebase = J + (TR_LMAX + 1);
+    int *spanC = lanebase + 4 * TR_LMAX;
 
     // the previous pass's readers of the tables are done
     __syncthreads();
@@ -107,92 +132,125 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         spanC[s] = p * qN + tm_divc(p * rN + mi - 1, mi);
     }
     __syncthreads();
+    // lane l, sub-vector i: slot position of its first value (before the
+    // span's lead) in bits 8.., its span in bits 0..7
     for (int e = tid; e < 4 * L; e += TM_THREADS) {
         int i = tm_divc(e, L), l = e - i * L;
         int w = tm_divc(l, m[i]), p = l - w * m[i];
         int64_t r = (int64_t)alpha[i] * J[l] - (int64_t)w * N - spanC[sb[i] + p];
-        lanebase[i * TM_LMAX + l] = ((slot0[i] + p * SL[i] + (int)r) << 5) | (sb[i] + p);
+        lanebase[i * TR_LMAX + l] = ((slot0[i] + p * SL[i] + (int)r) << 8) | (sb[i] + p);
     }
     __syncthreads();
     const int maxlen = tm_divc(N32 + L - 1, L);
     const int ntiles = (maxlen + T - 1) / T;
     const int it0 = ring.it;
+    const int N4 = (N32 + 3) & ~3;
 
     if (warp >= TM_CONS_WARPS) {
-        // ---------------- producer warps ----------------
-        const int sp = (warp - TM_CONS_WARPS) + TM_PROD_WARPS * lane;
-        const bool owner = sp < nspans;
-        int sp_i = 0, sp_alpha = 0;
-        int64_t sp_gam = 0, sp_C = 0;
-        uint32_t sp_doff = 0;
-        const float *sp_row = src;
-        if (owner) {
-            sp_i = tm_sub<4>(sp, sb);
-            const int sp_p = sp - sb[sp_i];
-            sp_alpha = alpha[sp_i];
-            sp_gam = gam[sp_i];
-            sp_C = spanC[sp];
-            sp_doff = 4u * (uint32_t)(slot0[sp_i] + sp_p * SL[sp_i]);
-            sp_row = src + (int64_t)sp_i * Np;
-        }
-        const uint32_t stage_base = smem_u32(stage0);
-        int issued_last = -1;   // last ring use this thread issued
-        for (int tile = 0; tile < ntiles; tile++) {
-            const int g = it0 + tile, s = g % TM_STAGES, u = g / TM_STAGES;
-            if (*ring.abort_flag)
-                break;
-            if (u > 0 && !mbar_wait(smem_u32(&ring.empty[s]), (uint32_t)((u - 1) & 1))) {
-                *ring.abort_flag = 1;
-                atomicOr(&st->status, WL_ETIMEOUT);
-                break;
-            }
-            const int t0 = tile * T;
-            const int Tt = min(T, maxlen - t0);
-            int *lead = (int *)(stage0 + s * tm_stage_words() + tm_stage_data_words());
-            const uint32_t full = smem_u32(&ring.full[s]);
-            const uint32_t d = stage_base + 4u * (uint32_t)(s * tm_stage_words()) + sp_doff;
-            int64_t addr = 0;
-            int len = 0, as = 0;
-            uint32_t bytes = 0;
-            bool wrap = false;
-            if (owner) {
-                addr = sp_C + (int64_t)sp_alpha * t0 + sp_gam;   // < 3N
-                if (addr >= N)
-                    addr -= N;
-                if (addr >= N)
-                    addr -= N;
-                len = sp_alpha * Tt;
-                as = (int)addr & ~3;
-                lead[sp] = (int)addr - as;
-                wrap = addr + len > N;
-                bytes = wrap ? 4u * (uint32_t)((int)N - as) + 4u * (uint32_t)(((int)(addr + len - N) + 3) & ~3)
-                             : 16u * (uint32_t)(((int)addr - as + len + 3) >> 2);
-            }
-            uint32_t total = bytes;
+        // ---------------- producer warps: spans ptid, ptid + 128 (KS per thread) ----------------
+        const int ptid = (warp - TM_CONS_WARPS) + TM_PROD_WARPS * lane;
+        auto produce = [&](auto ksc) {
+            constexpr int KS = decltype(ksc)::value;
+            int sp_alpha[KS];
+            int64_t sp_gam[KS], sp_C[KS];
+            uint32_t sp_doff[KS];
+            const float *sp_row[KS];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
-                total += __shfl_xor_sync(0xffffffffu, total, off);
-            if (lane == 0)
-                mbar_expect_tx(full, total);
-            __syncwarp();
-            if (owner) {
-                if (!wrap) {
-                    bulk_g2s(d, sp_row + as, bytes, full);
-                } else {
-                    const int e2 = ((int)(addr + len - N) + 3) & ~3;
-                    bulk_g2s(d, sp_row + as, 4u * (uint32_t)((int)N - as), full);
-                    bulk_g2s(d + 4u * (uint32_t)((int)N - as), sp_row, 4u * (uint32_t)e2, full);
+            for (int k = 0; k < KS; k++) {
+                const int sp = ptid + 32 * TM_PROD_WARPS * k;
+                sp_alpha[k] = 0;
+                sp_gam[k] = 0;
+                sp_C[k] = 0;
+                sp_doff[k] = 0;
+                sp_row[k] = src;
+                if (sp < nspans) {
+                    const int i = tm_sub<4>(sp, sb);
+                    const int p = sp - sb[i];
+                    sp_alpha[k] = alpha[i];
+                    sp_gam[k] = gam[i];
+                    sp_C[k] = spanC[sp];
+                    sp_doff[k] = (uint32_t)(slot0[i] + p * SL[i]);
+                    sp_row[k] = src + (int64_t)i * Np;
                 }
             }
-            mbar_arrive(full);
-            issued_last = g;
-        }
-        if (*ring.abort_flag) {
-            // copies still in flight must land before the CTA moves on
-            for (int g = max(it0, issued_last - TM_STAGES + 1); g <= issued_last; g++)
-                if (!mbar_wait(smem_u32(&ring.full[g % TM_STAGES]), (uint32_t)((g / TM_STAGES) & 1)))
+            const uint32_t stage_base = smem_u32(stage0);
+            int issued_last = -1;   // last ring use this thread issued
+            for (int tile = 0; tile < ntiles; tile++) {
+                const int g = it0 + tile, s = g % TM_STAGES, u = g / TM_STAGES;
+                if (*ring.abort_flag)
+                    break;
+                if (u > 0 && !mbar_wait(smem_u32(&ring.empty[s]), (uint32_t)((u - 1) & 1))) {
+                    *ring.abort_flag = 1;
                     atomicOr(&st->status, WL_ETIMEOUT);
-        }
+                    break;
+                }
+                const int t0 = tile * T;
+                const int Tt = min(T, maxlen - t0);
+                float *sdata = stage0 + s * tr_stage_words();
+                int *info0 = (int *)(sdata + tr_stage_data_words());   // lead | shift << 2
+                int *info1 = info0 + TR_MAXSPANS;                       // wrap threshold (slot position)
+                const uint32_t full = smem_u32(&ring.full[s]);
+                const uint32_t dbase = stage_base + 4u * (uint32_t)(s * tr_stage_words());
+                int as[KS], e2[KS];
+                uint32_t b1[KS];
+                uint32_t total = 0;
+#pragma unroll
+                for (int k = 0; k < KS; k++) {
+                    const int sp = ptid + 32 * TM_PROD_WARPS * k;
+                    as[k] = 0;
+                    e2[k] = 0;
+                    b1[k] = 0;
+                    if (sp < nspans) {
+                        int64_t addr = sp_C[k] + (int64_t)sp_alpha[k] * t0 + sp_gam[k];   // < 3N
+                        if (addr >= N)
+                            addr -= N;
+                        if (addr >= N)
+                            addr -= N;
+                        const int len = sp_alpha[k] * Tt;
+                        as[k] = (int)addr & ~3;
+                        if (addr + len > N) {
+                            // [as, N4), then [0, e2) at slot position N4 - as
+                            e2[k] = ((int)(addr + len - N) + 3) & ~3;
+                            b1[k] = 4u * (uint32_t)(N4 - as[k]);
+                            info0[sp] = ((int)addr - as[k]) | ((N4 - N32) << 2);
+                            info1[sp] = (int)sp_doff[k] + (N32 - as[k]);
+                        } else {
+                            b1[k] = 16u * (uint32_t)(((int)addr - as[k] + len + 3) >> 2);
+                            info0[sp] = (int)addr - as[k];
+                            info1[sp] = 0x7fffffff;
+                        }
+                        total += b1[k] + 4u * (uint32_t)e2[k];
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    total += __shfl_xor_sync(0xffffffffu, total, off);
+                if (lane == 0)
+                    mbar_expect_tx(full, total);
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < KS; k++) {
+                    if (b1[k]) {
+                        const uint32_t d = dbase + 4u * sp_doff[k];
+                        bulk_g2s(d, sp_row[k] + as[k], b1[k], full);
+                        if (e2[k])
+                            bulk_g2s(d + b1[k], sp_row[k], 4u * (uint32_t)e2[k], full);
+                    }
+                }
+                mbar_arrive(full);
+                issued_last = g;
+            }
+            if (*ring.abort_flag) {
+                // copies still in flight must land before the CTA moves on
+                for (int g = max(it0, issued_last - TM_STAGES + 1); g <= issued_last; g++)
+                    if (!mbar_wait(smem_u32(&ring.full[g % TM_STAGES]), (uint32_t)((g / TM_STAGES) & 1)))
+                        atomicOr(&st->status, WL_ETIMEOUT);
+            }
+        };
+        if (nspans > 32 * TM_PROD_WARPS)
+            produce(std::integral_constant<int, 2>{});
+        else
+            produce(std::integral_constant<int, 1>{});
     } else {
         // ---------------- consumer warps ----------------
         float *dstk[4], *outk[4];
@@ -203,66 +261,134 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
             ret[k] = (int64_t)(k + 1) * N <= w1;
             outk[k] = ret[k] ? o + k * N : o;
         }
-        uint32_t emax = 0;
-        for (int tile = 0; tile < ntiles; tile++) {
-            const int g = it0 + tile, s = g % TM_STAGES, u = g / TM_STAGES;
-            if (*ring.abort_flag)
-                break;
-            if (!mbar_wait(smem_u32(&ring.full[s]), (uint32_t)(u & 1))) {
-                *ring.abort_flag = 1;
-                atomicOr(&st->status, WL_ETIMEOUT);
-                break;
-            }
-            const int t0 = tile * T;
-            const int Tt = min(T, maxlen - t0);
-            const float *sdata = stage0 + s * tm_stage_words();
-            const int *lead = (const int *)(sdata + tm_stage_data_words());
-            uint64_t tl = 0;   // this tile's terms: at most 24 per thread, each below 2^48
-            for (int l = warp; l < L; l += TM_CONS_WARPS) {
-                const int jl = J[l];
-                const int tmax = min(Tt, J[l + 1] - jl - t0);
-                const float *gp[4];
+        // transform, store, sum of squares and returned values of one tuple
+        auto emit = [&](const float *gv, int64_t j, uint64_t &tl, uint32_t &emax) {
+            float y[4];
+            wl_xform4(gv, c, y);
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const int lb = lanebase[i * TM_LMAX + l];
-                    gp[i] = sdata + (lb >> 5) + lead[lb & 31];
+            for (int kk = 0; kk < 4; kk++) {
+                dstk[kk][j] = y[kk];
+                tl += term32(y[kk], emax);
+                if (ret[kk]) {
+                    outk[kk][j] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
+                } else {
+                    const int64_t q = kk * N + j;
+                    if (q < w1)
+                        o[q] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
                 }
-                const int64_t jb = (int64_t)jl + t0;
-                for (int t = lane; t < tmax; t += 64) {
-                    const bool v2 = t + 32 < tmax;
-                    float gv[4], h[4], y[4], z[4];
+            }
+        };
+        const uint32_t magicT = tl_magic((uint32_t)T);
+        uint32_t emax = 0;
+        const bool shifted = N4 != N32;   // wrapped spans sit shifted past their threshold
+        {
+            for (int tile = 0; tile < ntiles; tile++) {
+                const int g = it0 + tile, s = g % TM_STAGES, u = g / TM_STAGES;
+                if (*ring.abort_flag)
+                    break;
+                if (!mbar_wait(smem_u32(&ring.full[s]), (uint32_t)(u & 1))) {
+                    *ring.abort_flag = 1;
+                    atomicOr(&st->status, WL_ETIMEOUT);
+                    break;
+                }
+                const int t0 = tile * T;
+                const int Tt = min(T, maxlen - t0);
+                const float *sdata = stage0 + s * tr_stage_words();
+                const int *info0 = (const int *)(sdata + tr_stage_data_words());
+                const int *info1 = info0 + TR_MAXSPANS;
+                uint64_t tl = 0;   // this tile's terms: at most 40 per thread, each below 2^48
+                // L <= 90: each warp owns whole lanes, 64 lane times per step
+                auto lane_loop = [&](auto shc) {
+                    constexpr bool SH = decltype(shc)::value;
+                    for (int l = warp; l < L; l += TM_CONS_WARPS) {
+                        const int jl = J[l];
+                        const int tmax = min(Tt, J[l + 1] - jl - t0);
+                        int gb[4], thr[4], sh[4];
 #pragma unroll
-                    for (int i = 0; i < 4; i++) {
-                        gv[i] = gp[i][alpha[i] * t];
-                        h[i] = v2 ? gp[i][alpha[i] * (t + 32)] : 0.f;
-                    }
-                    wl_xform4(gv, c, y);
-                    wl_xform4(h, c, z);
-                    const int64_t j = jb + t;
+                        for (int i = 0; i < 4; i++) {
+                            const int lb = lanebase[i * TR_LMAX + l];
+                            const int f0 = info0[lb & 255];
+                            gb[i] = (lb >> 8) + (f0 & 3);
+                            sh[i] = f0 >> 2;
+                            thr[i] = info1[lb & 255];
+                        }
+                        const int64_t jb = (int64_t)jl + t0;
+                        for (int t = lane; t < tmax; t += 64) {
+                            // two independent values per thread: t and t + 32
+                            const bool v2 = t + 32 < tmax;
+                            float gv[4], hv[4];
 #pragma unroll
-                    for (int kk = 0; kk < 4; kk++) {
-                        dstk[kk][j] = y[kk];
-                        if (v2) dstk[kk][j + 32] = z[kk];
-                        tl += term32(y[kk], emax);
-                        if (v2) tl += term32(z[kk], emax);
-                        if (ret[kk]) {
-                            outk[kk][j] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
-                            if (v2) outk[kk][j + 32] = __fadd_rn(mu, __fmul_rn(sigma, z[kk]));
-                        } else {
-                            const int64_t q = kk * N + j;
-                            if (q < w1)
-                                o[q] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
-                            if (v2 && q + 32 < w1)
-                                o[q + 32] = __fadd_rn(mu, __fmul_rn(sigma, z[kk]));
+                            for (int i = 0; i < 4; i++) {
+                                int q = gb[i] + alpha[i] * t;
+                                int q2 = q + alpha[i] * 32;
+                                if constexpr (SH) {
+                                    q += q >= thr[i] ? sh[i] : 0;
+                                    q2 += q2 >= thr[i] ? sh[i] : 0;
+                                }
+                                gv[i] = sdata[q];
+                                hv[i] = v2 ? sdata[q2] : 0.f;
+                            }
+                            // both tuples' stores interleaved: each row gets
+                            // 256 contiguous bytes per warp at once
+                            float y[4], z[4];
+                            wl_xform4(gv, c, y);
+                            wl_xform4(hv, c, z);
+                            const int64_t j = jb + t;
+#pragma unroll
+                            for (int kk = 0; kk < 4; kk++) {
+                                dstk[kk][j] = y[kk];
+                                if (v2)
+                                    dstk[kk][j + 32] = z[kk];
+                                tl += term32(y[kk], emax);
+                                if (v2)
+                                    tl += term32(z[kk], emax);
+                                if (ret[kk]) {
+                                    outk[kk][j] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
+                                    if (v2)
+                                        outk[kk][j + 32] = __fadd_rn(mu, __fmul_rn(sigma, z[kk]));
+                                } else {
+                                    const int64_t q = kk * N + j;
+                                    if (q < w1)
+                                        o[q] = __fadd_rn(mu, __fmul_rn(sigma, y[kk]));
+                                    if (v2 && q + 32 < w1)
+                                        o[q + 32] = __fadd_rn(mu, __fmul_rn(sigma, z[kk]));
+                                }
+                            }
                         }
                     }
+                };
+                if (T >= 32) {
+                    if (shifted)
+                        lane_loop(std::true_type{});
+                    else
+                        lane_loop(std::false_type{});
+                } else {
+                    // short tiles: threads take (lane, time) pairs, times fastest
+                    const int npairs = L * T;
+                    for (int f = tid; f < npairs; f += TM_CONS_THREADS) {
+                        const int l = (int)tl_div((uint32_t)f, (uint32_t)T, magicT);
+                        const int t = f - l * T;
+                        const int jl = J[l];
+                        if (t >= Tt || t0 + t >= J[l + 1] - jl)
+                            continue;
+                        float gv[4];
+#pragma unroll
+                        for (int i = 0; i < 4; i++) {
+                            const int lb = lanebase[i * TR_LMAX + l];
+                            const int f0 = info0[lb & 255];
+                            int q = (lb >> 8) + (f0 & 3) + alpha[i] * t;
+                            q += q >= info1[lb & 255] ? (f0 >> 2) : 0;
+                            gv[i] = sdata[q];
+                        }
+                        emit(gv, (int64_t)jl + t0 + t, tl, emax);
+                    }
                 }
+                lo += tl;
+                hi += lo < tl ? 1ull : 0ull;
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(smem_u32(&ring.empty[s]));
             }
-            lo += tl;
-            hi += lo < tl ? 1ull : 0ull;
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(smem_u32(&ring.empty[s]));
         }
         bad |= emax >= 135u ? 1u : 0u;
         // the next pass reads this pool with bulk copies (the async proxy)
@@ -271,9 +397,9 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
     ring.it = it0 + ntiles;
 }
 
-// All passes of the spec (n = 4, N % 4 == 0, N >= TM_MIN_N) from global
-// memory through the bulk-copy pass; a pass whose strides do not all divide
-// 45 takes the plain gather.  Returns the index of the buffer holding the
+// All passes of the spec (a pool wl_tma_run_eligible accepts) from global
+// memory through the bulk-copy pass; a pass whose strides have lcm above
+// TR_LMAX takes the plain gather.  Returns the index of the buffer holding the
 // final pool.  s_prm: at least 9 words of shared memory.
 __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red, int32_t *s_prm,
                                  WlTmaRing &ring)
@@ -305,8 +431,8 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
         const int64_t w1 = o ? (p + 1 < d.passes ? d.R : d.last_take) : 0;
         uint64_t lo = 0, hi = 0;
         uint32_t bad = 0;
-        const int L = wl_tma_lanes45(alpha);
-        if (L > 0 && !*ring.abort_flag) {
+        const int L = wl_lcm4(alpha);
+        if (L <= TR_LMAX && !*ring.abort_flag) {
             wl_tma_pass_cta(src, dst, N, d.Np, L, alpha, gam, c, o, w1, d.mu, d.sigma, smem, ring, d.st,
                             lo, hi, bad);
         } else {

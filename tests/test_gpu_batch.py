@@ -53,14 +53,29 @@ def test_batch_n4_mixed_sizes_matches_oracle(orc, bulk):
 @pytest.mark.parametrize("tuning", [(1, 1280, 0), (3, 2560, 8192), (2, 640, 2048), (0, 2560, 4096),
                                     (0, 1280, 0)])
 def test_batch_tunings_give_identical_streams(orc, tuning):
-    """ctas_per_sm = 0: the bulk-copy runner (pools 30000, 65536, 100004 and
-    16384 take the stage ring; 45060 = 2^2 3 5 751 has fallback strides and
-    takes the plain gather inside it)."""
+    """ctas_per_sm = 0: the bulk-copy runner (pools 30000, 65536, 100004,
+    16384 and 45060 take the stage ring; 45060 = 2^2 3 5 751 has strides
+    from the divisors of 7^2 11, lanes up to 539)."""
     Ns = [300, 2000, 9000, 30000, 65536, 5001, 100004, 16384, 45060]
     seeds = [5, 6, 7, 8, 9, 10, 11, 12, 13]
     b = W.Batch(4, Ns, seeds, 0.5)
     b.set_tuning(*tuning)
     _check_batch(orc, b, Ns, seeds, 0.5, 4, runs=[2, 3])
+
+
+@pytest.mark.parametrize("tuning", [(0, 2560, 4096), (2, 2560, 2048)])
+def test_batch_bulk_runner_any_n_and_lane_count(orc, tuning):
+    """The bulk-copy runner on pools of every residue mod 4 (wrapping spans
+    shifted past N) and every lane count of the stride sets: 16387 (45 lanes,
+    N = 3 mod 4), 16386 = 2 3 2731 (divisors of 175), 20005 = 5 4001 (63),
+    17500 = 2^2 5^4 7 (99), 21504 = 2^10 3 7 (275), 16410 = 2 3 5 547 (539)
+    and 21000 = 2^3 3 5^3 7 (1573 > 539: the plain gather inside the runner).
+    The per-thread runner on the same pools gives the same streams."""
+    Ns = [16387, 16386, 20005, 17500, 21504, 16410, 21000, 16389]
+    seeds = [21, 22, 23, 24, 25, 26, 27, 28]
+    b = W.Batch(4, Ns, seeds, 0.5)
+    b.set_tuning(*tuning)
+    _check_batch(orc, b, Ns, seeds, 0.5, 4, runs=[2, 3], mu=-1.0, sigma=0.5)
 
 
 def test_batch_n8(orc):
