@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
     __shared__ uint64_t red[3 * (TM_THREADS / 32 + 1)];
     __shared__ int32_t s_prm[20];
     __shared__ int s_k;
-    __shared__ __align__(8) uint64_t bar_full[TM_STAGES];
-    __shared__ __align__(8) uint64_t bar_empty[TM_STAGES];
+    __shared__ __align__(8) uint64_t bar_full[TR_STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[TR_STAGES];
     __shared__ volatile int s_abort;
     __shared__ WlDevState sst;   // the running generator's state
     WlTmaRing ring;

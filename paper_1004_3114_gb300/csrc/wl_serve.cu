@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1) serve_tma_kernel(const ServeIte
     __shared__ uint64_t red[3 * (TM_THREADS / 32 + 1)];
     __shared__ int32_t s_prm[20];
     __shared__ int s_k;
-    __shared__ __align__(8) uint64_t bar_full[TM_STAGES];
-    __shared__ __align__(8) uint64_t bar_empty[TM_STAGES];
+    __shared__ __align__(8) uint64_t bar_full[TR_STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[TR_STAGES];
     __shared__ volatile int s_abort;
     __shared__ WlDevState sst;   // the running request's generator state
     WlTmaRing ring;

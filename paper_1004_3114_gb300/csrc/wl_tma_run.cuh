@@ -2,7 +2,7 @@
 // runs every pass of one n = 4 generator itself (the batched generators of
 // wl_batch.cu), with the same lane-tiled geometry and warp-specialised stage
 // ring as the grid-wide kernel (wl_tiled_tma.cu) -- 4 producer warps issue
-// one bulk copy per span into TM_STAGES shared-memory stages, 15 consumer
+// one bulk copy per span into TR_STAGES shared-memory stages, 15 consumer
 // warps own whole lanes (L <= 90) or take (lane, time) pairs -- but over all
 // tiles of the pool in order, for any N >= TM_MIN_N, with the
 // sum of squares and the chi-squared rescale (Eq. 3 of Brent's RANN4 paper)
@@ -20,8 +20,23 @@
 #include "wl_run_body.cuh"
 #include "wl_tma_common.cuh"
 
+// Ring shape: two stages of up to TR_ETARGET values per sub-vector.  Longer
+// tiles than the grid-wide kernel's (2880 in three stages) give lane counts
+// above 45 lanes of at least 24 values (L <= 220), hence whole-lane
+// consumers and fewer, longer bulk copies; the whole shared-memory block
+// (about 192 KiB) still leaves the L1 share the plain-gather pools rely on.
+#ifndef TR_STAGES
+#define TR_STAGES 2
+#endif
+#ifndef TR_ETARGET
+#define TR_ETARGET 5280  /* values per sub-vector per tile: L T <= this */
+#endif
+#ifndef TR_LANE_MIN_T
+#define TR_LANE_MIN_T 24 /* consumers own whole lanes when T is at least this */
+#endif
+
 struct WlTmaRing {
-    uint64_t *full, *empty;    // TM_STAGES mbarriers each, in shared memory
+    uint64_t *full, *empty;    // TR_STAGES mbarriers each, in shared memory
     int it;                    // stage uses so far
     volatile int *abort_flag;  // shared: a wait timed out in this CTA
 };
@@ -31,7 +46,7 @@ __device__ inline void wl_tma_ring_init(WlTmaRing &r)
 {
     using namespace wl_tma;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TM_STAGES; s++) {
+        for (int s = 0; s < TR_STAGES; s++) {
             mbar_init(smem_u32(&r.full[s]), 32 * TM_PROD_WARPS);
             mbar_init(smem_u32(&r.empty[s]), TM_CONS_WARPS);
         }
@@ -45,8 +60,8 @@ __device__ inline void wl_tma_ring_init(WlTmaRing &r)
 
 // Geometry limits of the runner.  The strides of a pass have lcm L dividing
 // p^2 q (p < q the smallest odd primes not dividing N): 45, 63, 99, 175, 275
-// or 539 unless 105 or 165 divides N.  With T = TM_ETARGET / L lane times a
-// tile still holds about TM_ETARGET values per sub-vector; the spans per tile
+// or 539 unless 105 or 165 divides N.  With T = TR_ETARGET / L lane times a
+// tile still holds about TR_ETARGET values per sub-vector; the spans per tile
 // are sum_i L / alpha_i <= 77 + 49 + 11 + 7 for L = 539.
 #define TR_LMAX 539
 #define TR_MAXSPANS 144
@@ -55,19 +70,19 @@ __device__ inline void wl_tma_ring_init(WlTmaRing &r)
 namespace wl_tma {
 
 // stage: span data, then per span its lead and shift, then its wrap threshold
-__host__ __device__ constexpr int tr_stage_data_words() { return 4 * TM_ETARGET + TR_SPAN_PAD * TR_MAXSPANS; }
+__host__ __device__ constexpr int tr_stage_data_words() { return 4 * TR_ETARGET + TR_SPAN_PAD * TR_MAXSPANS; }
 __host__ __device__ constexpr int tr_stage_words() { return tr_stage_data_words() + 2 * TR_MAXSPANS; }
 // common area: J[L + 1], lane table (4 rows of TR_LMAX), span starts
 __host__ __device__ constexpr int tr_common_words() { return (TR_LMAX + 1) + 4 * TR_LMAX + TR_MAXSPANS; }
 __host__ __device__ constexpr size_t tr_smem_bytes()
 {
-    return sizeof(float) * (size_t)(TM_STAGES * tr_stage_words() + tr_common_words());
+    return sizeof(float) * (size_t)(TR_STAGES * tr_stage_words() + tr_common_words());
 }
 
 } // namespace wl_tma
 
 // Pools the bulk-copy runner takes: n = 4 and N in [TM_MIN_N, 2^28] (32-bit
-// lane, span and slot offsets; a span of at most TM_ETARGET values wraps at
+// lane, span and slot offsets; a span of at most TR_ETARGET values wraps at
 // most once).  A pass whose strides have lcm above TR_LMAX runs the plain
 // gather instead.  Other pools take the per-thread runners.
 __host__ __device__ inline bool wl_tma_run_eligible(int n, int64_t N)
@@ -103,7 +118,7 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         sb[i + 1] = sb[i] + m[i];
     }
     const int nspans = sb[4];
-    const int T = tm_divc(TM_ETARGET, L);
+    const int T = tm_divc(TR_ETARGET, L);
     int SL[4], slot0[4];
     slot0[0] = 0;
 #pragma unroll
@@ -113,7 +128,7 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
             slot0[i + 1] = slot0[i] + m[i] * SL[i];
     }
     float *stage0 = smem;
-    int *common = (int *)(smem + TM_STAGES * tr_stage_words());
+    int *common = (int *)(smem + TR_STAGES * tr_stage_words());
     int *J = common;
     int *lanebase = J + (TR_LMAX + 1);
     int *spanC = lanebase + 4 * TR_LMAX;
@@ -176,7 +191,7 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
             const uint32_t stage_base = smem_u32(stage0);
             int issued_last = -1;   // last ring use this thread issued
             for (int tile = 0; tile < ntiles; tile++) {
-                const int g = it0 + tile, s = g % TM_STAGES, u = g / TM_STAGES;
+                const int g = it0 + tile, s = g % TR_STAGES, u = g / TR_STAGES;
                 if (*ring.abort_flag)
                     break;
                 if (u > 0 && !mbar_wait(smem_u32(&ring.empty[s]), (uint32_t)((u - 1) & 1))) {
@@ -242,8 +257,8 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
             }
             if (*ring.abort_flag) {
                 // copies still in flight must land before the CTA moves on
-                for (int g = max(it0, issued_last - TM_STAGES + 1); g <= issued_last; g++)
-                    if (!mbar_wait(smem_u32(&ring.full[g % TM_STAGES]), (uint32_t)((g / TM_STAGES) & 1)))
+                for (int g = max(it0, issued_last - TR_STAGES + 1); g <= issued_last; g++)
+                    if (!mbar_wait(smem_u32(&ring.full[g % TR_STAGES]), (uint32_t)((g / TR_STAGES) & 1)))
                         atomicOr(&st->status, WL_ETIMEOUT);
             }
         };
@@ -283,7 +298,7 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         const bool shifted = N4 != N32;   // wrapped spans sit shifted past their threshold
         {
             for (int tile = 0; tile < ntiles; tile++) {
-                const int g = it0 + tile, s = g % TM_STAGES, u = g / TM_STAGES;
+                const int g = it0 + tile, s = g % TR_STAGES, u = g / TR_STAGES;
                 if (*ring.abort_flag)
                     break;
                 if (!mbar_wait(smem_u32(&ring.full[s]), (uint32_t)(u & 1))) {
@@ -296,8 +311,8 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                 const float *sdata = stage0 + s * tr_stage_words();
                 const int *info0 = (const int *)(sdata + tr_stage_data_words());
                 const int *info1 = info0 + TR_MAXSPANS;
-                uint64_t tl = 0;   // this tile's terms: at most 40 per thread, each below 2^48
-                // L <= 90: each warp owns whole lanes, 64 lane times per step
+                uint64_t tl = 0;   // this tile's terms: under 100 per thread, each below 2^48
+                // long lanes: each warp owns whole lanes, 64 lane times per step
                 auto lane_loop = [&](auto shc) {
                     constexpr bool SH = decltype(shc)::value;
                     for (int l = warp; l < L; l += TM_CONS_WARPS) {
@@ -357,7 +372,7 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                         }
                     }
                 };
-                if (T >= 32) {
+                if (T >= TR_LANE_MIN_T) {
                     if (shifted)
                         lane_loop(std::true_type{});
                     else
