@@ -369,12 +369,17 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
                 uint64_t tl = 0;   // this tile's terms: at most 32 per thread, each below 2^48
                 if constexpr (NSUB == 2) {
                     // lanes x 64-time chunks dealt round-robin over the
-                    // consumer warps (21 to 55 lanes do not split evenly)
-                    // item = l nch + ch, stepped by the warp count without a division
+                    // consumer warps (21 to 55 lanes do not split evenly);
+                    // the deal continues from tile to tile (item i of tile k
+                    // goes to warp (k nitems + i) mod 15), so the extra items
+                    // of a tile fall on different warps each time.  item =
+                    // l nch + ch, stepped by the warp count without a division
                     const int nch = T >> 6, nitems = L * nch;
                     const int dq = tm_divc(TM_CONS_WARPS, nch), dr = TM_CONS_WARPS - dq * nch;
-                    int l = tm_divc(warp, nch), ch = warp - l * nch;
-                    for (int item = warp; item < nitems;
+                    int item0 = warp - (int)(((uint32_t)tile * (uint32_t)nitems) % TM_CONS_WARPS);
+                    item0 += item0 < 0 ? TM_CONS_WARPS : 0;
+                    int l = tm_divc(item0, nch), ch = item0 - l * nch;
+                    for (int item = item0; item < nitems;
                          item += TM_CONS_WARPS, l += dq + (ch + dr >= nch ? 1 : 0),
                          ch = ch + dr >= nch ? ch + dr - nch : ch + dr) {
                         const int jl = J[l];

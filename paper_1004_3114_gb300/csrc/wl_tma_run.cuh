@@ -312,10 +312,14 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                 const int *info0 = (const int *)(sdata + tr_stage_data_words());
                 const int *info1 = info0 + TR_MAXSPANS;
                 uint64_t tl = 0;   // this tile's terms: under 100 per thread, each below 2^48
-                // long lanes: each warp owns whole lanes, 64 lane times per step
+                // long lanes: each warp owns whole lanes, 64 lane times per
+                // step; lane l of tile k goes to warp (k L + l) mod 15, so when
+                // 15 does not divide L the extra lanes rotate over the warps
                 auto lane_loop = [&](auto shc) {
                     constexpr bool SH = decltype(shc)::value;
-                    for (int l = warp; l < L; l += TM_CONS_WARPS) {
+                    int l0 = warp - (int)(((uint32_t)tile * (uint32_t)L) % TM_CONS_WARPS);
+                    l0 += l0 < 0 ? TM_CONS_WARPS : 0;
+                    for (int l = l0; l < L; l += TM_CONS_WARPS) {
                         const int jl = J[l];
                         const int tmax = min(Tt, J[l + 1] - jl - t0);
                         int gb[4], thr[4], sh[4];
