@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -259,6 +260,48 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def distribution_summary(x):
+    """z-scores of the first four moments of a 1-D float32 device tensor
+    against N(0, 1) (standard errors sqrt(1/n), sqrt(2/n), sqrt(6/n),
+    sqrt(24/n)) and its Kolmogorov-Smirnov distance to the N(0, 1) CDF with
+    the asymptotic p-value: plain torch float64 reductions and a sort."""
+    import torch
+    from scipy import special
+    n = x.numel()
+    xd = x.double()
+    m = xd.mean()
+    c = xd - m
+    v = (c * c).mean()
+    skew = (c ** 3).mean() / v ** 1.5
+    kurt = (c ** 4).mean() / v ** 2 - 3.0
+    del xd, c
+    xs = torch.sort(x).values.double()
+    F = torch.special.ndtr(xs)
+    del xs
+    i = torch.arange(1, n + 1, device=x.device, dtype=torch.float64)
+    D = float(torch.maximum((i / n - F).max(), (F - (i - 1) / n).max()))
+    lam = math.sqrt(n) * D
+    return {"draws": n, "mean_z": float(m) / math.sqrt(1 / n), "var_z": (float(v) - 1.0) / math.sqrt(2 / n),
+            "skew_z": float(skew) / math.sqrt(6 / n), "kurt_z": float(kurt) / math.sqrt(24 / n),
+            "ks_D": D, "ks_sqrt_n_D": lam, "ks_p": float(special.kolmogorov(lam))}
+
+
+def stream_statistics(draws: int = 10 ** 8):
+    """The first `draws` returned values of the benchmark's generator (same
+    n, N, seed and frac, stream 0), summarised by distribution_summary."""
+    import torch
+    from paper_1004_3114_gb300 import wallace as W
+    g = W.Wallace(N_SUB, N_LEN, SEED, FRAC)
+    out = torch.empty(draws, dtype=torch.float32, device="cuda")
+    g.fill(out)
+    status = g.sync()
+    s = distribution_summary(out)
+    s["status"] = int(status)
+    g.close()
+    del out
+    return s
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1004_3114_gb300 import wallace as W
@@ -380,6 +423,9 @@ def run_ours(args, rank, world, local_rank):
         }
         if cmp:
             line["compare"] = cmp
+        if not args.no_stats:
+            # outside the timed region: moments and KS of the first 10^8 draws
+            line["stats"] = stream_statistics()
         if not args.no_cpu_baseline:
             v, dt = cpu_baseline(args.cpu_passes)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -715,6 +761,8 @@ def main():
                     help="--impl reference: time budget of the timed oracle steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-stats", action="store_true",
+                    help="skip the moment / KS summary of the first 10^8 draws")
     ap.add_argument("--batched", action="store_true",
                     help="4096 uneven generators in one persistent launch vs one handle each")
     ap.add_argument("--pow2", action="store_true", help="with --batched: power-of-two pool sizes")
