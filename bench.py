@@ -633,6 +633,68 @@ def variant_bench(steps: int = 2000, warmup: int = 5):
                       "peak_kind": kind, "steps": steps, "cases": res}), flush=True)
 
 
+def oracle_skip(g, count: int, chunk: int = 1 << 22):
+    """Advance an oracle generator's output stream by `count` values."""
+    import numpy as np
+    from oracle import py_oracle as orc
+    buf = np.empty(min(count, chunk), dtype=np.float32)
+    while count > 0:
+        k = min(count, buf.size)
+        orc.lib().orc_fill32(g._h, buf, k, np.float32(0.0), np.float32(1.0))
+        count -= k
+
+
+def batched_sampled_parity(Ns, seeds, sample, skip_passes, check_passes, got_out, got_pools, Rs):
+    """Generators `sample` of the batch: their last `check_passes` passes'
+    returned values (got_out[s], mu = 0, sigma = 1) and final pools
+    (got_pools[s]) against the oracle advanced by `skip_passes` passes first."""
+    import numpy as np
+    from oracle import py_oracle as orc
+    ok = {}
+
+    def job(s):
+        def run():
+            g = orc.Generator(4, int(Ns[s]), int(seeds[s]), 1.0)
+            oracle_skip(g, skip_passes * int(Rs[s]))
+            ref = g.fill(check_passes * int(Rs[s]))
+            ok[s] = bool(np.array_equal(ref.view(np.uint32), got_out[s].view(np.uint32)) and
+                         np.array_equal(g.pool32().view(np.uint32), got_pools[s].view(np.uint32)))
+            g.close()
+        return run
+    oracle_threads([job(s) for s in sample])
+    return {"generators": len(sample), "bit_exact": int(sum(ok.values())),
+            "checked": f"returned values of the last {check_passes} passes and the final pool, "
+                       f"after {skip_passes} passes", "N": [int(Ns[s]) for s in sample]}
+
+
+def serve_sampled_parity(srv, Ns, seeds, tr, k: int = 8, count: int = 1 << 14):
+    """After the trace: one more request for k sampled clients, compared value
+    by value with the oracle advanced by each client's requests of the trace."""
+    import numpy as np
+    from oracle import py_oracle as orc
+    rng = np.random.default_rng(7)
+    clients = [int(c) for c in rng.choice(np.unique(tr["client"]), size=k, replace=False)]
+    rids = [srv.submit(c, count, 0.5, 2.0) for c in clients]
+    srv.drain()
+    got = {c: srv.result_host(r) for c, r in zip(clients, rids)}
+    for r in rids:
+        srv.release(r)
+    ok = {}
+
+    def job(c):
+        def run():
+            g = orc.Generator(4, int(Ns[c]), int(seeds[c]), 1 / 3)
+            oracle_skip(g, int(tr["count"][tr["client"] == c].sum()))
+            ref = g.fill(count, 0.5, 2.0)
+            ok[c] = bool(np.array_equal(ref.view(np.uint32), got[c].view(np.uint32)))
+            g.close()
+        return run
+    oracle_threads([job(c) for c in clients])
+    return {"clients": k, "values_per_client": count, "bit_exact": int(sum(ok.values())),
+            "checked": "one request per sampled client after the trace, against the oracle "
+                       "advanced by that client's requests"}
+
+
 def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
                   power_of_two: bool = False, count: int = 4096):
     """4096 generators, n = 4, N log-uniform on [2^8, 2^18], seeds 0..4095,
@@ -671,8 +733,17 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
     value = passes * R_total / (ms * 1e-3)
     peak, kind = hbm_peak()
     achieved = passes * bytes_per_pass / (ms * 1e-3) / 1e9
+    # sampled parity: the largest and smallest pools and a spread between
+    order = np.argsort(Ns, kind="stable")
+    sample = sorted(set(int(order[i]) for i in np.linspace(0, len(Ns) - 1, 16).astype(int)))
+    got_out = {s: out[b.out_offset(s, passes_per_run):b.out_offset(s, passes_per_run)
+                      + passes_per_run * int(b.R[s])].cpu().numpy() for s in sample}
+    got_pools = {s: b.pool(s) for s in sample}
+    Rs = b.R.copy()
     b.close()
     del out
+    parity = batched_sampled_parity(Ns, seeds, sample, 1 + passes - passes_per_run, passes_per_run,
+                                    got_out, got_pools, Rs)
     # the same generators, one handle each, one after another
     handles = [W.Wallace(4, int(N), int(sd), 1.0, stream=stream) for N, sd in zip(Ns, seeds)]
     outs = [torch.empty(seq_passes * h.R, dtype=torch.float32, device="cuda") for h in handles]
@@ -702,7 +773,8 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
                    "autotune_s": tune_s},
         "sequential_handles": {"value": seq_value, "passes": seq_passes, "ms": seq_ms,
                                "launches": "one fill per generator"},
-        "speedup_vs_sequential": value / seq_value, "status": int(status)}), flush=True)
+        "speedup_vs_sequential": value / seq_value, "sampled_parity": parity,
+        "status": int(status)}), flush=True)
 
 
 def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float = 50_000.0,
@@ -730,6 +802,7 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
     values = int(tr["count"].sum())
     peak, kind = hbm_peak()
     bytes_moved = 28 * values        # per returned value at f = 3: 3 x 8 B pool read+write + 4 B out
+    parity = serve_sampled_parity(srv, Ns, seeds, tr)
     srv.close()
     cpu = serve_cpu_baseline(Ns, seeds, tr)
     print(json.dumps({
@@ -747,7 +820,8 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
                      "bytes_per_value": 28},
         "passes_per_tick": passes_per_tick, "ctas_per_sm": ctas_per_sm,
         "runner": "bulk-copy for one-CTA requests on 16384 <= N (n=4)" if ctas_per_sm == 0
-                  else "async-copy", "create_s": create_s, "status": int(st.status)}), flush=True)
+                  else "async-copy", "create_s": create_s, "sampled_parity": parity,
+        "status": int(st.status)}), flush=True)
 
 
 def main():
