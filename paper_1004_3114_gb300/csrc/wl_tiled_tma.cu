@@ -14,7 +14,7 @@
 //                     alignment lead (stored for the consumers), its byte
 //                     count, and one bulk copy (cp.async.bulk, the TMA engine;
 //                     two for a span that wraps past the end of its row) into
-//                     a ring of TM_STAGES shared-memory stages, completing on
+//                     a ring of shared-memory stages (3 for n = 4, 2 for n = 2), completing on
 //                     the stage's "full" mbarrier.  Span sp belongs to lane
 //                     sp / 4 of producer warp sp % 4: a single warp issues
 //                     bulk copies too slowly for spans of about 1 KB;
@@ -59,17 +59,19 @@ __device__ __forceinline__ float tm_wait_prev(WlDevState *st, volatile float *s_
 // SG: the generator draws a sign pattern each pass (matrix A D_k); the
 // fixed-matrix kernel has no trace of it.  NSUB: 4 (A = J/2 - I) or 2
 // (RANN4's rotation, strides from {3,5} and {7,11}: L = alpha beta <= 55 lanes,
-// T = 5760 / L lane times per tile).
+// T = 11520 / L lane times per tile, rounded down to a multiple of 64).
 template <bool SG, int NSUB>
 __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double rnu)
 {
     constexpr int LMAXN = NSUB == 4 ? TM_LMAX : TM_LMAX2;     // lanes, and lane-table row stride
-    constexpr int ET = NSUB == 4 ? TM_ETARGET : 2 * TM_ETARGET;   // lane-times per tile, at most
+    constexpr int ET = tm_et<NSUB>();          // lane-times per tile, at most
+    constexpr int STG = tm_stages<NSUB>();     // ring stages
+    constexpr int SW = tm_stage_words<NSUB>(), SDW = tm_stage_data_words<NSUB>();
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t bar_full[TM_STAGES];
-    __shared__ __align__(8) uint64_t bar_empty[TM_STAGES];
-    __shared__ __align__(8) uint64_t bar_tile[TM_STAGES];   // a stage's tile index is published
-    __shared__ volatile int s_stage_tile[TM_STAGES];
+    __shared__ __align__(8) uint64_t bar_full[STG];
+    __shared__ __align__(8) uint64_t bar_empty[STG];
+    __shared__ __align__(8) uint64_t bar_tile[STG];   // a stage's tile index is published
+    __shared__ volatile int s_stage_tile[STG];
     __shared__ uint64_t red[3 * (TM_THREADS / 32 + 1)];
     __shared__ volatile int s_abort;
 
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
                 slot0[i + 1] = slot0[i] + m[i] * SL[i];
         }
         float *stage0 = smem;
-        int *common = (int *)(smem + TM_STAGES * tm_stage_words());
+        int *common = (int *)(smem + STG * SW);
         int *J = common;
         int *lanebase = J + (TM_LMAX2 + 1);
         int *spanC = lanebase + 4 * TM_LMAX;
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
             spanC[s] = p * qN + tm_divc(p * rN + mi - 1, mi);
         }
         if (tid == 0) {
-            for (int s = 0; s < TM_STAGES; s++) {
+            for (int s = 0; s < STG; s++) {
                 mbar_init(smem_u32(&bar_full[s]), 32 * TM_PROD_WARPS);
                 mbar_init(smem_u32(&bar_empty[s]), TM_CONS_WARPS);
                 mbar_init(smem_u32(&bar_tile[s]), 1);
@@ -256,14 +258,14 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
                 sp_row = src + (int64_t)sp_i * Np;
             }
             const uint32_t stage_base = smem_u32(stage0);
-            int issued[TM_STAGES];
+            int issued[STG];
 #pragma unroll
-            for (int s = 0; s < TM_STAGES; s++)
+            for (int s = 0; s < STG; s++)
                 issued[s] = 0;
             const int pw = warp - TM_CONS_WARPS;
             for (int it = 0;; it++) {
-                const int s = it % TM_STAGES;
-                const int k = it / TM_STAGES;
+                const int s = it % STG;
+                const int k = it / STG;
                 if (s_abort)
                     break;
                 if (k > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (uint32_t)((k - 1) & 1))) {
@@ -293,9 +295,9 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
                 }
                 const int t0 = tile * T;
                 const int Tt = min(T, maxlen - t0);
-                int *lead = (int *)(stage0 + s * tm_stage_words() + tm_stage_data_words());
+                int *lead = (int *)(stage0 + s * SW + SDW);
                 const uint32_t full = smem_u32(&bar_full[s]);
-                const uint32_t d = stage_base + 4u * (uint32_t)(s * tm_stage_words()) + sp_doff;
+                const uint32_t d = stage_base + 4u * (uint32_t)(s * SW) + sp_doff;
                 int64_t addr = 0;
                 int len = 0, as = 0;
                 uint32_t bytes = 0;
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
                 issued[s] = k + 1;
             }
             // copies still in flight must land before the CTA leaves
-            for (int s = 0; s < TM_STAGES; s++)
+            for (int s = 0; s < STG; s++)
                 if (issued[s] > 0 && !mbar_wait(smem_u32(&bar_full[s]), (uint32_t)((issued[s] - 1) & 1)))
                     atomicOr(&st->status, WL_ETIMEOUT);
         } else {
@@ -350,8 +352,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
             }
             uint32_t emax = 0;
             for (int it = 0;; it++) {
-                const int s = it % TM_STAGES;
-                const int k = it / TM_STAGES;
+                const int s = it % STG;
+                const int k = it / STG;
                 if (s_abort)
                     break;
                 if (!mbar_wait(smem_u32(&bar_full[s]), (uint32_t)(k & 1))) {
@@ -364,8 +366,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
                     break;
                 const int t0 = tile * T;
                 const int Tt = min(T, maxlen - t0);
-                const float *sdata = stage0 + s * tm_stage_words();
-                const int *lead = (const int *)(sdata + tm_stage_data_words());
+                const float *sdata = stage0 + s * SW;
+                const int *lead = (const int *)(sdata + SDW);
                 uint64_t tl = 0;   // this tile's terms: at most 32 per thread, each below 2^48
                 if constexpr (NSUB == 2) {
                     // lanes x 64-time chunks dealt round-robin over the
@@ -503,7 +505,7 @@ bool wl_tma_supported(int n, int64_t N, int fp64, int sm_count)
 
 cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream)
 {
-    const size_t smem = tm_smem_bytes();
+    const size_t smem = a.n == 2 ? tm_smem_bytes<2>() : tm_smem_bytes<4>();
     const int which = a.n == 2 ? 2 : (signs ? 1 : 0);
     auto kern = which == 2 ? tma_kernel<false, 2> : (which == 1 ? tma_kernel<true, 4> : tma_kernel<false, 4>);
     if (!g_tma_configured[which]) {

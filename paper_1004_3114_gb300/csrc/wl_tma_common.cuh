@@ -13,8 +13,10 @@
 #define TM_CONS_THREADS (TM_CONS_WARPS * 32)
 #define TM_PROD_WARPS 4          /* one warp issues a bulk copy only every ~80 cycles */
 #define TM_THREADS (TM_CONS_THREADS + 32 * TM_PROD_WARPS)
-#define TM_STAGES 3
+#define TM_STAGES 3               /* n = 4: ring stages */
 #define TM_ETARGET 2880          /* n = 4: lane-times per tile, L * T <= this (T = 64 at L = 45) */
+#define TM_STAGES2 2              /* n = 2: ring stages */
+#define TM_ETARGET2 11520        /* n = 2: lane-times per tile (T = 192 to 512 at L = 55 to 21) */
 #define TM_LMAX 45               /* n = 4: strides divide 45 */
 #define TM_LMAX2 55              /* n = 2: L = alpha beta <= 5 * 11 */
 #define TM_MAXSPANS 32           /* sum_i 45 / alpha_i <= 15 + 9 + 5 + 3 */
@@ -24,13 +26,23 @@
 namespace wl_tma {
 
 
-__host__ __device__ constexpr int tm_stage_data_words() { return 4 * TM_ETARGET + 12 * TM_MAXSPANS; }
-__host__ __device__ constexpr int tm_stage_words() { return tm_stage_data_words() + TM_MAXSPANS; }
+// Ring geometry of the pass kernel per sub-vector count: n = 4 keeps three
+// stages of 2880 lane-times (45 lanes x 64); n = 2 has two stages of twice
+// the values (lanes of 192 to 512 times fill its 64-time items better).
+template <int NSUB>
+__host__ __device__ constexpr int tm_stages() { return NSUB == 4 ? TM_STAGES : TM_STAGES2; }
+template <int NSUB>
+__host__ __device__ constexpr int tm_et() { return NSUB == 4 ? TM_ETARGET : TM_ETARGET2; }
+template <int NSUB>
+__host__ __device__ constexpr int tm_stage_data_words() { return NSUB * tm_et<NSUB>() + 12 * TM_MAXSPANS; }
+template <int NSUB>
+__host__ __device__ constexpr int tm_stage_words() { return tm_stage_data_words<NSUB>() + TM_MAXSPANS; }
 // common area: J[L + 1] (room for n = 2's 55 lanes), lane table (n * lanes <= 180), span starts
 __host__ __device__ constexpr int tm_common_words() { return (TM_LMAX2 + 1) + 4 * TM_LMAX + TM_MAXSPANS; }
+template <int NSUB>
 __host__ __device__ constexpr size_t tm_smem_bytes()
 {
-    return sizeof(float) * (size_t)(TM_STAGES * tm_stage_words() + tm_common_words());
+    return sizeof(float) * (size_t)(tm_stages<NSUB>() * tm_stage_words<NSUB>() + tm_common_words());
 }
 
 // x / d for x >= 0 and d a lane count or span count of either geometry
