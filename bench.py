@@ -715,7 +715,7 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
     cache = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
                          "wallace_batch_tune.jsonl")
     t0 = time.perf_counter()
-    tuning = b.autotune(cache, 1)
+    tuning = b.autotune(cache, 2)
     tune_s = time.perf_counter() - t0
     out = torch.empty(b.out_size(passes_per_run), dtype=torch.float32, device="cuda")
     b.run(1, None)   # warm-up (graph instantiation)

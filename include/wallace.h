@@ -283,7 +283,8 @@ int wallace_batch_get_pool(wallace_batch_t *b, int s, float *host_out);
  * wallace_batch_set_tuning / wallace_batch_get_tuning -- launch shape: CTAs
  * per SM (capped by occupancy), lane-times per tile of the tiled gather
  * (4 <= etarget <= 2560), and the largest pool (n*N values) kept in shared
- * memory across passes (at most ~8400 values fit).  ctas_per_sm = 0 selects
+ * memory across passes (at most ~8400 values fit; ~24500 with the bulk-copy
+ * runner).  ctas_per_sm = 0 selects
  * the bulk-copy runner instead: one CTA of 608 threads per SM, pools with
  * n = 4 and 16384 <= N <= 2^28 regenerated through a warp-specialised stage
  * ring fed by bulk (TMA) copies, the others as before (etarget and fused_max

@@ -618,15 +618,19 @@ int wallace_batch_autotune(wallace_batch_t *b, const char *cache_path, int trial
     // async-copy runner: CTAs per SM x tile size x shared-memory pool limit;
     // bulk-copy runner (one CTA per SM): shared-memory pool limit x the async
     // tile size its smaller global pools use
+    // (the bulk-copy runner's shared memory holds pools of up to ~24.5K
+    // values across passes; the async runner's, about 8K)
     const int ctas_list[] = {1, 2, 3, 0};
     const int et_list[] = {1280, 1920, TL_EMAX};
-    const int64_t fm_list[] = {2048, 4096, 8192};
+    const int64_t fm_list[] = {2048, 4096, 8192, 16384, 24576};
     for (int ci = 0; ci < 4 && e == cudaSuccess; ci++) {
         const bool tma = ctas_list[ci] == 0;
         if (!tma && ctas_list[ci] > b->max_ctas_per_sm)
             continue;
         for (int ei = 0; ei < 3 && e == cudaSuccess; ei++)
-            for (int fi = 0; fi < 3 && e == cudaSuccess; fi++) {
+            for (int fi = 0; fi < 5 && e == cudaSuccess; fi++) {
+                if (!tma && fm_list[fi] > 8192)
+                    continue;
                 b->tune.runner = tma ? 1 : 0;
                 b->tune.ctas_per_sm = tma ? 1 : ctas_list[ci];
                 b->tune.etarget = et_list[ei];

@@ -51,7 +51,7 @@ def test_batch_n4_mixed_sizes_matches_oracle(orc, bulk):
 
 
 @pytest.mark.parametrize("tuning", [(1, 1280, 0), (3, 2560, 8192), (2, 640, 2048), (0, 2560, 4096),
-                                    (0, 1280, 0)])
+                                    (0, 1280, 0), (0, 2560, 24576)])
 def test_batch_tunings_give_identical_streams(orc, tuning):
     """ctas_per_sm = 0: the bulk-copy runner (pools 30000, 65536, 100004,
     16384 and 45060 take the stage ring; 45060 = 2^2 3 5 751 has strides
