@@ -9,6 +9,8 @@
 // (Eq. 1), accumulate the exact sum of squares, and write the returned prefix;
 // thread 0 then runs the chi-squared rescale (Eq. 3) and drift check and draws
 // the next parameters.  At the end the pool is written back to global memory.
+#include <algorithm>
+
 #include "wl_common.cuh"
 #include "wl_launch.h"
 
@@ -38,7 +40,7 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
     const double rnu = wl_rnu(nu);
     T *buf0 = (T *)fsm;
     T *buf1 = buf0 + nu;
-    for (int q = tid; q < nu; q += FU_THREADS) {
+    for (int q = tid; q < nu; q += blockDim.x) {
         int i = q / (int)N;
         buf0[q] = gin[(int64_t)i * Np + (q - i * (int)N)];
     }
@@ -66,15 +68,17 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
         const uint32_t signs = s_signs;
         const int take = (int)(pass + 1 < passes ? R : last_take);
         T *o = out + pass * R;
+        // 32-bit index arithmetic: N <= 7040 here and alpha * blockDim < 2^32
+        const uint32_t uN = (uint32_t)N, nth = blockDim.x;
         int idx[NSUB], stp[NSUB];
 #pragma unroll
         for (int i = 0; i < NSUB; i++) {
-            idx[i] = (int)(((int64_t)s_alpha[i] * (tid < N ? tid : 0) + s_gamma[i]) % N);
-            stp[i] = (int)(((int64_t)s_alpha[i] * FU_THREADS) % N);
+            idx[i] = (int)(((uint32_t)s_alpha[i] * (uint32_t)(tid < (int)N ? tid : 0) + (uint32_t)s_gamma[i]) % uN);
+            stp[i] = (int)(((uint32_t)s_alpha[i] * nth) % uN);
         }
         uint64_t lo = 0, hi = 0;
         uint32_t bad = 0;
-        for (int j = tid; j < (int)N; j += FU_THREADS) {
+        for (int j = tid; j < (int)N; j += (int)nth) {
             T g[NSUB], y[NSUB];
 #pragma unroll
             for (int i = 0; i < NSUB; i++) {
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
         src = dst;
         dst = t;
     }
-    for (int q = tid; q < nu; q += FU_THREADS) {
+    for (int q = tid; q < nu; q += blockDim.x) {
         int i = q / (int)N;
         gout[(int64_t)i * Np + (q - i * (int)N)] = src[q];
     }
@@ -147,7 +151,10 @@ cudaError_t launch_one(void *pin, void *pout, int64_t N, int64_t Np, WlDevState 
             return e;
         configured = true;
     }
-    fused_kernel<NSUB, T><<<1, FU_THREADS, smem, stream>>>((const T *)pin, (T *)pout, N, Np, st,
+    // one thread per tuple up to FU_THREADS (at least four warps: the
+    // finaliser's chains take three): fewer idle threads at each barrier
+    const int threads = (int)std::min<int64_t>(FU_THREADS, std::max<int64_t>(128, (N + 31) / 32 * 32));
+    fused_kernel<NSUB, T><<<1, threads, smem, stream>>>((const T *)pin, (T *)pout, N, Np, st,
                                                           passes, R, last_take, (T *)out, mu,
                                                           sigma);
     return cudaGetLastError();

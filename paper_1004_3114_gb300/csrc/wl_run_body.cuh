@@ -86,11 +86,14 @@ __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red, int32
         }
         __syncthreads();
         const float c = __int_as_float(s_prm[16]);
+        // 32-bit index arithmetic: a pool in shared memory has N < 2^13 and
+        // alpha * blockDim < 2^32
         int idx[NSUB], stp[NSUB];
 #pragma unroll
         for (int i = 0; i < NSUB; i++) {
-            idx[i] = (int)(((int64_t)s_prm[i] * (tid < N ? tid : 0) + s_prm[8 + i]) % N);
-            stp[i] = (int)(((int64_t)s_prm[i] * nth) % N);
+            idx[i] = (int)(((uint32_t)s_prm[i] * (uint32_t)(tid < N ? tid : 0) + (uint32_t)s_prm[8 + i]) %
+                           (uint32_t)N);
+            stp[i] = (int)(((uint32_t)s_prm[i] * (uint32_t)nth) % (uint32_t)N);
         }
         float *o = d.out ? d.out + p * d.R : nullptr;
         const int w1 = o ? (int)(p + 1 < d.passes ? d.R : d.last_take) : 0;
