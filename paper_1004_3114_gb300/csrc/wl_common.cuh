@@ -718,6 +718,107 @@ __device__ inline void wl_finalise_par(WlDevState *st, int n, int64_t N, int64_t
     }
 }
 
+// End of a pass that one CTA ran over the whole pool (the CTA's sum is Q):
+// the same update as wl_finalise_par with two barriers.  Per-warp partial
+// sums go to `red` (3 words per warp); warps 0 and 2 each complete Q and S
+// and run the scale (c, Eq. 3) and the drift ratio (Section 8) respectively,
+// while warp 1 draws the strides of the pass after next (at least 3 warps).  The caller copies
+// st->last = st->next at the start of the pass (nothing writes `next`
+// during it), so the two warps write disjoint fields; for n = 2 the
+// rotation with the scale folded in (next.rc*, next.rs*) is left to
+// wl_fold_rotation, after the barrier.  st: the CTA's shared-memory copy
+// of the state.  Every thread calls.
+template <typename XF>
+__device__ inline void wl_end_pass_cta(WlDevState *st, int n, int64_t N, int64_t nu, double rnu, uint64_t lo,
+                                       uint64_t hi, uint32_t bad, uint64_t *red, XF xf, int msigns, bool fp64)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        uint64_t olo = __shfl_down_sync(0xffffffffu, lo, off);
+        uint64_t ohi = __shfl_down_sync(0xffffffffu, hi, off);
+        wl_add128(lo, hi, olo, ohi);
+    }
+    bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        red[warp] = lo;
+        red[nw + warp] = hi;
+        red[2 * nw + warp] = bad;
+    }
+    __syncthreads();
+    if (warp == 0 || warp == 2) {
+        // both complete Q (and S): warp 0 for the scale, warp 2 for the drift
+        lo = lane < nw ? red[lane] : 0ull;
+        hi = lane < nw ? red[nw + lane] : 0ull;
+        bad = lane < nw ? (uint32_t)red[2 * nw + lane] : 0u;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            uint64_t olo = __shfl_down_sync(0xffffffffu, lo, off);
+            uint64_t ohi = __shfl_down_sync(0xffffffffu, hi, off);
+            wl_add128(lo, hi, olo, ohi);
+        }
+        bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
+        if (lane == 0) {
+            if (!fp64 && hi != 0)
+                bad = 1u;
+            const double q = fp64 ? __dadd_rn(__ull2double_rn(hi),
+                                              __dmul_rn(__ull2double_rn(lo), 1.0 / 18446744073709551616.0))
+                                  : __dmul_rn(__ull2double_rn(lo), 1.0 / 4294967296.0);
+            const int chi = st->chi;
+            const double x = xf();
+            double S;
+            if (!chi && rnu > 0.0) {
+                const double xr = __dadd_rn(x, rnu);
+                S = __dmul_rn(__dmul_rn(xr, xr), 0.5);
+            } else {
+                S = wl_chi_sample(chi, nu, x);
+            }
+            int32_t f = 0;
+            if (warp == 0) {
+                double c = 1.0;
+                if (bad || (chi && !(S > 0.0)) || !(q > 0.0))
+                    f = WL_ECORRUPT;
+                else
+                    c = __dsqrt_rn(__ddiv_rn(S, q));
+                st->q_lo = lo;
+                st->q_hi = hi;
+                st->q = q;
+                st->S = S;
+                st->c = c;
+                st->bad = (int32_t)bad;
+                st->next.c64 = c;
+                st->next.c32 = __double2float_rn(c);
+            } else {
+                double drift = 0.0;
+                if (st->have_prev) {
+                    drift = __dsub_rn(__ddiv_rn(q, st->S_prev), 1.0);
+                    if (!(fabs(drift) <= 1e-3))
+                        f = WL_ECORRUPT;
+                }
+                st->drift = drift;
+                st->S_prev = S;
+                st->have_prev = 1;
+            }
+            if (f)
+                atomicOr(&st->status, f);
+        }
+    } else if (warp == 1 && lane == 0) {
+        st->passes += 1;
+        wl_advance_strides(st, n, N, st->lcg, st->lcg_pend, msigns);
+    }
+    __syncthreads();
+}
+
+// n = 2: the scale folded into the next pass's rotation (one thread).
+__device__ __forceinline__ void wl_fold_rotation(WlDevState *st)
+{
+    st->next.rc64 = __dmul_rn(st->next.c64, st->next.rcos);
+    st->next.rs64 = __dmul_rn(st->next.c64, st->next.rsin);
+    st->next.rc32 = __double2float_rn(st->next.rc64);
+    st->next.rs32 = __double2float_rn(st->next.rs64);
+}
+
 // The grid-wide bulk-copy pass's form: binary32 pool, x read from the new
 // pool in device memory.
 __device__ inline void wl_finalise_cta(WlDevState *st, int n, int64_t N, int64_t nu, double rnu,

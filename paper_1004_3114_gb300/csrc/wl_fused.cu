@@ -28,10 +28,6 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
 {
     extern __shared__ __align__(16) unsigned char fsm[];
     __shared__ uint64_t red[3 * (FU_THREADS / 32)];
-    __shared__ int32_t s_alpha[NSUB];
-    __shared__ int32_t s_gamma[NSUB];
-    __shared__ T s_c, s_rC, s_rS;
-    __shared__ uint32_t s_signs;
     __shared__ WlDevState sst;   // the state, on chip for the whole run
     wl_state_load(&sst, st_g);
     WlDevState *st = &sst;
@@ -44,28 +40,39 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
         int i = q / (int)N;
         buf0[q] = gin[(int64_t)i * Np + (q - i * (int)N)];
     }
+    __syncthreads();   // the pool is on chip; each pass then ends with a barrier
     const T mu = (T)mu_d, sigma = (T)sigma_d;
     T *src = buf0, *dst = buf1;
     for (int64_t pass = 0; pass < passes; pass++) {
-        if (tid == 0) {
-            for (int i = 0; i < NSUB; i++) {
-                s_alpha[i] = st->next.alpha[i];
-                s_gamma[i] = (int32_t)st->next.gamma[i];
-            }
-            if constexpr (sizeof(T) == 8) {
-                s_c = st->next.c64;
-                s_rC = st->next.rc64;
-                s_rS = st->next.rs64;
-            } else {
-                s_c = st->next.c32;
-                s_rC = st->next.rc32;
-                s_rS = st->next.rs32;
-            }
-            s_signs = st->next.signs;
+        // this pass's parameters, as the previous pass's end left them; thread
+        // 0 records them as the most recent pass's (nothing writes `next`
+        // until the end of the pass)
+        if (tid == 0)
+            st->last = st->next;
+        int32_t s_alpha[NSUB], s_gamma[NSUB];
+#pragma unroll
+        for (int i = 0; i < NSUB; i++) {
+            s_alpha[i] = st->next.alpha[i];
+            s_gamma[i] = (int32_t)st->next.gamma[i];
         }
-        __syncthreads();
-        const T c = s_c, rC = s_rC, rS = s_rS;
-        const uint32_t signs = s_signs;
+        T c, rC = (T)0, rS = (T)0;
+        if constexpr (sizeof(T) == 8)
+            c = st->next.c64;
+        else
+            c = st->next.c32;
+        if constexpr (NSUB == 2) {
+            // the scale folded into the rotation, as wl_fold_rotation does
+            const double rc = __dmul_rn(st->next.c64, st->next.rcos);
+            const double rs = __dmul_rn(st->next.c64, st->next.rsin);
+            if constexpr (sizeof(T) == 8) {
+                rC = rc;
+                rS = rs;
+            } else {
+                rC = __double2float_rn(rc);
+                rS = __double2float_rn(rs);
+            }
+        }
+        const uint32_t signs = st->next.signs;
         const int take = (int)(pass + 1 < passes ? R : last_take);
         T *o = out + pass * R;
         // 32-bit index arithmetic: N <= 7040 here and alpha * blockDim < 2^32
@@ -119,16 +126,15 @@ __global__ void __launch_bounds__(FU_THREADS) fused_kernel(const T *gin, T *gout
                 }
             }
         }
-        wl_cta_reduce_to_state(lo, hi, bad, st, red);
-        __syncthreads();
-        const double xlast = (double)dst[nu - 1];
-        wl_finalise_par(st, NSUB, N, (int64_t)nu, rnu, [xlast]() { return xlast; }, st->msigns,
-                        sizeof(T) == 8);
-        __syncthreads();
+        const T *xp = &dst[nu - 1];
+        wl_end_pass_cta(st, NSUB, N, (int64_t)nu, rnu, lo, hi, bad, red, [xp]() { return (double)*xp; },
+                        st->msigns, sizeof(T) == 8);
         T *t = src;
         src = dst;
         dst = t;
     }
+    if (NSUB == 2 && tid == 0)
+        wl_fold_rotation(st);
     for (int q = tid; q < nu; q += blockDim.x) {
         int i = q / (int)N;
         gout[(int64_t)i * Np + (q - i * (int)N)] = src[q];

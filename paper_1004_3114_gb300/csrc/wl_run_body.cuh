@@ -75,25 +75,24 @@ __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red, int32
         int i = q / N;
         src[q] = g0[(int64_t)i * d.Np + (q - i * N)];
     }
+    __syncthreads();   // the pool is on chip; each pass then ends with a barrier
+    WlDevState *st = d.st;   // the CTA's shared-memory copy of the state
     for (int64_t p = 0; p < d.passes; p++) {
-        __syncthreads();
-        if (tid == 0) {
-            for (int i = 0; i < NSUB; i++) {
-                s_prm[i] = d.st->next.alpha[i];
-                s_prm[8 + i] = (int32_t)d.st->next.gamma[i];
-            }
-            s_prm[16] = __float_as_int(d.st->next.c32);
-        }
-        __syncthreads();
-        const float c = __int_as_float(s_prm[16]);
+        // this pass's parameters, as the previous pass's end left them; thread
+        // 0 records them as the most recent pass's
+        if (tid == 0)
+            st->last = st->next;
+        const float c = st->next.c32;
         // 32-bit index arithmetic: a pool in shared memory has N < 2^13 and
         // alpha * blockDim < 2^32
+        int32_t al[NSUB];
         int idx[NSUB], stp[NSUB];
 #pragma unroll
         for (int i = 0; i < NSUB; i++) {
-            idx[i] = (int)(((uint32_t)s_prm[i] * (uint32_t)(tid < N ? tid : 0) + (uint32_t)s_prm[8 + i]) %
+            al[i] = st->next.alpha[i];
+            idx[i] = (int)(((uint32_t)al[i] * (uint32_t)(tid < N ? tid : 0) + (uint32_t)st->next.gamma[i]) %
                            (uint32_t)N);
-            stp[i] = (int)(((uint32_t)s_prm[i] * (uint32_t)nth) % (uint32_t)N);
+            stp[i] = (int)(((uint32_t)al[i] * (uint32_t)nth) % (uint32_t)N);
         }
         float *o = d.out ? d.out + p * d.R : nullptr;
         const int w1 = o ? (int)(p + 1 < d.passes ? d.R : d.last_take) : 0;
@@ -121,15 +120,13 @@ __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red, int32
                     o[q] = __fadd_rn(d.mu, __fmul_rn(d.sigma, y[k]));
             }
         }
-        wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
-        __syncthreads();
-        const double xlast = (double)dst[nu - 1];
-        wl_finalise_par(d.st, NSUB, N, nu, rnu, [xlast]() { return xlast; }, d.st->msigns, false);
+        const float *xp = &dst[nu - 1];
+        wl_end_pass_cta(st, NSUB, N, nu, rnu, lo, hi, bad, red, [xp]() { return (double)*xp; }, st->msigns,
+                        false);
         float *t = src;
         src = dst;
         dst = t;
     }
-    __syncthreads();
     float *g1 = d.buf[d.cur];
     for (int q = tid; q < nu; q += nth) {
         int i = q / N;
@@ -146,16 +143,19 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
     const int64_t N = d.N, nu = NSUB * N;
     const double rnu = wl_rnu(nu);
     int cur = d.cur;
+    WlDevState *st = d.st;   // the CTA's shared-memory copy of the state
     for (int64_t p = 0; p < d.passes; p++) {
-        __syncthreads();   // the previous pass's parameters are written
+        // parameters as the previous pass's end (a barrier) left them
+        if (tid == 0)
+            st->last = st->next;
         int32_t alpha[NSUB];
         int64_t gam[NSUB];
 #pragma unroll
         for (int i = 0; i < NSUB; i++) {
-            alpha[i] = d.st->next.alpha[i];
-            gam[i] = d.st->next.gamma[i];
+            alpha[i] = st->next.alpha[i];
+            gam[i] = st->next.gamma[i];
         }
-        const float c = d.st->next.c32;
+        const float c = st->next.c32;
         const float *src = d.buf[cur];
         float *dst = d.buf[1 - cur];
         float *o = d.out ? d.out + p * d.R : nullptr;
@@ -187,10 +187,9 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
             wl_gather_range_n<NSUB>(src, dst, N, d.Np, alpha, gam, c, o, w1, d.mu, d.sigma, lo, hi,
                                     bad);
         }
-        wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
-        __syncthreads();
         const float *xp = &dst[wl_phys(nu - 1, N, d.Np)];
-        wl_finalise_par(d.st, NSUB, N, nu, rnu, [xp]() { return (double)__ldcg(xp); }, d.st->msigns, false);
+        wl_end_pass_cta(st, NSUB, N, nu, rnu, lo, hi, bad, red, [xp]() { return (double)__ldcg(xp); },
+                        st->msigns, false);
         cur = 1 - cur;
     }
     return cur;

@@ -427,23 +427,19 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
     const int64_t N = d.N, nu = 4 * N;
     const double rnu = wl_rnu(nu);
     int cur = d.cur;
+    WlDevState *st = d.st;   // the CTA's shared-memory copy of the state
     for (int64_t p = 0; p < d.passes; p++) {
-        __syncthreads();   // the previous pass's finaliser has written the parameters
-        if (tid < 4) {
-            s_prm[tid] = d.st->next.alpha[tid];
-            s_prm[4 + tid] = (int32_t)d.st->next.gamma[tid];
-        } else if (tid == 4) {
-            s_prm[8] = __float_as_int(d.st->next.c32);
-        }
-        __syncthreads();
+        // parameters as the previous pass's end (a barrier) left them
+        if (tid == 0)
+            st->last = st->next;
         int32_t alpha[4];
         int64_t gam[4];
 #pragma unroll
         for (int i = 0; i < 4; i++) {
-            alpha[i] = s_prm[i];
-            gam[i] = s_prm[4 + i];
+            alpha[i] = st->next.alpha[i];
+            gam[i] = st->next.gamma[i];
         }
-        const float c = __int_as_float(s_prm[8]);
+        const float c = st->next.c32;
         const float *src = d.buf[cur];
         float *dst = d.buf[1 - cur];
         float *o = d.out ? d.out + p * d.R : nullptr;
@@ -474,10 +470,9 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
             // the next pass may read this pool with bulk copies
             asm volatile("fence.proxy.async.global;\n" ::: "memory");
         }
-        wl_cta_reduce_to_state(lo, hi, bad, d.st, red);
-        __syncthreads();
         const float *xp = &dst[wl_phys(nu - 1, N, d.Np)];
-        wl_finalise_par(d.st, 4, N, nu, rnu, [xp]() { return (double)__ldcg(xp); }, d.st->msigns, false);
+        wl_end_pass_cta(st, 4, N, nu, rnu, lo, hi, bad, red, [xp]() { return (double)__ldcg(xp); }, st->msigns,
+                        false);
         cur = 1 - cur;
     }
     return cur;
