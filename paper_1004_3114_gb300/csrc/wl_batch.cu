@@ -4,17 +4,21 @@
 //
 // The CTAs take whole generators from a work counter, largest pool first.  A
 // CTA runs every pass of its generator itself, so the end-of-pass sum of
-// squares and chi-squared rescale (Eq. 3) are CTA-local and no CTA ever waits
-// for another:
-//   * a pool that fits in shared memory is loaded once and regenerated there
-//     for all passes (only the returned values go to global memory);
-//   * a larger n = 4 pool whose pass has strides with lcm <= 315 runs the
-//     lane-tiled gather (wl_tiled_body.cuh) over all of its tiles;
-//   * anything else runs the plain strided gather.
+// squares and chi-squared rescale (Eq. 3) are CTA-local (wl_end_pass_cta)
+// and no CTA ever waits for another.  Two runners:
+//   * per-thread async copies (batch_kernel, 1 to 3 CTAs of 256 threads per
+//     SM): a pool that fits in shared memory is loaded once and regenerated
+//     there for all passes (only the returned values go to global memory); a
+//     larger n = 4 pool whose strides have lcm <= 315 runs the lane-tiled
+//     gather (wl_tiled_body.cuh) over all of its tiles; anything else runs
+//     the plain strided gather;
+//   * bulk copies (batch_tma_kernel, one 608-thread CTA per SM): n = 4 pools
+//     with N >= 16384 go through the warp-specialised stage ring
+//     (wl_tma_run.cuh), the others as above.
 // The launch is a CUDA graph (work-counter reset + kernel) whose kernel
 // arguments are updated per run.  An autotuner times candidate settings
-// (CTAs per SM, tile size, shared-memory pool limit) on a snapshot of the
-// generators and caches the best in a JSON-lines file.
+// (runner and CTAs per SM, tile size, shared-memory pool limit) on a
+// snapshot of the generators and caches the best in a JSON-lines file.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>

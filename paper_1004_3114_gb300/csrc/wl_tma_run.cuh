@@ -3,10 +3,11 @@
 // wl_batch.cu), with the same lane-tiled geometry and warp-specialised stage
 // ring as the grid-wide kernel (wl_tiled_tma.cu) -- 4 producer warps issue
 // one bulk copy per span into TR_STAGES shared-memory stages, 15 consumer
-// warps own whole lanes (L <= 90) or take (lane, time) pairs -- but over all
-// tiles of the pool in order, for any N >= TM_MIN_N, with the
-// sum of squares and the chi-squared rescale (Eq. 3 of Brent's RANN4 paper)
-// done by the CTA itself, so no CTA waits for another.
+// warps own whole lanes (T >= TR_LANE_MIN_T) or take (lane, time) pairs --
+// but over all tiles of the pool in order, for any N >= TM_MIN_N and lane
+// counts up to TR_LMAX, with the sum of squares and the chi-squared rescale
+// (Eq. 3 of Brent's RANN4 paper) done by the CTA itself (wl_end_pass_cta),
+// so no CTA waits for another.
 //
 // The ring's mbarriers are initialised once per CTA and `it` counts the
 // stage uses so far (the same in every thread), so the phase parities stay
