@@ -29,16 +29,20 @@
 #ifndef TR_STAGES
 #define TR_STAGES 2
 #endif
+static_assert(TR_STAGES == 2, "the runner's ring alternates two stages (or uses them as one)");
 #ifndef TR_ETARGET
 #define TR_ETARGET 5280  /* values per sub-vector per tile: L T <= this */
 #endif
 #ifndef TR_LANE_MIN_T
 #define TR_LANE_MIN_T 24 /* consumers own whole lanes when T is at least this */
 #endif
+#ifndef TR_ONE_STAGE_L
+#define TR_ONE_STAGE_L 63 /* from this many lanes on, the stages form one stage of twice T */
+#endif
 
 struct WlTmaRing {
     uint64_t *full, *empty;    // TR_STAGES mbarriers each, in shared memory
-    int it;                    // stage uses so far
+    int uses[TR_STAGES];       // completed uses of each stage's barriers (the same in every thread)
     volatile int *abort_flag;  // shared: a wait timed out in this CTA
 };
 
@@ -56,7 +60,8 @@ __device__ inline void wl_tma_ring_init(WlTmaRing &r)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     __syncthreads();
-    r.it = 0;
+    for (int s = 0; s < TR_STAGES; s++)
+        r.uses[s] = 0;
 }
 
 // Geometry limits of the runner.  The strides of a pass have lcm L dividing
@@ -119,7 +124,14 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         sb[i + 1] = sb[i] + m[i];
     }
     const int nspans = sb[4];
-    const int T = tm_divc(TR_ETARGET, L);
+    // Large lane counts leave lanes of few values per tile, and their short
+    // store runs end in partially written sectors that L2 completes by
+    // reading DRAM; there the ring's memory forms one stage of twice the
+    // lane times (the consumers, not the copies, set the pace of such pools)
+    const int S = L >= TR_ONE_STAGE_L ? 1 : TR_STAGES;
+    const int SW = TR_STAGES * tr_stage_words() / S;   // words per stage
+    const int SDW = SW - 2 * TR_MAXSPANS;               // span data words per stage
+    const int T = tm_divc(TR_ETARGET * TR_STAGES / S, L);
     int SL[4], slot0[4];
     slot0[0] = 0;
 #pragma unroll
@@ -159,7 +171,8 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
     __syncthreads();
     const int maxlen = tm_divc(N32 + L - 1, L);
     const int ntiles = (maxlen + T - 1) / T;
-    const int it0 = ring.it;
+    // tile k uses stage k % S for the (uses[s] + k / S)-th time
+    const int use0 = ring.uses[0], use1 = TR_STAGES > 1 ? ring.uses[TR_STAGES - 1] : 0;
     const int N4 = (N32 + 3) & ~3;
 
     if (warp >= TM_CONS_WARPS) {
@@ -190,9 +203,16 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                 }
             }
             const uint32_t stage_base = smem_u32(stage0);
-            int issued_last = -1;   // last ring use this thread issued
+            // the stage layout may differ from the previous pass's: order the
+            // consumers' reads of this memory (before the pass's first
+            // barrier) before this pass's bulk copies into it
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            int issued[TR_STAGES];   // uses of each stage this thread issued copies for, + 1
+#pragma unroll
+            for (int q = 0; q < TR_STAGES; q++)
+                issued[q] = 0;
             for (int tile = 0; tile < ntiles; tile++) {
-                const int g = it0 + tile, s = g % TR_STAGES, u = g / TR_STAGES;
+                const int s = S == 1 ? 0 : tile & 1, u = (s == 0 ? use0 : use1) + (S == 1 ? tile : tile >> 1);
                 if (*ring.abort_flag)
                     break;
                 if (u > 0 && !mbar_wait(smem_u32(&ring.empty[s]), (uint32_t)((u - 1) & 1))) {
@@ -202,11 +222,11 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                 }
                 const int t0 = tile * T;
                 const int Tt = min(T, maxlen - t0);
-                float *sdata = stage0 + s * tr_stage_words();
-                int *info0 = (int *)(sdata + tr_stage_data_words());   // lead | shift << 2
+                float *sdata = stage0 + s * SW;
+                int *info0 = (int *)(sdata + SDW);   // lead | shift << 2
                 int *info1 = info0 + TR_MAXSPANS;                       // wrap threshold (slot position)
                 const uint32_t full = smem_u32(&ring.full[s]);
-                const uint32_t dbase = stage_base + 4u * (uint32_t)(s * tr_stage_words());
+                const uint32_t dbase = stage_base + 4u * (uint32_t)(s * SW);
                 int as[KS], e2[KS];
                 uint32_t b1[KS];
                 uint32_t total = 0;
@@ -254,12 +274,16 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                     }
                 }
                 mbar_arrive(full);
-                issued_last = g;
+                if (s == 0)
+                    issued[0] = u + 1;
+                else
+                    issued[TR_STAGES - 1] = u + 1;
             }
             if (*ring.abort_flag) {
                 // copies still in flight must land before the CTA moves on
-                for (int g = max(it0, issued_last - TR_STAGES + 1); g <= issued_last; g++)
-                    if (!mbar_wait(smem_u32(&ring.full[g % TR_STAGES]), (uint32_t)((g / TR_STAGES) & 1)))
+#pragma unroll
+                for (int q = 0; q < TR_STAGES; q++)
+                    if (issued[q] > 0 && !mbar_wait(smem_u32(&ring.full[q]), (uint32_t)((issued[q] - 1) & 1)))
                         atomicOr(&st->status, WL_ETIMEOUT);
             }
         };
@@ -299,7 +323,7 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         const bool shifted = N4 != N32;   // wrapped spans sit shifted past their threshold
         {
             for (int tile = 0; tile < ntiles; tile++) {
-                const int g = it0 + tile, s = g % TR_STAGES, u = g / TR_STAGES;
+                const int s = S == 1 ? 0 : tile & 1, u = (s == 0 ? use0 : use1) + (S == 1 ? tile : tile >> 1);
                 if (*ring.abort_flag)
                     break;
                 if (!mbar_wait(smem_u32(&ring.full[s]), (uint32_t)(u & 1))) {
@@ -309,10 +333,10 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                 }
                 const int t0 = tile * T;
                 const int Tt = min(T, maxlen - t0);
-                const float *sdata = stage0 + s * tr_stage_words();
-                const int *info0 = (const int *)(sdata + tr_stage_data_words());
+                const float *sdata = stage0 + s * SW;
+                const int *info0 = (const int *)(sdata + SDW);
                 const int *info1 = info0 + TR_MAXSPANS;
-                uint64_t tl = 0;   // this tile's terms: under 100 per thread, each below 2^48
+                uint64_t tl = 0;   // this tile's terms: a few hundred per thread at most, each below 2^48
                 // long lanes: each warp owns whole lanes, 64 lane times per
                 // step; lane l of tile k goes to warp (k L + l) mod 15, so when
                 // 15 does not divide L the extra lanes rotate over the warps
@@ -414,7 +438,10 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         // the next pass reads this pool with bulk copies (the async proxy)
         asm volatile("fence.proxy.async.global;\n" ::: "memory");
     }
-    ring.it = it0 + ntiles;
+    // the uses every thread counted, the same in all of them
+    ring.uses[0] = use0 + (S == 1 ? ntiles : (ntiles + 1) >> 1);
+    if (S > 1)
+        ring.uses[TR_STAGES - 1] = use1 + (ntiles >> 1);
 }
 
 // All passes of the spec (a pool wl_tma_run_eligible accepts) from global
