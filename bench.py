@@ -777,6 +777,73 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
         "status": int(status)}), flush=True)
 
 
+def lane_count(N: int) -> int:
+    """Lanes of the lane-tiled geometry of an n = 4 pool of length N: the lcm
+    of any pass's strides, p^2 q for p < q the smallest odd primes not
+    dividing N (the stride candidates are the odd divisors of p^2 q).  Used
+    only to sort pool sizes into classes."""
+    pr = [p for p in (3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61) if N % p][:2]
+    return pr[0] * pr[0] * pr[1]
+
+
+# n4div: 4 divides N; other: it does not; small: N below 2^14 (per-thread paths)
+BATCH_CLASSES = {
+    "45_lanes_n4div": lambda N: N >= 1 << 14 and lane_count(N) == 45 and N % 4 == 0,
+    "45_lanes_other": lambda N: N >= 1 << 14 and lane_count(N) == 45 and N % 4 != 0,
+    "63_lanes": lambda N: N >= 1 << 14 and lane_count(N) == 63,
+    "175_lanes": lambda N: N >= 1 << 14 and lane_count(N) == 175,
+    "539_lanes": lambda N: N >= 1 << 14 and lane_count(N) == 539,
+    "over_539_lanes": lambda N: N >= 1 << 14 and lane_count(N) > 539,
+    "small": lambda N: N < 1 << 14,
+}
+
+
+def batched_classes_bench(names=None, pools: int = 1024, passes: int = 10, runs: int = 3):
+    """The bulk-copy batched runner on one class of pool sizes at a time:
+    `pools` generators whose N (log-uniform on [2^14, 2^18], or [2^8, 2^14]
+    for the small class, seeded) fall in the class, `runs` timed launches of
+    `passes` passes after one warm-up launch; rate in algorithmic bytes."""
+    import numpy as np
+    import torch
+    from paper_1004_3114_gb300 import wallace as W
+    peak, kind = hbm_peak()
+    res = {}
+    for name in names or list(BATCH_CLASSES):
+        cond = BATCH_CLASSES[name]
+        rng = np.random.default_rng(11)
+        lo, hi = (8, 14) if name.startswith("small") else (14, 18)
+        Ns = []
+        while len(Ns) < pools:
+            N = int(2 ** (lo + (hi - lo) * rng.random()))
+            if cond(N):
+                Ns.append(N)
+        Ns = np.array(Ns, dtype=np.int64)
+        stream = torch.cuda.Stream()
+        b = W.Batch(4, Ns, np.arange(pools, dtype=np.uint32), 1.0, stream=stream)
+        b.set_tuning(0, 2560, 2048)
+        out = torch.empty(b.out_size(passes), dtype=torch.float32, device="cuda")
+        b.run(passes, out)
+        b.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(runs):
+                b.run(passes, out)
+            ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / (runs * passes)
+        status = b.sync()
+        nu = int(4 * Ns.sum())
+        byt = 8 * nu + 4 * int(b.R.sum())
+        res[name] = {"pools": pools, "sum_nu": nu, "ms_per_pass": ms, "TBps": byt / (ms * 1e-3) / 1e12,
+                     "frac": byt / (ms * 1e-3) / 1e9 / peak, "status": int(status)}
+        b.close()
+        del out
+    print(json.dumps({"metric": "batched bulk-copy runner by pool class: algorithmic bytes per second",
+                      "peak_gbs": peak, "peak_kind": kind, "passes_per_launch": passes, "runs": runs,
+                      "tuning": [0, 2560, 2048], "classes": res}), flush=True)
+
+
 def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float = 50_000.0,
                 budget_gb: float = 40.0, passes_per_tick: int = 2, ctas_per_sm: int = 0):
     """Serving loop: n_clients generators (n = 4, N log-uniform on
@@ -856,6 +923,13 @@ def main():
     ap.add_argument("--serve-ppt", type=int, default=2)
     ap.add_argument("--serve-ctas", type=int, default=0,
                     help="CTAs per SM of the one-CTA requests; 0: bulk-copy runner where it applies")
+    ap.add_argument("--batched-classes", action="store_true",
+                    help="the bulk-copy batched runner on one class of pool sizes (lane count) at a time")
+    ap.add_argument("--class", dest="classes", action="append", choices=list(BATCH_CLASSES),
+                    help="with --batched-classes: only this class (repeatable)")
+    ap.add_argument("--class-pools", type=int, default=1024)
+    ap.add_argument("--class-passes", type=int, default=10)
+    ap.add_argument("--class-runs", type=int, default=3)
     ap.add_argument("--precision-study", action="store_true",
                     help="binary32 vs binary64 pool study (N=2^22, n=4 and 8, 1000 passes) instead of the benchmark")
     args = ap.parse_args()
@@ -864,6 +938,10 @@ def main():
         return
     if args.batched:
         batched_bench(power_of_two=args.pow2, count=args.batched_count, runs=args.batched_runs)
+        return
+    if args.batched_classes:
+        batched_classes_bench(args.classes, pools=args.class_pools, passes=args.class_passes,
+                              runs=args.class_runs)
         return
     if args.small:
         small_config_bench()
