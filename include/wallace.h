@@ -471,6 +471,20 @@ int wallace_pass_static(int n, int64_t N, float *pool, const int32_t *alpha, con
 int wallace_boxmuller_fill(uint32_t seed, uint32_t stream_id, int64_t offset, float *out,
                            int64_t count, float mu, float sigma, int exact, void *cuda_stream);
 
+/*
+ * wallace_selftest_bounded_wait -- exercises the bounded device-side wait
+ * that every shared-memory barrier wait of the bulk-copy kernels uses (not a
+ * part of the paper's method: the library's own failure detection).  One
+ * CTA on the current device waits on a barrier that nothing arrives at, which
+ * must give up after its cycle budget (about one second), and on a barrier
+ * whose phase has completed, which must return at once.  Synchronous.
+ * Returns WALLACE_ETIMEOUT when the first wait gave up as designed (the
+ * context stays usable), WALLACE_OK if it did not, WALLACE_ECUDA on a CUDA
+ * error.  *completed_ok (may be NULL) receives 1 when the second wait
+ * returned.
+ */
+int wallace_selftest_bounded_wait(int *completed_ok);
+
 /* wallace_strerror -- static text for a status code (lowest set bit). */
 const char *wallace_strerror(int code);
 

@@ -125,6 +125,7 @@ _SIGS = {
                                       C.POINTER(PassResult), C.c_void_p]),
     "wallace_boxmuller_fill": (C.c_int, [C.c_uint32, C.c_uint32, C.c_int64, C.c_void_p, C.c_int64,
                                          C.c_float, C.c_float, C.c_int, C.c_void_p]),
+    "wallace_selftest_bounded_wait": (C.c_int, [C.POINTER(C.c_int)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -327,6 +328,15 @@ def boxmuller_fill(out, seed: int, stream_id: int = 0, offset: int = 0, mu: floa
     _check(_lib.wallace_boxmuller_fill(seed, stream_id, offset, C.c_void_p(out.data_ptr()),
                                        out.numel(), mu, sigma, 1 if exact else 0, _stream_ptr(stream)),
            "wallace_boxmuller_fill")
+
+
+def selftest_bounded_wait() -> tuple[int, bool]:
+    """wallace_selftest_bounded_wait: (status of the wait on a barrier nothing
+    arrives at -- ETIMEOUT when it gave up as designed --, whether the wait on
+    a completed barrier returned)."""
+    ok = C.c_int(0)
+    rc = int(_lib.wallace_selftest_bounded_wait(C.byref(ok)))
+    return rc, bool(ok.value)
 
 
 class WallaceError(RuntimeError):
