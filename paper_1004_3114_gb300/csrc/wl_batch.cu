@@ -62,9 +62,8 @@ struct BatchArgs {
 
 __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
 {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     __shared__ uint64_t red[3 * (BT_THREADS / 32)];
-    __shared__ int32_t s_prm[20];
     __shared__ int s_k;
     __shared__ WlDevState sst;   // the running generator's state
     const int tid = threadIdx.x;
@@ -95,21 +94,20 @@ __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
         r.etarget = a.etarget;
         wl_state_load(&sst, d.st);
         r.st = &sst;
-        const int cur = wl_run_spec(r, a.fused_max, smem_values, smem, red, s_prm);
+        const int cur = wl_run_spec(r, a.fused_max, smem_values, smem, red);
         wl_state_store(d.st, &sst);
         if (tid == 0)
             a.streams[a.order[k]].cur = cur;
     }
 }
 
-// The same work with the CTA-local bulk-copy runner for pools the
-// single-generator pass would tile with bulk copies (n = 4, N % 4 == 0,
-// N >= TM_MIN_N): one CTA of TM_THREADS threads per SM.
+// The same work with the CTA-local bulk-copy runner for the pools it takes
+// (wl_tma_run_eligible: n = 4, N >= TM_MIN_N): one CTA of TM_THREADS threads
+// per SM; the other pools as in batch_kernel.
 __global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
 {
     extern __shared__ __align__(128) float smem[];
     __shared__ uint64_t red[3 * (TM_THREADS / 32 + 1)];
-    __shared__ int32_t s_prm[20];
     __shared__ int s_k;
     __shared__ __align__(8) uint64_t bar_full[TR_STAGES];
     __shared__ __align__(8) uint64_t bar_empty[TR_STAGES];
@@ -150,9 +148,9 @@ __global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
         wl_state_load(&sst, d.st);
         r.st = &sst;
         if (wl_tma_run_eligible(d.n, d.N) && !wl_run_is_fused(4, d.N, a.fused_max, smem_values))
-            cur = wl_run_tma(r, smem, red, s_prm, ring);
+            cur = wl_run_tma(r, smem, red, ring);
         else
-            cur = wl_run_spec(r, a.fused_max, smem_values, smem, red, s_prm);
+            cur = wl_run_spec(r, a.fused_max, smem_values, smem, red);
         wl_state_store(d.st, &sst);
         if (tid == 0)
             a.streams[a.order[k]].cur = cur;

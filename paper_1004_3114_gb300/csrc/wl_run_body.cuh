@@ -64,7 +64,7 @@ __device__ void wl_gather_range_n(const float *src, float *dst, int64_t N, int64
 // All passes with the pool in shared memory (2 n N floats of `sm`); the pool
 // is written back to buf[cur] at the end.
 template <int NSUB>
-__device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red, int32_t *s_prm)
+__device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red)
 {
     const int tid = threadIdx.x, nth = blockDim.x;
     const int N = (int)d.N, nu = NSUB * N;
@@ -199,14 +199,14 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
 // caller has (smem_values floats) and n N <= fused_max; returns the final
 // buffer index (unchanged for the fused path, which writes back in place).
 __device__ inline int wl_run_spec(const WlRunSpec &d, int64_t fused_max, int64_t smem_values, float *sm,
-                                  uint64_t *red, int32_t *s_prm)
+                                  uint64_t *red)
 {
     const int64_t nu = (int64_t)d.n * d.N;
     if (nu <= fused_max && 2 * nu <= smem_values) {
         if (d.n == 4)
-            wl_run_fused<4>(d, sm, red, s_prm);
+            wl_run_fused<4>(d, sm, red);
         else
-            wl_run_fused<8>(d, sm, red, s_prm);
+            wl_run_fused<8>(d, sm, red);
         return d.cur;
     }
     return d.n == 4 ? wl_run_global<4>(d, sm, red) : wl_run_global<8>(d, sm, red);

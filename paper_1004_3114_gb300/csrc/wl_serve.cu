@@ -56,9 +56,8 @@ struct ServeItem {
 __global__ void __launch_bounds__(SV_THREADS, 3) serve_kernel(const ServeItem *items, int count,
                                                              int *queue, int64_t fused_max)
 {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     __shared__ uint64_t red[3 * (SV_THREADS / 32)];
-    __shared__ int32_t s_prm[20];
     __shared__ int s_k;
     __shared__ WlDevState sst;   // the running request's generator state
     const int tid = threadIdx.x;
@@ -81,7 +80,7 @@ __global__ void __launch_bounds__(SV_THREADS, 3) serve_kernel(const ServeItem *i
             WlRunSpec r = it.spec;
             wl_state_load(&sst, it.spec.st);
             r.st = &sst;
-            wl_run_spec(r, fused_max, smem_values, smem, red, s_prm);
+            wl_run_spec(r, fused_max, smem_values, smem, red);
             wl_state_store(it.spec.st, &sst);
         }
     }
@@ -101,7 +100,6 @@ __global__ void __launch_bounds__(TM_THREADS, 1) serve_tma_kernel(const ServeIte
 {
     extern __shared__ __align__(128) float smem[];
     __shared__ uint64_t red[3 * (TM_THREADS / 32 + 1)];
-    __shared__ int32_t s_prm[20];
     __shared__ int s_k;
     __shared__ __align__(8) uint64_t bar_full[TR_STAGES];
     __shared__ __align__(8) uint64_t bar_empty[TR_STAGES];
@@ -132,9 +130,9 @@ __global__ void __launch_bounds__(TM_THREADS, 1) serve_tma_kernel(const ServeIte
             wl_state_load(&sst, it.spec.st);
             r.st = &sst;
             if (sv_bulk_eligible(it.spec.n, it.spec.N, it.spec.passes, fused_max, smem_values))
-                wl_run_tma(r, smem, red, s_prm, ring);
+                wl_run_tma(r, smem, red, ring);
             else
-                wl_run_spec(r, fused_max, smem_values, smem, red, s_prm);
+                wl_run_spec(r, fused_max, smem_values, smem, red);
             wl_state_store(it.spec.st, &sst);
         }
     }
@@ -177,7 +175,7 @@ __global__ void __launch_bounds__(SV_THREADS, 3) pass_units_kernel(const PassIte
                                                                   const PassUnit *units, int nunits,
                                                                   int *queue)
 {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
     __shared__ uint64_t red[3 * (SV_THREADS / 32)];
     __shared__ int s_k;
     const int tid = threadIdx.x;

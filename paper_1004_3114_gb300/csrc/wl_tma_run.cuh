@@ -447,8 +447,8 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
 // All passes of the spec (a pool wl_tma_run_eligible accepts) from global
 // memory through the bulk-copy pass; a pass whose strides have lcm above
 // TR_LMAX takes the plain gather.  Returns the index of the buffer holding the
-// final pool.  s_prm: at least 9 words of shared memory.
-__device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red, int32_t *s_prm,
+// final pool.
+__device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
                                  WlTmaRing &ring)
 {
     const int tid = threadIdx.x;
