@@ -589,7 +589,8 @@ def variant_bench(steps: int = 2000, warmup: int = 5):
     pass per step as in the default line: RANN4 itself (n = 2, N = 2^25,
     frac = 1/3 as RANN4's f = 3), and n = 4 with a random sign pattern per
     pass, with the Wilson-Hilferty sample, and with restarts every 1000 N / R
-    passes (Section 5)."""
+    passes (Section 5); n = 8 (A = J/4 - I, N = 2^23: plain strided gather)
+    and the binary64 reference pool (plain gather, 16 bytes per pool value)."""
     import torch
     from paper_1004_3114_gb300 import wallace as W
     peak, kind = hbm_peak()
@@ -598,6 +599,8 @@ def variant_bench(steps: int = 2000, warmup: int = 5):
         ("n4_signs", 4, 1 << 24, 0.5, W.FP32 | W.MATRIX_SIGNS, 0),
         ("n4_wilson_hilferty", 4, 1 << 24, 0.5, W.FP32 | W.CHI_WH, 0),
         ("n4_restart", 4, 1 << 24, 0.5, W.FP32, -1),
+        ("n8", 8, 1 << 23, 0.5, W.FP32, 0),
+        ("n4_fp64_pool", 4, 1 << 24, 0.5, W.FP64POOL, 0),
     ]
     res = {}
     stream = torch.cuda.Stream()
@@ -605,7 +608,8 @@ def variant_bench(steps: int = 2000, warmup: int = 5):
         g = W.Wallace(n, N, SEED, frac, mode=mode, stream=stream)
         if restart:
             g.set_restart(max(1, (1000 * N) // g.R))
-        out = torch.empty(g.R, dtype=torch.float32, device="cuda")
+        esize = 8 if mode == W.FP64POOL else 4
+        out = torch.empty(g.R, dtype=torch.float64 if esize == 8 else torch.float32, device="cuda")
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 g.fill(out)
@@ -621,7 +625,7 @@ def variant_bench(steps: int = 2000, warmup: int = 5):
         ms = e0.elapsed_time(e1)
         s1 = g.stats()
         nu = n * N
-        bytes_pass = 8 * nu + 4 * g.R
+        bytes_pass = 2 * esize * nu + esize * g.R
         launches = s1.launches - s0.launches
         res[name] = {"n": n, "N": N, "frac": frac, "value": steps * g.R / (ms * 1e-3),
                      "ms_per_pass": ms / steps, "launches_per_pass": launches / steps,
