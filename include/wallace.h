@@ -81,6 +81,12 @@ typedef struct wallace wallace_t;
                                          into a stage ring; needs N % 4 == 0 and, for
                                          n = 4, N coprime to 15 (else the per-thread-copy
                                          kernel runs)                                   */
+#define WALLACE_VARIANT_TWOPHASE    6 /* n = 8 binary32 pools: every sub-vector
+                                         un-strided into a j-ordered copy, then the
+                                         transform streamed over it (2 launches per
+                                         pass; a third pool-sized buffer held from
+                                         creation when every stride N can draw is
+                                         at most 16384)                              */
 
 /* Scalars of the most recent pass (or of the initial pool after create). */
 typedef struct {

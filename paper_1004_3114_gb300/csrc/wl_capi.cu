@@ -21,6 +21,7 @@ struct wallace {
     int device = 0, sm_count = 1;
     cudaStream_t stream = nullptr;
     void *pool[2] = {nullptr, nullptr};
+    void *scratch = nullptr;      // the two-phase pass's j-ordered copy (n = 8, binary64 pools)
     int cur = 0;
     int64_t pass_index = 0;   // passes launched (selects a pass's strides slot)
     uint32_t seed = 0, stream_id = 0;
@@ -114,7 +115,25 @@ int pick_variant(const wallace_t *h)
         return WALLACE_VARIANT_TILED;
     if (wl_fused_supported(h->n, h->N, fp64, nullptr))
         return WALLACE_VARIANT_FUSED;
+    if (h->scratch)
+        return WALLACE_VARIANT_TWOPHASE;
     return WALLACE_VARIANT_GATHER;
+}
+
+// Largest stride a pass of (n, N) can draw (the n = 4, 8 candidates are the
+// odd divisors of p^2 q, p^2 q r; n = 2's fallback stays below 64): the
+// two-phase pass needs every stride within its shared-memory block.
+int64_t max_stride(int n, int64_t N)
+{
+    if (n == 2)
+        return 64;
+    const int64_t P[17] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61};
+    int64_t pr[3] = {0, 0, 0};
+    int got = 0;
+    for (int k = 0; k < 17 && got < 3; k++)
+        if (N % P[k] != 0)
+            pr[got++] = P[k];
+    return n == 8 ? pr[0] * pr[0] * pr[1] * pr[2] : pr[0] * pr[0] * pr[1];
 }
 
 // One pass on the device.  Values q in [w0, w1) of the new pool are also
@@ -174,7 +193,10 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
                   v == WALLACE_VARIANT_TILED_TMA) &&
                  wl_tiled_supported(h->n, h->N, fp64))
             e = wl_launch_tiled(a, h->sm_count, h->stream);
-        else
+        else if (v == WALLACE_VARIANT_TWOPHASE && h->scratch) {
+            e = wl_launch_twophase(a, h->scratch, fp64, h->sm_count, h->stream);
+            h->launches++;   // its second kernel
+        } else
             e = wl_launch_gather(a, fp64, h->sm_count, h->stream);
     }
     if (e != cudaSuccess)
@@ -314,6 +336,15 @@ int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, doubl
         wallace_destroy(h);
         return WALLACE_ENOMEM;
     }
+    // n = 8 binary32 pools: the two-phase pass's scratch copy, when every
+    // stride this N can draw fits its block (else they keep the plain gather;
+    // binary64 pools keep it too: their transform is bound by the binary64
+    // units, so a second phase would only add traffic)
+    if (n == 8 && mode == WALLACE_FP32 && max_stride(n, N) <= WL_TWOPHASE_MAX_STRIDE &&
+        cudaMalloc(&h->scratch, bytes) != cudaSuccess) {
+        wallace_destroy(h);
+        return WALLACE_ENOMEM;
+    }
     e = cudaMemsetAsync(h->pool[0], 0, bytes, h->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(h->pool[1], 0, bytes, h->stream);
@@ -342,6 +373,7 @@ void wallace_destroy(wallace_t *h)
     cudaStreamSynchronize(h->stream);
     if (h->copy_stream)
         cudaStreamSynchronize(h->copy_stream);
+    cudaFree(h->scratch);
     for (int b = 0; b < 2; b++) {
         cudaFree(h->pool[b]);
         cudaFree(h->stage[b]);
@@ -480,6 +512,10 @@ int wallace_set_variant(wallace_t *h, int variant)
         break;
     case WALLACE_VARIANT_TILED_ASYNC:
         if (!wl_tiled_supported(h->n, h->N, fp64))
+            return WALLACE_EINVAL;
+        break;
+    case WALLACE_VARIANT_TWOPHASE:
+        if (!h->scratch)
             return WALLACE_EINVAL;
         break;
     case WALLACE_VARIANT_FUSED:

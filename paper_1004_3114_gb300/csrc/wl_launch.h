@@ -34,6 +34,11 @@ cudaError_t wl_launch_restart(void *pool, int fp64, int n, int64_t N, int64_t Np
                               cudaStream_t stream);
 
 // direct strided gather from global memory, any n, N, either precision
+// Two-phase pass for stride sets with strides up to WL_TWOPHASE_MAX_STRIDE
+// (binary32; half of it for binary64 pools): un-stride into `scratch` (n rows
+// of pitch Np), then stream the transform (2 launches).
+#define WL_TWOPHASE_MAX_STRIDE 16384
+cudaError_t wl_launch_twophase(const WlPassArgs &a, void *scratch, int fp64, int sm_count, cudaStream_t stream);
 cudaError_t wl_launch_gather(const WlPassArgs &a, int fp64, int sm_count, cudaStream_t stream);
 
 // out[k] = mu + sigma * pool[pos + k], k < count (values already produced)

@@ -10,7 +10,9 @@
 
 namespace {
 
-template <int NSUB, typename T>
+// IDENT: src already holds g_i in j order (the two-phase pass below):
+// index j itself, one unit-stride read per sub-vector.
+template <int NSUB, typename T, bool IDENT = false>
 __global__ void __launch_bounds__(256) gather_kernel(WlPassArgs a)
 {
     __shared__ uint64_t red[3 * 8];
@@ -25,9 +27,14 @@ __global__ void __launch_bounds__(256) gather_kernel(WlPassArgs a)
     int64_t idx[NSUB], step[NSUB];
 #pragma unroll
     for (int i = 0; i < NSUB; i++) {
-        int64_t al = st->next.alpha[i], ga = st->next.gamma[i];
-        idx[i] = (int64_t)(((uint64_t)al * (uint64_t)(j < N ? j : 0) + (uint64_t)ga) % (uint64_t)N);
-        step[i] = (int64_t)(((uint64_t)al * (uint64_t)G) % (uint64_t)N);
+        if constexpr (IDENT) {
+            idx[i] = j;
+            step[i] = G;
+        } else {
+            int64_t al = st->next.alpha[i], ga = st->next.gamma[i];
+            idx[i] = (int64_t)(((uint64_t)al * (uint64_t)(j < N ? j : 0) + (uint64_t)ga) % (uint64_t)N);
+            step[i] = (int64_t)(((uint64_t)al * (uint64_t)G) % (uint64_t)N);
+        }
     }
     T *out = (T *)a.out;
     const T mu = (T)a.mu, sigma = (T)a.sigma;
@@ -42,7 +49,7 @@ __global__ void __launch_bounds__(256) gather_kernel(WlPassArgs a)
         for (int i = 0; i < NSUB; i++) {
             g[i] = wl_sgn(src[i * Np + idx[i]], signs, i);
             idx[i] += step[i];
-            if (idx[i] >= N)
+            if (!IDENT && idx[i] >= N)
                 idx[i] -= N;
         }
         if constexpr (sizeof(T) == 8) {
@@ -81,6 +88,101 @@ __global__ void __launch_bounds__(256) gather_kernel(WlPassArgs a)
     if (wl_last_cta(st) && threadIdx.x == 0) {
         double x = (double)__ldcg(&dst[wl_phys(a.nu - 1, N, Np)]);
         wl_finalise(st, a.n, N, a.nu, x, f64, WL_FIN_PASS);
+    }
+}
+
+// Phase 1 of the two-phase pass: tmp_i[j] = x_i[(alpha_i j + gamma_i) mod N]
+// for every sub-vector, with unit-stride reads and writes.  For one
+// sub-vector the alpha lanes l (starting at J_l = ceil(l N / alpha)) read, at
+// lane time t, the alpha consecutive addresses alpha t + gamma + [0, alpha)
+// mod N, lane l the one at offset r_l = alpha J_l - l N (the r_l are a
+// permutation of 0..alpha-1 since gcd(alpha, N) = 1; Eq. 2).  A tile of TT
+// lane times is therefore one contiguous block of alpha TT values, loaded
+// into shared memory, and alpha runs of TT values in j order, written from
+// it.  Work items (sub-vector, tile) are dealt over the grid; inside a tile,
+// (lane, 256-time chunk) items over the warps.
+#define US_THREADS 256
+// values per block: 64 KB of shared memory, three CTAs per SM
+template <typename T>
+__host__ __device__ constexpr int64_t us_bmax() { return sizeof(T) == 8 ? WL_TWOPHASE_MAX_STRIDE / 2 : WL_TWOPHASE_MAX_STRIDE; }
+
+template <typename T>
+__global__ void __launch_bounds__(US_THREADS) unstride_kernel(const T *__restrict__ src, T *__restrict__ tmp,
+                                                               const WlDevState *st, int n, int64_t N,
+                                                               int64_t Np)
+{
+    extern __shared__ __align__(16) unsigned char usm[];
+    T *blk = (T *)usm;
+    constexpr int64_t US_BMAX = us_bmax<T>();
+    int64_t pre[9];
+    pre[0] = 0;
+    for (int i = 0; i < n; i++) {
+        const int64_t al = st->next.alpha[i];
+        const int64_t TT = al < US_BMAX ? US_BMAX / al : 1;
+        const int64_t maxlen = (N + al - 1) / al;
+        pre[i + 1] = pre[i] + (maxlen + TT - 1) / TT;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t w = blockIdx.x; w < pre[n]; w += gridDim.x) {
+        int i = 0;
+        while (w >= pre[i + 1])
+            i++;
+        const int64_t al = st->next.alpha[i], ga = st->next.gamma[i];
+        const int64_t TT = al < US_BMAX ? US_BMAX / al : 1;
+        const int64_t maxlen = (N + al - 1) / al;
+        const int64_t t0 = (w - pre[i]) * TT;
+        const int Tt = (int)min(TT, maxlen - t0);
+        int64_t a0 = al * t0 + ga;   // < 3N
+        if (a0 >= N)
+            a0 -= N;
+        if (a0 >= N)
+            a0 -= N;
+        const int blen = (int)min(al * Tt, N - al * t0);
+        const T *row = src + (int64_t)i * Np;
+        __syncthreads();   // the previous tile's readers are done
+        // value e of the block goes to blk[lead + e].  16-byte async copies of
+        // the block's aligned cover; when the block wraps past N, only the
+        // whole chunks below N (the rest of the cover would land where the
+        // wrapped values go), and the values from the last whole chunk up to
+        // N and the wrapped ones from the row start, one copy per value.  A
+        // block that does not wrap may read a few values past its end (the
+        // row pitch leaves room past N) into unused words.
+        constexpr int VPC = 16 / sizeof(T);
+        const int64_t a0s = a0 & ~(int64_t)(VPC - 1);
+        const int lead = (int)(a0 - a0s);
+        const bool wraps = a0 + blen > N;
+        const int nchunk = wraps ? (int)((N - a0s) / VPC) : (int)((a0 + blen - a0s + VPC - 1) / VPC);
+        const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(blk);
+        for (int ck = threadIdx.x; ck < nchunk; ck += US_THREADS)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sbase + 16u * (uint32_t)ck),
+                         "l"(row + a0s + (int64_t)ck * VPC)
+                         : "memory");
+        if (wraps) {
+            // positions nchunk VPC .. lead + blen - 1: row[a0s + p] below N, then row[p - (N - a0s)]
+            const int p0 = nchunk * VPC, p1 = lead + blen, pN = (int)(N - a0s);
+            for (int q = p0 + (int)threadIdx.x; q < p1; q += US_THREADS)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(
+                                 sbase + (uint32_t)sizeof(T) * (uint32_t)q),
+                             "l"(q < pN ? row + a0s + q : row + (q - pN)), "n"(sizeof(T))
+                             : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        T *out = tmp + (int64_t)i * Np;
+        const int nch = (Tt + 255) >> 8;
+        const int items = (int)al * nch;
+        const int64_t q = N / al, rm = N - q * al;
+        for (int it = warp; it < items; it += US_THREADS / 32) {
+            const int l = it / nch, ch = it - l * nch;
+            // J_l = l q + ceil(l rm / al); lane length J_{l+1} - J_l
+            const int64_t Jl = (int64_t)l * q + ((int64_t)l * rm + al - 1) / al;
+            const int64_t Jn = (int64_t)(l + 1) * q + ((int64_t)(l + 1) * rm + al - 1) / al;
+            const int rl = (int)(al * Jl - (int64_t)l * N);
+            const int tend = (int)min((int64_t)min(Tt, (ch + 1) << 8), Jn - Jl - t0);
+            for (int t = (ch << 8) + lane; t < tend; t += 32)
+                out[Jl + t0 + t] = blk[lead + rl + (int)al * t];
+        }
     }
 }
 
@@ -123,6 +225,47 @@ cudaError_t wl_launch_gather(const WlPassArgs &a, int fp64, int sm_count, cudaSt
             gather_kernel<8, float><<<grid, 256, 0, stream>>>(a);
     }
     return cudaGetLastError();
+}
+
+// Two-phase pass: every sub-vector un-strided into `scratch` (same layout as
+// a pool), then the transform streamed over j.
+template <int NSUB, typename T>
+static cudaError_t launch_twophase(const WlPassArgs &a, void *scratch, int sm_count, cudaStream_t stream)
+{
+    static bool configured = false;
+    const size_t smem = sizeof(T) * (us_bmax<T>() + 32 / sizeof(T));   // + the lead and the cover's tail
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(unstride_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        configured = true;
+    }
+    const int per_sm = 3;
+    unstride_kernel<T><<<sm_count * per_sm, US_THREADS, smem, stream>>>((const T *)a.src, (T *)scratch, a.st,
+                                                                        NSUB, a.N, a.Np);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    WlPassArgs b = a;
+    b.src = scratch;
+    int64_t want = (a.N + 255) / 256;
+    int64_t cap = (int64_t)sm_count * 8;
+    int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    gather_kernel<NSUB, T, true><<<grid, 256, 0, stream>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t wl_launch_twophase(const WlPassArgs &a, void *scratch, int fp64, int sm_count, cudaStream_t stream)
+{
+    if (a.n == 2)
+        return fp64 ? launch_twophase<2, double>(a, scratch, sm_count, stream)
+                    : launch_twophase<2, float>(a, scratch, sm_count, stream);
+    if (a.n == 4)
+        return fp64 ? launch_twophase<4, double>(a, scratch, sm_count, stream)
+                    : launch_twophase<4, float>(a, scratch, sm_count, stream);
+    return fp64 ? launch_twophase<8, double>(a, scratch, sm_count, stream)
+                : launch_twophase<8, float>(a, scratch, sm_count, stream);
 }
 
 cudaError_t wl_launch_drain(const void *pool, int fp64, int64_t N, int64_t Np, int64_t pos,

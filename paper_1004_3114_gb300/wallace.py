@@ -23,7 +23,7 @@ FP32, FP64POOL = 0, 1
 CHI_WH = 0x100   # mode flag: Wilson-Hilferty chi-squared sample
 MATRIX_SIGNS = 0x200   # mode flag: random sign pattern per pass (matrix A D_k)
 VARIANT_AUTO, VARIANT_GATHER, VARIANT_TILED, VARIANT_FUSED = 0, 1, 2, 3
-VARIANT_TILED_ASYNC, VARIANT_TILED_TMA = 4, 5
+VARIANT_TILED_ASYNC, VARIANT_TILED_TMA, VARIANT_TWOPHASE = 4, 5, 6
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with "

@@ -172,6 +172,43 @@ def test_fp64_pool_mode_bit_exact(orc, n, N):
         assert_stats_equal(g, o, f"fp64 pass {k}")
 
 
+@pytest.mark.parametrize("n,N,frac,variant,mode", [
+    (8, 20000, 0.5, W.VARIANT_TWOPHASE, W.FP32),
+    (8, 100003, 1 / 3, W.VARIANT_AUTO, W.FP32),       # AUTO picks the two-phase pass
+    (8, 1 << 16, 1.0, W.VARIANT_TWOPHASE, W.FP32),
+    (8, 9000, 0.25, W.VARIANT_TWOPHASE, W.FP32),      # 3 and 5 divide N: strides up to 7^2 11 13
+    (8, 16385, 0.5, W.VARIANT_TWOPHASE, W.FP32),      # N % 4 == 1: blocks that wrap unaligned
+])
+def test_twophase_pass_bit_exact(orc, n, N, frac, variant, mode):
+    """The two-phase pass (every sub-vector un-strided into a j-ordered copy,
+    then the transform streamed): pools, returned values and every state
+    scalar against the oracle, pass by pass."""
+    omode = orc.FP32 if mode == W.FP32 else orc.FP64
+    g = W.Wallace(n, N, 29, frac, mode=mode)
+    g.set_variant(variant)
+    o = orc.Generator(n, N, 29, frac, mode=omode)
+    for k in range(5):
+        assert_same(fill_dev(g, g.R, -2.0, 0.5), o.fill(g.R, -2.0, 0.5), f"pass {k + 1} output")
+        if mode == W.FP32:
+            assert_same(g.pool(), o.pool32(), f"pass {k + 1} pool")
+        else:
+            assert_same(g.pool64(), o.pool64(), f"pass {k + 1} pool")
+        assert_stats_equal(g, o, f"pass {k + 1}")
+    st = g.stats()
+    assert st.launches >= 2 * 5   # two kernels a pass
+
+
+def test_twophase_needs_small_strides(orc):
+    """N = 45045 = 3^2 5 7 11 13: n = 8 strides may reach 17^2 19 23 > 16384,
+    so no two-phase buffer; AUTO keeps the plain gather (still bit-exact)."""
+    g = W.Wallace(8, 45045, 3, 0.5)
+    with pytest.raises(W.WallaceError):
+        g.set_variant(W.VARIANT_TWOPHASE)
+    o = orc.Generator(8, 45045, 3, 0.5)
+    for k in range(2):
+        assert_same(fill_dev(g, g.R), o.fill(g.R), f"pass {k + 1}")
+
+
 def test_corruption_detected(orc):
     g = W.Wallace(4, 16384, 1, 0.5)
     fill_dev(g, 3 * g.R)
@@ -308,6 +345,7 @@ def test_restart_bit_exact(orc, n, N, variant, mode):
     (4, 20000, W.VARIANT_TILED_ASYNC, W.FP32),
     (4, 45045, W.VARIANT_TILED, W.FP32),           # fallback strides: in-kernel gather
     (8, 5000, W.VARIANT_GATHER, W.FP32),
+    (8, 20000, W.VARIANT_TWOPHASE, W.FP32),
     (8, 3001, W.VARIANT_FUSED, W.FP32),
     (4, 1024, W.VARIANT_AUTO, W.FP64POOL),
 ])
