@@ -81,12 +81,13 @@ typedef struct wallace wallace_t;
                                          into a stage ring; needs N % 4 == 0 and, for
                                          n = 4, N coprime to 15 (else the per-thread-copy
                                          kernel runs)                                   */
-#define WALLACE_VARIANT_TWOPHASE    6 /* n = 8 binary32 pools: every sub-vector
-                                         un-strided into a j-ordered copy, then the
-                                         transform streamed over it (2 launches per
-                                         pass; a third pool-sized buffer held from
-                                         creation when every stride N can draw is
-                                         at most 16384)                              */
+#define WALLACE_VARIANT_TWOPHASE    6 /* binary32 pools the lane-tiled kernels cannot
+                                         tile (n = 8; n = 4 with 15 dividing N): every
+                                         sub-vector un-strided into a j-ordered copy,
+                                         then the transform streamed over it (2
+                                         launches per pass; a third pool-sized buffer
+                                         held from creation when every stride N can
+                                         draw is at most 16384)                       */
 
 /* Scalars of the most recent pass (or of the initial pool after create). */
 typedef struct {

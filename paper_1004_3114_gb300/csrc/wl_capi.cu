@@ -111,12 +111,14 @@ int pick_variant(const wallace_t *h)
     if (h->variant != WALLACE_VARIANT_AUTO)
         return h->variant;
     const int fp64 = h->mode == WALLACE_FP64POOL;
+    // a handle with the two-phase buffer has strides the tiled kernels cannot
+    // tile (n = 8, or n = 4 with more than 315 lanes)
+    if (h->scratch && !wl_fused_supported(h->n, h->N, fp64, nullptr))
+        return WALLACE_VARIANT_TWOPHASE;
     if (wl_tiled_supported(h->n, h->N, fp64) || wl_tma_supported(h->n, h->N, fp64, h->sm_count))
         return WALLACE_VARIANT_TILED;
     if (wl_fused_supported(h->n, h->N, fp64, nullptr))
         return WALLACE_VARIANT_FUSED;
-    if (h->scratch)
-        return WALLACE_VARIANT_TWOPHASE;
     return WALLACE_VARIANT_GATHER;
 }
 
@@ -336,11 +338,13 @@ int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, doubl
         wallace_destroy(h);
         return WALLACE_ENOMEM;
     }
-    // n = 8 binary32 pools: the two-phase pass's scratch copy, when every
-    // stride this N can draw fits its block (else they keep the plain gather;
-    // binary64 pools keep it too: their transform is bound by the binary64
-    // units, so a second phase would only add traffic)
-    if (n == 8 && mode == WALLACE_FP32 && max_stride(n, N) <= WL_TWOPHASE_MAX_STRIDE &&
+    // binary32 pools whose strides the lane-tiled kernels cannot tile (n = 8:
+    // 315 lanes; n = 4 with N a multiple of 15: 539 lanes or more) get the
+    // two-phase pass's scratch copy, when every stride this N can draw fits
+    // its block (else they keep the plain gather; binary64 pools keep it too:
+    // their transform is bound by the binary64 units)
+    const int64_t ms = max_stride(n, N);
+    if (mode == WALLACE_FP32 && (n == 8 || (n == 4 && ms > 315)) && ms <= WL_TWOPHASE_MAX_STRIDE &&
         cudaMalloc(&h->scratch, bytes) != cudaSuccess) {
         wallace_destroy(h);
         return WALLACE_ENOMEM;

@@ -178,6 +178,8 @@ def test_fp64_pool_mode_bit_exact(orc, n, N):
     (8, 1 << 16, 1.0, W.VARIANT_TWOPHASE, W.FP32),
     (8, 9000, 0.25, W.VARIANT_TWOPHASE, W.FP32),      # 3 and 5 divide N: strides up to 7^2 11 13
     (8, 16385, 0.5, W.VARIANT_TWOPHASE, W.FP32),      # N % 4 == 1: blocks that wrap unaligned
+    (4, 15 * 4099, 0.5, W.VARIANT_AUTO, W.FP32),      # n = 4, 15 | N: 539 lanes, AUTO two-phase
+    (4, 105 * 1001, 1.0, W.VARIANT_TWOPHASE, W.FP32), # 105 | N: strides up to 11^2 13
 ])
 def test_twophase_pass_bit_exact(orc, n, N, frac, variant, mode):
     """The two-phase pass (every sub-vector un-strided into a j-ordered copy,
@@ -195,7 +197,7 @@ def test_twophase_pass_bit_exact(orc, n, N, frac, variant, mode):
             assert_same(g.pool64(), o.pool64(), f"pass {k + 1} pool")
         assert_stats_equal(g, o, f"pass {k + 1}")
     st = g.stats()
-    assert st.launches >= 2 * 5   # two kernels a pass
+    assert st.launches >= 2 * 5   # two kernels a pass (AUTO picks the two-phase pass here)
 
 
 def test_twophase_needs_small_strides(orc):
