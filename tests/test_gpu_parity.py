@@ -198,6 +198,9 @@ def test_twophase_pass_bit_exact(orc, n, N, frac, variant, mode):
         assert_stats_equal(g, o, f"pass {k + 1}")
     st = g.stats()
     assert st.launches >= 2 * 5   # two kernels a pass (AUTO picks the two-phase pass here)
+    # fills that start mid-pass: returned values land at unaligned addresses
+    for cnt in (1001, 3 * g.R + 5, 7):
+        assert_same(fill_dev(g, cnt, 0.25, 3.0), o.fill(cnt, 0.25, 3.0), f"fill of {cnt}")
 
 
 def test_twophase_needs_small_strides(orc):
