@@ -589,23 +589,29 @@ def variant_bench(steps: int = 2000, warmup: int = 5):
     pass per step as in the default line: RANN4 itself (n = 2, N = 2^25,
     frac = 1/3 as RANN4's f = 3), and n = 4 with a random sign pattern per
     pass, with the Wilson-Hilferty sample, and with restarts every 1000 N / R
-    passes (Section 5); n = 8 (A = J/4 - I, N = 2^23: plain strided gather)
-    and the binary64 reference pool (plain gather, 16 bytes per pool value)."""
+    passes (Section 5); n = 8 (A = J/4 - I) at N = 2^23 (315-lane bulk-copy
+    kernel), the same pool through the two-phase pass, and N = 3 2^21 (strides
+    up to 5^2 7 11: the two-phase pass is AUTO's choice); and the binary64
+    reference pool (plain gather, 16 bytes per pool value)."""
     import torch
     from paper_1004_3114_gb300 import wallace as W
     peak, kind = hbm_peak()
+    A = W.VARIANT_AUTO
     cases = [
-        ("rann4_n2", 2, 1 << 25, 1 / 3, W.FP32, 0),
-        ("n4_signs", 4, 1 << 24, 0.5, W.FP32 | W.MATRIX_SIGNS, 0),
-        ("n4_wilson_hilferty", 4, 1 << 24, 0.5, W.FP32 | W.CHI_WH, 0),
-        ("n4_restart", 4, 1 << 24, 0.5, W.FP32, -1),
-        ("n8", 8, 1 << 23, 0.5, W.FP32, 0),
-        ("n4_fp64_pool", 4, 1 << 24, 0.5, W.FP64POOL, 0),
+        ("rann4_n2", 2, 1 << 25, 1 / 3, W.FP32, 0, A),
+        ("n4_signs", 4, 1 << 24, 0.5, W.FP32 | W.MATRIX_SIGNS, 0, A),
+        ("n4_wilson_hilferty", 4, 1 << 24, 0.5, W.FP32 | W.CHI_WH, 0, A),
+        ("n4_restart", 4, 1 << 24, 0.5, W.FP32, -1, A),
+        ("n8", 8, 1 << 23, 0.5, W.FP32, 0, A),
+        ("n8_twophase", 8, 1 << 23, 0.5, W.FP32, 0, W.VARIANT_TWOPHASE),
+        ("n8_N_3x2p21", 8, 3 << 21, 0.5, W.FP32, 0, A),
+        ("n4_fp64_pool", 4, 1 << 24, 0.5, W.FP64POOL, 0, A),
     ]
     res = {}
     stream = torch.cuda.Stream()
-    for name, n, N, frac, mode, restart in cases:
+    for name, n, N, frac, mode, restart, variant in cases:
         g = W.Wallace(n, N, SEED, frac, mode=mode, stream=stream)
+        g.set_variant(variant)
         if restart:
             g.set_restart(max(1, (1000 * N) // g.R))
         esize = 8 if mode == W.FP64POOL else 4

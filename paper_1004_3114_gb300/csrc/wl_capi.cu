@@ -111,8 +111,11 @@ int pick_variant(const wallace_t *h)
     if (h->variant != WALLACE_VARIANT_AUTO)
         return h->variant;
     const int fp64 = h->mode == WALLACE_FP64POOL;
+    if (wl_tma8_supported(h->n, h->N, fp64) && !wl_fused_supported(h->n, h->N, fp64, nullptr))
+        return WALLACE_VARIANT_TILED;
     // a handle with the two-phase buffer has strides the tiled kernels cannot
-    // tile (n = 8, or n = 4 with more than 315 lanes)
+    // tile (n = 8 with N a multiple of 3, 5 or 7, or n = 4 with more than 315
+    // lanes)
     if (h->scratch && !wl_fused_supported(h->n, h->N, fp64, nullptr))
         return WALLACE_VARIANT_TWOPHASE;
     if (wl_tiled_supported(h->n, h->N, fp64) || wl_tma_supported(h->n, h->N, fp64, h->sm_count))
@@ -191,6 +194,12 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
         if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_TMA) &&
             wl_tma_supported(h->n, h->N, fp64, h->sm_count))
             e = wl_launch_tma(a, h->sm_count, h->msigns, h->stream);
+        else if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_TMA) &&
+                 wl_tma8_supported(h->n, h->N, fp64)) {
+            e = wl_launch_tma8(a, h->sm_count, h->msigns, h->stream);
+            if (wl_tma8_return_kernel(a))
+                h->launches++;   // the returned values' kernel
+        }
         else if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_ASYNC ||
                   v == WALLACE_VARIANT_TILED_TMA) &&
                  wl_tiled_supported(h->n, h->N, fp64))
@@ -511,7 +520,8 @@ int wallace_set_variant(wallace_t *h, int variant)
         break;
     case WALLACE_VARIANT_TILED:
     case WALLACE_VARIANT_TILED_TMA:
-        if (!wl_tiled_supported(h->n, h->N, fp64) && !wl_tma_supported(h->n, h->N, fp64, h->sm_count))
+        if (!wl_tiled_supported(h->n, h->N, fp64) && !wl_tma_supported(h->n, h->N, fp64, h->sm_count) &&
+            !wl_tma8_supported(h->n, h->N, fp64))
             return WALLACE_EINVAL;
         break;
     case WALLACE_VARIANT_TILED_ASYNC:

@@ -56,6 +56,14 @@ bool wl_tma_supported(int n, int64_t N, int fp64, int sm_count);
 // signs: the generator draws a sign pattern per pass (matrix A D_k)
 cudaError_t wl_launch_tma(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream);
 
+// the same for n = 8 (binary32, N a multiple of 4 and coprime to 105: 315
+// lanes, eight sub-vectors per stage)
+bool wl_tma8_supported(int n, int64_t N, int fp64);
+// the pass's returned values, for pools above 64 MB, come from a second
+// kernel (streaming, after the pass): whether this pass takes it
+bool wl_tma8_return_kernel(const WlPassArgs &a);
+cudaError_t wl_launch_tma8(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream);
+
 // whole pool resident in shared memory for `passes` passes in one launch.
 // Pass k (0-based) writes its values [0, take_k) to out + out_off_k where
 // take_k = R for k < passes-1 and last_take for the final pass.

@@ -203,6 +203,41 @@ def test_twophase_pass_bit_exact(orc, n, N, frac, variant, mode):
         assert_same(fill_dev(g, cnt, 0.25, 3.0), o.fill(cnt, 0.25, 3.0), f"fill of {cnt}")
 
 
+@pytest.mark.parametrize("N,frac,seed", [
+    (16384, 0.5, 29),           # smallest: 7 tiles of 315 lanes x 8 lane times
+    (16388, 1 / 3, 5),          # 4 * 17 * 241: spans that wrap at unaligned offsets
+    (1 << 16, 1.0, 7),
+    (100004, 0.25, 11),         # returned prefix ends inside sub-vector 1
+    ((1 << 20) + 12, 0.5, 3),
+    ((1 << 21) + 32, 0.5, 19),  # 32 * 65537: a 64 MB+ pool, returned values from a second kernel
+    ((1 << 21) + 32, 0.3, 23),
+])
+def test_tma8_pass_bit_exact(orc, N, frac, seed):
+    """n = 8 with N coprime to 105: every pass has 315 lanes, and AUTO runs the
+    bulk-copy lane-tiled kernel (pools over 64 MB: then the returned values'
+    kernel).  Pools, returned values and state scalars against the oracle,
+    pass by pass, then fills that start mid-pass."""
+    g = W.Wallace(8, N, seed, frac)
+    o = orc.Generator(8, N, seed, frac)
+    before = g.stats().launches
+    for k in range(5):
+        assert_same(fill_dev(g, g.R, -2.0, 0.5), o.fill(g.R, -2.0, 0.5), f"pass {k + 1} output")
+        assert_same(g.pool(), o.pool32(), f"pass {k + 1} pool")
+        assert_stats_equal(g, o, f"pass {k + 1}")
+    split = 8 * 4 * N > (64 << 20)
+    assert g.stats().launches - before == (10 if split else 5)   # the pass (and its returned values)
+    # a pass that returns nothing yet is a single kernel (the two-phase pass takes two)
+    before = g.stats().launches
+    g.pass_()
+    assert g.stats().launches - before == 1
+    assert_same(fill_dev(g, g.R, 1.0, 2.0), o.fill(g.R, 1.0, 2.0), "values of a wallace_pass")
+    for cnt in (1001, 3 * g.R + 5, 7):
+        assert_same(fill_dev(g, cnt, 0.25, 3.0), o.fill(cnt, 0.25, 3.0), f"fill of {cnt}")
+    # the two-phase pass stays selectable on the same handle
+    g.set_variant(W.VARIANT_TWOPHASE)
+    assert_same(fill_dev(g, 2 * g.R), o.fill(2 * g.R), "two-phase after the tiled kernel")
+
+
 def test_twophase_needs_small_strides(orc):
     """N = 45045 = 3^2 5 7 11 13: n = 8 strides may reach 17^2 19 23 > 16384,
     so no two-phase buffer; AUTO keeps the plain gather (still bit-exact)."""
@@ -351,6 +386,7 @@ def test_restart_bit_exact(orc, n, N, variant, mode):
     (4, 45045, W.VARIANT_TILED, W.FP32),           # fallback strides: in-kernel gather
     (8, 5000, W.VARIANT_GATHER, W.FP32),
     (8, 20000, W.VARIANT_TWOPHASE, W.FP32),
+    (8, 1 << 17, W.VARIANT_TILED_TMA, W.FP32),     # n = 8 bulk-copy kernel, with restarts
     (8, 3001, W.VARIANT_FUSED, W.FP32),
     (4, 1024, W.VARIANT_AUTO, W.FP64POOL),
 ])
