@@ -70,6 +70,10 @@ __device__ inline void wl_tma_ring_init(WlTmaRing &r)
 // tile still holds about TR_ETARGET values per sub-vector; the spans per tile
 // are sum_i L / alpha_i <= 77 + 49 + 11 + 7 for L = 539.
 #define TR_LMAX 539
+/* from this many lanes on (the 539-lane stride sets) a tile's store runs are
+   19 values: the returned values are then copied from the new pool after the
+   pass instead of being stored beside it */
+#define TR_RETURN_COPY_L 539
 #define TR_MAXSPANS 144
 #define TR_SPAN_PAD 12   /* slot words per span beyond alpha T: 3 lead + 3 wrap shift, rounded to 4 */
 
@@ -444,6 +448,34 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         ring.uses[TR_STAGES - 1] = use1 + (ntiles >> 1);
 }
 
+// out[q] = mu + sigma pool[q] for q < w1 (logical positions; rows of N at
+// pitch Np): the returned values of the pass that just wrote `pool`, read
+// back while it is still in L2.  Consecutive threads take consecutive
+// values, eight loads in flight per thread.  Every thread of the CTA calls,
+// after a barrier that follows the pass's stores.
+static __device__ __noinline__ void wl_return_copy(const float *pool, int64_t N, int64_t Np, int64_t w1, float *o, float mu,
+                                      float sigma)
+{
+    const int B = blockDim.x;
+    for (int k = 0; k < 4 && (int64_t)k * N < w1; k++) {
+        const int n = (int)min(N, w1 - (int64_t)k * N);
+        const float *row = pool + k * Np;
+        float *ok = o + (int64_t)k * N;
+        int j = threadIdx.x;
+        for (; j + 7 * B < n; j += 8 * B) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                v[u] = __ldcg(row + j + u * B);
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                ok[j + u * B] = __fadd_rn(mu, __fmul_rn(sigma, v[u]));
+        }
+        for (; j < n; j += B)
+            ok[j] = __fadd_rn(mu, __fmul_rn(sigma, __ldcg(row + j)));
+    }
+}
+
 // All passes of the spec (a pool wl_tma_run_eligible accepts) from global
 // memory through the bulk-copy pass; a pass whose strides have lcm above
 // TR_LMAX takes the plain gather.  Returns the index of the buffer holding the
@@ -475,9 +507,12 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
         uint64_t lo = 0, hi = 0;
         uint32_t bad = 0;
         const int L = wl_lcm4(alpha);
-        if (L <= TR_LMAX && !*ring.abort_flag) {
-            wl_tma_pass_cta(src, dst, N, d.Np, L, alpha, gam, c, o, w1, d.mu, d.sigma, smem, ring, d.st,
-                            lo, hi, bad);
+        const bool tma = L <= TR_LMAX && !*ring.abort_flag;
+        // the plain gather below writes its returned values itself
+        const bool copy_back = tma && L >= TR_RETURN_COPY_L && o && w1 > 0;
+        if (tma) {
+            wl_tma_pass_cta(src, dst, N, d.Np, L, alpha, gam, c, copy_back ? nullptr : o, copy_back ? 0 : w1,
+                            d.mu, d.sigma, smem, ring, d.st, lo, hi, bad);
         } else {
             WlTileJob job;
             job.src = src;
@@ -501,6 +536,8 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
         const float *xp = &dst[wl_phys(nu - 1, N, d.Np)];
         wl_end_pass_cta(st, 4, N, nu, rnu, lo, hi, bad, red, [xp]() { return (double)__ldcg(xp); }, st->msigns,
                         false);
+        if (copy_back)
+            wl_return_copy(dst, N, d.Np, w1, o, d.mu, d.sigma);
         cur = 1 - cur;
     }
     return cur;
