@@ -366,15 +366,17 @@ def run_ours(args, rank, world, local_rank):
     g.set_timing(False)
     isolated_ms = (s1.kernel_ms - s0.kernel_ms) / max(s1.kernel_launches - s0.kernel_launches, 1)
 
-    # end to end through the C ABI into pinned HOST memory (D2H inside the timed region)
-    host = torch.empty(R, dtype=torch.float32).pin_memory()
+    # end to end through the C ABI into pinned HOST memory (D2H inside the timed region):
+    # one wallace_fill_host call for the values of all timed steps, as a caller
+    # streaming values to the host makes it; the call copies each pass's
+    # returned values to the host while the next pass runs
     e2e_steps = max(3, min(args.steps, 20))
-    g.fill_host(host)
+    host = torch.empty(e2e_steps * R, dtype=torch.float32, pin_memory=True)
+    g.fill_host(host[:R])
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        g.fill_host(host)
+    g.fill_host(host)
     e2e_s = time.perf_counter() - t0
     e2e_s, e2e_units = reduce_over_ranks(e2e_s, e2e_steps * R, dist, dev)
 
@@ -416,7 +418,8 @@ def run_ours(args, rank, world, local_rank):
                          "timing": "span of the timed region over its launches (one pass kernel per step)",
                          "algorithmic_bytes_per_launch": BYTES_PER_PASS},
             "e2e": {"value": e2e_units / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * R},
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * R,
+                    "call": f"one wallace_fill_host of {e2e_steps} steps' values into pinned host memory"},
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "status": int(status),
