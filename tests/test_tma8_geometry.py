@@ -1,0 +1,105 @@
+"""Host-side checks of the fixed geometry the n = 8 lane-tiled kernel
+(paper_1004_3114_gb300/csrc/wl_tiled_tma8.cu) is compiled for: 315 lanes,
+8 lane times per tile, at most 300 spans, slots of 8 alpha + 8 words.
+
+The kernel takes these as constants for N coprime to 105 (and N % 4 == 0).
+They follow from the stride candidates of that N (Section 3's strides, with
+the candidate reading of this implementation: the odd divisors above one of
+p^2 q r, p < q < r the smallest odd primes not dividing N) and from the lane
+geometry of Eq. 1 (lane l from J_l = ceil(l N / L); span p of sub-vector i
+starts at ceil(p N / m_i), m_i = L / alpha_i).  The constants are read from
+the kernel source, the candidates from the oracle."""
+import itertools
+import math
+import os
+import random
+import re
+
+import pytest
+
+from oracle import py_oracle as orc
+
+SRC = os.path.join(os.path.dirname(__file__), "..", "paper_1004_3114_gb300", "csrc", "wl_tiled_tma8.cu")
+
+
+def _consts():
+    text = open(SRC).read()
+    vals = {}
+    for name in ("T8_L", "T8_T", "T8_MAXSPANS", "T8_SPAN_PAD"):
+        m = re.search(r"#define %s (\d+)" % name, text)
+        assert m, name
+        vals[name] = int(m.group(1))
+    return vals
+
+
+def _lcm(values):
+    out = 1
+    for v in values:
+        out = out * v // math.gcd(out, v)
+    return out
+
+
+def test_candidates_for_n_coprime_to_105_are_the_divisors_of_315():
+    for N in (1 << 14, 1 << 20, (1 << 21) + 32, 1 << 23, 100004):
+        assert N % 3 and N % 5 and N % 7
+        assert orc.stride_candidates(8, N) == [d for d in range(3, 316, 2) if 315 % d == 0]
+
+
+def test_every_stride_set_has_315_lanes_and_fits_the_stage():
+    c = _consts()
+    L, T, maxsp, pad = c["T8_L"], c["T8_T"], c["T8_MAXSPANS"], c["T8_SPAN_PAD"]
+    cand = orc.stride_candidates(8, 1 << 23)
+    sdw = 8 * L * T + pad * maxsp   # the stage's data words the kernel reserves
+    worst = 0
+    for sub in itertools.combinations(cand, 8):
+        assert _lcm(sub) == L
+        nspans = sum(L // a for a in sub)
+        assert nspans <= maxsp
+        worst = max(worst, nspans)
+        # slots of alpha T values plus the alignment lead and a wrap's rounding
+        assert sum((L // a) * (T * a + pad) for a in sub) <= sdw
+        # 16-byte aligned slots for the bulk copies
+        assert all((T * a + pad) % 4 == 0 for a in sub)
+    assert worst == maxsp   # the eight smallest candidates reach the bound
+
+
+def _tile_reads(N, alpha, gamma, L, T, pad):
+    """Every (sub-vector, lane, lane time) read of every tile through the span
+    slots, as positions of the pool row; checks the bounds on the way."""
+    J = [-((-l * N) // L) for l in range(L + 1)]
+    maxlen = -(-N // L)
+    assert max(J[l + 1] - J[l] for l in range(L)) <= maxlen
+    seen = [[0] * N for _ in range(8)]
+    for tile in range(-(-maxlen // T)):
+        t0 = tile * T
+        Tt = min(T, maxlen - t0)
+        for i in range(8):
+            a, m = alpha[i], L // alpha[i]
+            for l in range(L):
+                w, p = divmod(l, m)
+                C = -((-p * N) // m)
+                r = a * J[l] - w * N - C
+                assert 0 <= r < a
+                start = (C + a * t0 + gamma[i]) % N      # span p of this tile
+                lead = start % 4
+                words = 4 * ((lead + a * Tt + 3) // 4)
+                assert words <= T * a + pad
+                for t in range(min(Tt, J[l + 1] - J[l] - t0)):
+                    off = lead + r + a * t
+                    assert off < words
+                    pos = (start - lead + off) % N
+                    assert pos == (a * (J[l] + t0 + t) + gamma[i]) % N   # Eq. 1
+                    seen[i][J[l] + t0 + t] += 1
+    return seen
+
+
+@pytest.mark.parametrize("N", [16384, 16388, 20012])
+def test_lane_geometry_reads_eq1_positions_once(N):
+    c = _consts()
+    rng = random.Random(N)
+    cand = orc.stride_candidates(8, N)
+    for trial in range(2):
+        alpha = list(cand[:8]) if trial == 0 else rng.sample(cand, 8)
+        gamma = [rng.randrange(N) for _ in range(8)]
+        seen = _tile_reads(N, alpha, gamma, c["T8_L"], c["T8_T"], c["T8_SPAN_PAD"])
+        assert all(v == 1 for row in seen for v in row)
