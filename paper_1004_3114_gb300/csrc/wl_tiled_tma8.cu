@@ -13,9 +13,12 @@
 // reads: at most 105 + 63 + 45 + 35 + 21 + 15 + 9 + 7 = 300 spans of 96 B to
 // 10 KB.  A tile is 8 x 315 x 8 values (80 KB); two stages of it and their
 // slack take 180 KB of shared memory, which is what holds T at 8.  A lane's
-// store run per tile is 32 bytes: the neighbouring tile, taken by another
-// CTA at about the same time, writes the rest of each sector while it is
-// still in L2.
+// store run per tile is therefore 32 bytes and mostly half sectors (the
+// neighbouring tile, taken by another CTA at about the same time, writes the
+// rest of each sector while it is still in L2); these stores set the pace.
+// For pools over 64 MB the returned values are not stored beside the pool but
+// copied from the new pool after the pass by a streaming kernel
+// (t8_return_kernel, float4 where the output allows).
 //
 // Pipeline as in the n = 4 kernel: one persistent CTA per SM, tiles handed
 // out from the generator's counter; producer threads each own up to T8_KS
@@ -38,7 +41,7 @@
 #define T8_MAXSPANS 300           /* sum of 315 / alpha over the eight smallest candidates */
 #define T8_SPAN_PAD 8             /* slot words past 8 alpha: alignment lead and a wrap's rounding */
 #define T8_CONS_WARPS 20          /* 15 and 24 time 3% slower */
-#define T8_PROD_WARPS 4           /* 8 time the same: the copies, not their issue, set the pace */
+#define T8_PROD_WARPS 4           /* 8 warps time the same */
 #define T8_KS ((T8_MAXSPANS + 32 * T8_PROD_WARPS - 1) / (32 * T8_PROD_WARPS))
 #define T8_THREADS (32 * (T8_CONS_WARPS + T8_PROD_WARPS))
 #define T8_GROUPS ((T8_L + 3) / 4)   /* consumer items per tile, 4 lanes each */
