@@ -11,6 +11,13 @@ Prints one JSON line.  `value` is returned N(0,1) variates per second over
 all ranks (each rank runs an independent generator, stream id = rank: weak
 scaling, no data-path collective).  `--impl reference` times the plain-C
 oracle of the same workload on the host cores instead.
+
+On one GPU the line also carries, measured after the timed region, the other
+configurations against the plain pass: `batched` (4096 generators in one
+launch, every generator checked against its own oracle run), `serve` (the
+continuous-batching server under Poisson arrivals: served against offered
+values/s, p50/p99), `n8` (A = J/4 - I on the same 2^26-value pool) and
+`precision` (binary32 against binary64 pools, 1000 passes).
 """
 from __future__ import annotations
 
@@ -37,6 +44,7 @@ BYTES_PER_PASS = 8 * NU + 4 * R          # pool read + pool write + returned out
 WORKLOAD = (f"Wallace pass, n=4, N=2^24 (2^26-value FP32 pool), A=J/2-I, seed {SEED}, "
             f"frac=1/2 (R=2^25 returned per pass, mu=0 sigma=1, written to HBM)")
 PROFILE = os.path.join(ROOT, "profiles", "wl_tma_pass_n4_N2p24.txt")
+CLOCK_WINDOW_S = 1.5
 KERNEL_SOURCES = ["paper_1004_3114_gb300/csrc/wl_tiled_tma.cu", "paper_1004_3114_gb300/csrc/wl_common.cuh",
                   "paper_1004_3114_gb300/csrc/wl_tma_common.cuh"]
 
@@ -335,7 +343,12 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # nvidia-smi samples every 200 ms, longer than the timed region at small
+    # K: the sampler runs over a window that opens with the timed region and
+    # continues with the same back-to-back passes (untimed) until it has
+    # lasted CLOCK_WINDOW_S seconds
     with ClockSampler(local_rank) as clocks:
+        t_open = time.perf_counter()
         with torch.cuda.stream(stream):
             ev0.record(stream)
             for _ in range(args.steps):
@@ -343,10 +356,18 @@ def run_ours(args, rank, world, local_rank):
             ev1.record(stream)
         ev1.synchronize()
         torch.cuda.synchronize()
+        st1 = g.stats()
+        window_passes = 0
+        while time.perf_counter() - t_open < CLOCK_WINDOW_S:
+            with torch.cuda.stream(stream):
+                for _ in range(200):
+                    g.fill(out)
+            window_passes += 200
+            stream.synchronize()
+        window_s = time.perf_counter() - t_open
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1)
-    st1 = g.stats()
     launches = st1.launches - st0.launches
     if launches != args.steps:
         raise SystemExit(f"expected one pass kernel per step, saw {launches} launches in {args.steps} steps")
@@ -421,7 +442,8 @@ def run_ours(args, rank, world, local_rank):
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * R,
                     "call": f"one wallace_fill_host of {e2e_steps} steps' values into pinned host memory"},
             "gpu_launches": int(launches),
-            "clocks": clocks.summary(),
+            "clocks": dict(clocks.summary(), window_s=window_s, window_passes=args.steps + window_passes,
+                           window="the timed region, then the same back-to-back passes untimed"),
             "status": int(status),
         }
         if cmp:
@@ -434,6 +456,19 @@ def run_ours(args, rank, world, local_rank):
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"{args.cpu_passes} oracle passes of the same "
                                               f"workload ({dt:.1f} s, creation excluded)"}
+        if world == 1 and not args.no_extras:
+            # the other configurations, each against the plain pass above
+            # (outside the timed region; one GPU)
+            plain = value
+            b = batched_bench(tune_cache=args.tune_cache, cpu_baseline=not args.no_cpu_baseline)
+            b["vs_plain_pass"] = b["value"] / plain
+            line["batched"] = b
+            torch.cuda.empty_cache()
+            sv = serve_bench(cpu_baseline=not args.no_cpu_baseline)
+            sv["vs_plain_pass"] = sv["value"] / plain
+            line["serve"] = sv
+            line["n8"] = n8_bench()
+            line["precision"] = precision_study()
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -467,7 +502,57 @@ def precision_study(passes: int = 1000, N: int = 1 << 22, seed: int = 3):
             "status": [int(g32.sync()), int(g64.sync())]})
         g32.close()
         g64.close()
-    print(json.dumps(res), flush=True)
+    return res
+
+
+def n8_bench(steps: int = 2000, warmup: int = 5, N: int = 1 << 23, frac: float = 0.5) -> dict:
+    """n = 8 (A = J/4 - I) on the same 2^26-value pool as the default line
+    (N = 2^23, seed 7, frac = 1/2): `steps` back-to-back passes, one step =
+    one pass (the 315-lane bulk-copy kernel, plus the returned values'
+    streaming kernel for pools over 64 MB).  First, one pass is compared with
+    the oracle element by element (returned values and pool)."""
+    import numpy as np
+    import torch
+    from oracle import py_oracle as orc
+    from paper_1004_3114_gb300 import wallace as W
+    n = 8
+    stream = torch.cuda.Stream()
+    g = W.Wallace(n, N, SEED, frac, stream=stream)
+    o = orc.Generator(n, N, SEED, frac)
+    out = torch.empty(g.R, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        g.fill(out)
+    got = out.cpu().numpy()
+    ref = o.fill(g.R)
+    parity = bool(np.array_equal(got.view(np.uint32), ref.view(np.uint32)) and
+                  np.array_equal(g.pool().view(np.uint32), o.pool32().view(np.uint32)))
+    o.close()
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            g.fill(out)
+    g.sync()
+    s0 = g.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            g.fill(out)
+        e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    s1 = g.stats()
+    status = g.sync()
+    peak, kind = hbm_peak()
+    bytes_pass = 8 * n * N + 4 * g.R
+    achieved = bytes_pass * steps / (ms * 1e-3) / 1e9
+    res = {"metric": "n = 8 pass: N(0,1) variates/s", "value": steps * g.R / (ms * 1e-3), "unit": UNIT,
+           "workload": f"n=8, N=2^{N.bit_length() - 1}, A=J/4-I, seed {SEED}, frac={frac}",
+           "ms_per_pass": ms / steps, "steps": steps, "launches_per_pass": (s1.launches - s0.launches) / steps,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes_per_pass": bytes_pass},
+           "parity_first_pass": parity, "status": int(status)}
+    g.close()
+    return res
 
 
 def small_config_bench(passes: int = 1000, reps: int = 20):
@@ -657,27 +742,42 @@ def oracle_skip(g, count: int, chunk: int = 1 << 22):
         count -= k
 
 
-def batched_sampled_parity(Ns, seeds, sample, skip_passes, check_passes, got_out, got_pools, Rs):
-    """Generators `sample` of the batch: their last `check_passes` passes'
-    returned values (got_out[s], mu = 0, sigma = 1) and final pools
-    (got_pools[s]) against the oracle advanced by `skip_passes` passes first."""
+def batched_full_parity(b, Ns, seeds, passes: int, out, passes_in_out: int):
+    """Every generator of the batch against its own oracle run: after
+    `passes` passes, the returned values of the last pass (mu = 0, sigma = 1;
+    the last of the `passes_in_out` passes held in `out`), the final pool, Q,
+    S, c, the pass count and the uniform state.  Oracle runs on all host
+    threads, largest pools first."""
     import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
     from oracle import py_oracle as orc
-    ok = {}
+    t0 = time.perf_counter()
 
-    def job(s):
-        def run():
-            g = orc.Generator(4, int(Ns[s]), int(seeds[s]), 1.0)
-            oracle_skip(g, skip_passes * int(Rs[s]))
-            ref = g.fill(check_passes * int(Rs[s]))
-            ok[s] = bool(np.array_equal(ref.view(np.uint32), got_out[s].view(np.uint32)) and
-                         np.array_equal(g.pool32().view(np.uint32), got_pools[s].view(np.uint32)))
-            g.close()
-        return run
-    oracle_threads([job(s) for s in sample])
-    return {"generators": len(sample), "bit_exact": int(sum(ok.values())),
-            "checked": f"returned values of the last {check_passes} passes and the final pool, "
-                       f"after {skip_passes} passes", "N": [int(Ns[s]) for s in sample]}
+    def check(s, got_out, got_pool, gst):
+        o = orc.Generator(4, int(Ns[s]), int(seeds[s]), 1.0)
+        for _ in range(passes):
+            o.pass_()
+        ref = o.fill(int(b.R[s]))
+        ost = o.stats()
+        ok = (np.array_equal(ref.view(np.uint32), got_out.view(np.uint32))
+              and np.array_equal(o.pool32().view(np.uint32), got_pool.view(np.uint32))
+              and gst.Q == ost.Q and gst.S == ost.S and gst.c == ost.c and gst.c32 == ost.c32
+              and gst.passes == ost.passes == passes and gst.lcg == ost.lcg)
+        o.close()
+        return ok
+
+    threads = os.cpu_count() or 1
+    with ThreadPoolExecutor(threads) as ex:
+        futs = []
+        for s in (int(v) for v in np.argsort(-np.asarray(Ns), kind="stable")):
+            off = b.out_offset(s, passes_in_out) + (passes_in_out - 1) * int(b.R[s])
+            futs.append(ex.submit(check, s, out[off:off + int(b.R[s])].cpu().numpy(), b.pool(s),
+                                  b.stats(s)))
+        good = sum(1 for f in futs if f.result())
+    return {"generators": len(Ns), "bit_exact": int(good), "threads": threads,
+            "seconds": time.perf_counter() - t0,
+            "checked": f"every generator after {passes} passes: returned values of the last pass, "
+                       f"final pool, Q, S, c, pass count and uniform state against its own oracle run"}
 
 
 def serve_sampled_parity(srv, Ns, seeds, tr, k: int = 8, count: int = 1 << 14):
@@ -709,7 +809,8 @@ def serve_sampled_parity(srv, Ns, seeds, tr, k: int = 8, count: int = 1 << 14):
 
 
 def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
-                  power_of_two: bool = False, count: int = 4096):
+                  power_of_two: bool = False, count: int = 4096, tune_cache: str | None = None,
+                  cpu_baseline: bool = True) -> dict:
     """4096 generators, n = 4, N log-uniform on [2^8, 2^18], seeds 0..4095,
     frac = 1: `runs` batched launches of `passes_per_run` passes (autotuned,
     CUDA graph), against the same generators run one after another through
@@ -725,10 +826,8 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
     nu_total = int(4 * Ns.sum())
     R_total = int(b.R.sum())
     bytes_per_pass = 8 * nu_total + 4 * R_total
-    cache = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                         "wallace_batch_tune.jsonl")
     t0 = time.perf_counter()
-    tuning = b.autotune(cache, 2)
+    tuning = b.autotune(tune_cache, 2)
     tune_s = time.perf_counter() - t0
     out = torch.empty(b.out_size(passes_per_run), dtype=torch.float32, device="cuda")
     b.run(1, None)   # warm-up (graph instantiation)
@@ -746,17 +845,10 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
     value = passes * R_total / (ms * 1e-3)
     peak, kind = hbm_peak()
     achieved = passes * bytes_per_pass / (ms * 1e-3) / 1e9
-    # sampled parity: the largest and smallest pools and a spread between
-    order = np.argsort(Ns, kind="stable")
-    sample = sorted(set(int(order[i]) for i in np.linspace(0, len(Ns) - 1, 16).astype(int)))
-    got_out = {s: out[b.out_offset(s, passes_per_run):b.out_offset(s, passes_per_run)
-                      + passes_per_run * int(b.R[s])].cpu().numpy() for s in sample}
-    got_pools = {s: b.pool(s) for s in sample}
-    Rs = b.R.copy()
+    # parity of every generator (1 warm-up pass + the timed passes)
+    parity = batched_full_parity(b, Ns, seeds, 1 + passes, out, passes_per_run)
     b.close()
     del out
-    parity = batched_sampled_parity(Ns, seeds, sample, 1 + passes - passes_per_run, passes_per_run,
-                                    got_out, got_pools, Rs)
     # the same generators, one handle each, one after another
     handles = [W.Wallace(4, int(N), int(sd), 1.0, stream=stream) for N, sd in zip(Ns, seeds)]
     outs = [torch.empty(seq_passes * h.R, dtype=torch.float32, device="cuda") for h in handles]
@@ -772,8 +864,8 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
     seq_value = seq_passes * R_total / (seq_ms * 1e-3)
     for h in handles:
         h.close()
-    cpu = batched_cpu_baseline(Ns, seeds)
-    print(json.dumps({
+    cpu = batched_cpu_baseline(Ns, seeds) if cpu_baseline else None
+    return {
         "metric": "batched generators: N(0,1) variates/s", "value": value, "unit": UNIT,
         "cpu_baseline": cpu,
         "workload": f"{count} generators, n=4, N log-uniform on [2^8, 2^18]"
@@ -786,8 +878,8 @@ def batched_bench(passes_per_run: int = 10, runs: int = 10, seq_passes: int = 2,
                    "autotune_s": tune_s},
         "sequential_handles": {"value": seq_value, "passes": seq_passes, "ms": seq_ms,
                                "launches": "one fill per generator"},
-        "speedup_vs_sequential": value / seq_value, "sampled_parity": parity,
-        "status": int(status)}), flush=True)
+        "speedup_vs_sequential": value / seq_value, "parity": parity,
+        "status": int(status)}
 
 
 def lane_count(N: int) -> int:
@@ -858,7 +950,8 @@ def batched_classes_bench(names=None, pools: int = 1024, passes: int = 10, runs:
 
 
 def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float = 50_000.0,
-                budget_gb: float = 40.0, passes_per_tick: int = 2, ctas_per_sm: int = 0):
+                budget_gb: float = 40.0, passes_per_tick: int = 2, ctas_per_sm: int = 0,
+                cpu_baseline: bool = True) -> dict:
     """Serving loop: n_clients generators (n = 4, N log-uniform on
     [2^10, 2^20], frac = 1/3), Poisson arrivals at `rate`, counts log-uniform
     on [2^10, 2^24], mu ~ U[-10, 10], sigma ~ U[0.1, 10], admitted against a
@@ -884,8 +977,9 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
     bytes_moved = 28 * values        # per returned value at f = 3: 3 x 8 B pool read+write + 4 B out
     parity = serve_sampled_parity(srv, Ns, seeds, tr)
     srv.close()
-    cpu = serve_cpu_baseline(Ns, seeds, tr)
-    print(json.dumps({
+    cpu = serve_cpu_baseline(Ns, seeds, tr) if cpu_baseline else None
+    offered = values / float(tr["arrival_s"][-1])
+    return {
         "metric": "served N(mu, sigma^2) variates/s", "value": values / st.elapsed_s, "unit": UNIT,
         "cpu_baseline": cpu,
         "workload": f"{n_clients} clients, n=4, N log-uniform on [2^10, 2^20], frac=1/3; "
@@ -893,7 +987,7 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
                     f"mu~U[-10,10], sigma~U[0.1,10]; budget {budget_gb} GB",
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "values": values, "elapsed_s": st.elapsed_s, "wall_s": wall,
-        "offered_values_per_s": values / float(tr["arrival_s"][-1]),
+        "offered_values_per_s": offered, "served_over_offered": values / st.elapsed_s / offered,
         "ticks": int(st.ticks), "hbm_peak_gb": st.hbm_peak / 2**30, "hbm_budget_gb": st.hbm_budget / 2**30,
         "roofline": {"bound": "hbm", "achieved": bytes_moved / st.elapsed_s / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": bytes_moved / st.elapsed_s / 1e9 / peak, "peak_kind": kind,
@@ -901,7 +995,7 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
         "passes_per_tick": passes_per_tick, "ctas_per_sm": ctas_per_sm,
         "runner": "bulk-copy for one-CTA requests on 16384 <= N (n=4)" if ctas_per_sm == 0
                   else "async-copy", "create_s": create_s, "sampled_parity": parity,
-        "status": int(st.status)}), flush=True)
+        "status": int(st.status)}
 
 
 def main():
@@ -943,14 +1037,19 @@ def main():
     ap.add_argument("--class-pools", type=int, default=1024)
     ap.add_argument("--class-passes", type=int, default=10)
     ap.add_argument("--class-runs", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line only: skip the batched, serving, n = 8 and precision objects")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON-lines file caching the batched autotuner's choice (default: tune every run)")
     ap.add_argument("--precision-study", action="store_true",
                     help="binary32 vs binary64 pool study (N=2^22, n=4 and 8, 1000 passes) instead of the benchmark")
     args = ap.parse_args()
     if args.precision_study:
-        precision_study()
+        print(json.dumps(precision_study()), flush=True)
         return
     if args.batched:
-        batched_bench(power_of_two=args.pow2, count=args.batched_count, runs=args.batched_runs)
+        print(json.dumps(batched_bench(power_of_two=args.pow2, count=args.batched_count,
+                                       runs=args.batched_runs, tune_cache=args.tune_cache)), flush=True)
         return
     if args.batched_classes:
         batched_classes_bench(args.classes, pools=args.class_pools, passes=args.class_passes,
@@ -966,8 +1065,9 @@ def main():
         variant_bench(steps=args.variants_steps)
         return
     if args.serve:
-        serve_bench(n_requests=args.serve_requests, rate=args.serve_rate,
-                    passes_per_tick=args.serve_ppt, ctas_per_sm=args.serve_ctas)
+        print(json.dumps(serve_bench(n_requests=args.serve_requests, rate=args.serve_rate,
+                                     passes_per_tick=args.serve_ppt, ctas_per_sm=args.serve_ctas)),
+              flush=True)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -428,12 +428,19 @@ int wallace_server_stats(wallace_server_t *s, wallace_server_stats_t *out);
  *               are coprime to N as Eq. 2 requires
  *   c32         scale of this pass (the c32 a previous pass reported)
  *   out         device, receives mu + sigma*y for the first out_count values
- *               of the new pool (0 <= out_count <= n*N; NULL if 0)
+ *               of the new pool (0 <= out_count <= n*N - 1, as a handle's R:
+ *               the last value sets the next scale and is never returned;
+ *               NULL if 0).  Must not overlap `pool`.
  *   result      host; receives Q, q, S and the next pass's c and c32
  *   cuda_stream stream to run on (NULL: legacy default stream)
- * Synchronous: returns after the pass, the copy back into `pool` and the
- * result copy have finished.  Returns WALLACE_OK, WALLACE_EINVAL,
- * WALLACE_ECUDA, or WALLACE_ECORRUPT (bad value, Q = 0 or Q >= 2^64).
+ * The next scale comes from Eq. 3's sample only (no WALLACE_CHI_WH option),
+ * and there is no drift check (Section 8): the caller keeps the previous S.
+ * With the strides and offsets a handle drew, the results equal that
+ * handle's pass when it uses the default chi-squared sample.
+ * Synchronous: every call waits on `cuda_stream` until the pass, the copy
+ * back into `pool` and the result copy have finished.  Returns WALLACE_OK,
+ * WALLACE_EINVAL, WALLACE_ECUDA, or WALLACE_ECORRUPT (bad value, Q = 0 or
+ * Q >= 2^64).
  *
  * The scratch array is shared by every call: calls that overlap on the GPU
  * (in flight at the same time on any streams) race and give wrong results.

@@ -204,9 +204,10 @@ void orc_boxmuller_stream(uint32_t seed, uint32_t stream, int64_t offset, int64_
  * Per-pass parameters (Eq. 1 and Eq. 2; Sections 3, 7 and 8).  The paper asks
  * for strides that are distinct, greater than one, odd, and coprime to N, and
  * offsets uniform on {0..N-1}, all redrawn every pass; RANN4 picks its two
- * strides from {3,5} and {7,11}, and Section 7's vector gather wants strides
- * whose common multiple is small.  Reading for n = 4 and n = 8 (the paper
- * gives only n = 2): with p < q < r the three smallest odd primes that do not
+ * strides from {3,5} and {7,11}.  Reading for n = 4 and n = 8 (the paper
+ * gives only n = 2; this rule is a choice made for the GPU's lane tiling,
+ * whose lane count is the strides' lcm, within those constraints -- the
+ * paper itself asks nothing of the lcm): with p < q < r the three smallest odd primes that do not
  * divide N, the candidate strides are the odd divisors > 1 of p^2 q (n = 4:
  * five values) or of p^2 q r (n = 8: eleven values), in increasing order.
  * Every candidate is then coprime to N and the lcm of any pass's strides

@@ -537,12 +537,15 @@ __device__ __forceinline__ double wl_chi_sample(int chi, int64_t nu, double x)
 // c = sqrt(S / q).  q / S_prev - 1 beyond 1e-3 means the pool was overwritten
 // (Section 8).  Then the next pass's parameters are drawn.
 // kind: what made the pool -- WL_FIN_INIT (creation: the strides of the
-// first two passes are drawn), WL_FIN_PASS (a pass: the strides advance), or
+// first two passes are drawn), WL_FIN_PASS (a pass: the strides advance),
 // WL_FIN_RESTART (a Box-Muller refill, Section 5: the drift history restarts,
-// the strides and the pass count are untouched).
+// the strides and the pass count are untouched), or WL_FIN_SCALE (a pass whose
+// caller holds the parameters: only Q, S and the next scale c are computed --
+// no drift check, no stride draw).
 #define WL_FIN_INIT 0
 #define WL_FIN_PASS 1
 #define WL_FIN_RESTART 2
+#define WL_FIN_SCALE 3
 // local: st is a CTA's shared-memory copy of the state (a run of many passes
 // on one CTA), so no device-scope fence is needed; rnu > 0: sqrt(2 nu - 1)
 // precomputed by the caller (Eq. 3's sample).
@@ -578,8 +581,9 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
         status |= WL_ECORRUPT;
     else
         c = __dsqrt_rn(__ddiv_rn(S, q));
+    const bool params = kind == WL_FIN_INIT || kind == WL_FIN_PASS;
     double drift = 0.0;
-    if (st->have_prev && kind != WL_FIN_RESTART) {
+    if (st->have_prev && params) {
         drift = __dsub_rn(__ddiv_rn(q, st->S_prev), 1.0);
         if (!(fabs(drift) <= 1e-3))
             status |= WL_ECORRUPT;
@@ -594,7 +598,7 @@ __device__ inline void wl_finalise(WlDevState *st, int n, int64_t N, int64_t nu,
     st->drift = drift;
     st->bad = (int32_t)bad;
     st->status = status;
-    if (kind != WL_FIN_RESTART) {
+    if (params) {
         uint64_t s = st->lcg, rep = st->lcg_pend;
         if (kind == WL_FIN_PASS) {
             st->last = st->next;

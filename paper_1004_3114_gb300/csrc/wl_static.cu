@@ -15,6 +15,11 @@
 // streams, race on it).  The first call on each device looks up the array's
 // device address (cudaGetSymbolAddress) with that device current; make that
 // first call before any stream capture begins.
+//
+// The pass computes the next scale from the fixed Eq. 3 sample only: there is
+// no Wilson-Hilferty option, and no drift check (the caller, who holds the
+// pool between calls, holds the previous chi-squared target too).  Like a
+// handle, it never returns the new pool's last value, which sets that scale.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -85,7 +90,7 @@ __global__ void __launch_bounds__(256) static_gather_kernel(const float *__restr
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st) && threadIdx.x == 0) {
         double x = (double)__ldcg(&dst[nu - 1]);
-        wl_finalise(st, NSUB, N, nu, x, false, WL_FIN_INIT);
+        wl_finalise(st, NSUB, N, nu, x, false, WL_FIN_SCALE);
     }
 }
 
@@ -121,7 +126,8 @@ extern "C" int wallace_pass_static(int n, int64_t N, float *pool, const int32_t 
     const int64_t nu = (int64_t)n * N;
     if (nu > (int64_t)WALLACE_STATIC_MAX_VALUES)
         return WALLACE_EINVAL;   // beyond the fixed scratch array
-    if (out_count < 0 || out_count > nu || (out_count > 0 && !out))
+    // the last value is withheld (Section 4): it sets the next pass's scale
+    if (out_count < 0 || out_count > nu - 1 || (out_count > 0 && !out))
         return WALLACE_EINVAL;
     WlParams prm = {};
     for (int i = 0; i < n; i++) {

@@ -307,17 +307,47 @@ def _device_floats(ptr: int, count: int):
     return torch.as_tensor(_View(), device="cuda")
 
 
-def pass_static(n: int, N: int, pool, alpha, gamma, c32: float, out=None, out_count: int = 0,
+def _check_dev_f32(t, name: str, min_numel: int) -> None:
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name} holds {t.numel()} values, needs {min_numel}")
+
+
+def pass_static(n: int, N: int, pool, alpha, gamma, c32: float, out=None, out_count: int | None = None,
                 mu: float = 0.0, sigma: float = 1.0, stream=None) -> tuple[int, PassResult]:
     """wallace_pass_static: one pass on a caller-held pool (CUDA float32 tensor of
     n*N values, rows of N), using the library's fixed scratch array; returns
-    (status, result)."""
-    a = (C.c_int32 * 8)(*[int(v) for v in alpha])
-    g = (C.c_int64 * 8)(*[int(v) for v in gamma])
+    (status, result).  out_count defaults to out.numel() (0 without `out`).
+    The C call cannot see the tensors' sizes, so they are checked here; a pool
+    beyond the scratch array's limit is passed through for the library to
+    reject."""
+    if len(alpha) < n or len(gamma) < n:
+        raise ValueError(f"need {n} strides and offsets")
+    if out_count is None:
+        out_count = out.numel() if out is not None else 0
+    if n * N <= STATIC_MAX_VALUES:
+        _check_dev_f32(pool, "pool", n * N)
+        if pool.numel() != n * N:
+            raise ValueError(f"pool holds {pool.numel()} values, expected n*N = {n * N}")
+    if out_count > 0:
+        if out is None:
+            raise ValueError("out_count > 0 needs an output tensor")
+        _check_dev_f32(out, "out", out_count)
+        if out.device != pool.device:
+            raise ValueError("out and pool must be on the same device")
+        p0, p1 = pool.data_ptr(), pool.data_ptr() + 4 * pool.numel()
+        o0, o1 = out.data_ptr(), out.data_ptr() + 4 * out_count
+        if o0 < p1 and p0 < o1:
+            raise ValueError("out overlaps pool: the pass reads the pool while it writes out")
+    a = (C.c_int32 * 8)(*[int(v) for v in alpha[:n]])
+    g = (C.c_int64 * 8)(*[int(v) for v in gamma[:n]])
     res = PassResult()
     rc = _lib.wallace_pass_static(n, N, C.c_void_p(pool.data_ptr()), a, g, c32,
-                                  C.c_void_p(out.data_ptr() if out is not None else 0), out_count,
-                                  mu, sigma, C.byref(res), _stream_ptr(stream))
+                                  C.c_void_p(out.data_ptr() if out is not None and out_count > 0 else 0),
+                                  out_count, mu, sigma, C.byref(res), _stream_ptr(stream))
     return int(rc), res
 
 

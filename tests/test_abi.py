@@ -52,3 +52,16 @@ def test_product_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower() or f == "__init__.py", f
+
+
+def test_static_pass_binding_checks_tensors_before_the_call(libpath):
+    """The C entry point cannot see a tensor's size or device, so the binding
+    rejects a CPU, wrongly typed or undersized pool before calling it."""
+    torch = pytest.importorskip("torch")
+    from paper_1004_3114_gb300 import wallace as W
+    n, N = 4, 256
+    for bad in (torch.zeros(n * N), torch.zeros(n * N, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            W.pass_static(n, N, bad, [3, 5, 9, 45], [0, 0, 0, 0], 1.0)
+    with pytest.raises(ValueError):
+        W.pass_static(n, N, torch.zeros(n * N), [3, 5, 9], [0, 0, 0], 1.0)   # too few strides

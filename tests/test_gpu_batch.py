@@ -104,3 +104,48 @@ def test_batch_without_output_and_autotune_does_not_advance(orc):
         o.pass_()
         o.pass_()
         assert np.array_equal(b.pool(s).view(np.uint32), o.pool32().view(np.uint32))
+
+
+def test_config4_all_4096_generators_against_oracle(orc):
+    """The batched configuration in full: 4096 generators, n = 4, N
+    log-uniform on [2^8, 2^18] (seeded shapes), seeds 0..4095, frac = 1,
+    100 passes in one autotuned launch per run (99 passes discarding their
+    values, then one pass writing them).  Every generator is checked against
+    its own oracle run of the same 100 passes: the returned values of pass
+    100, the final pool, Q, S, c, the pass count and the uniform state.  The
+    oracle runs go on all host threads (its C calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1004_3114_gb300.workloads import batch_sizes
+    Ns = batch_sizes()
+    seeds = np.arange(Ns.size, dtype=np.uint32)
+    b = W.Batch(4, Ns, seeds, 1.0)
+    b.autotune(None, 2)
+    b.run(99, None)
+    out = torch.empty(b.out_size(1), dtype=torch.float32, device="cuda")
+    b.run(1, out)
+    assert b.sync() == 0
+    P = 100
+
+    def check(s, got_out, got_pool, gst):
+        o = orc.Generator(4, int(Ns[s]), int(seeds[s]), 1.0)
+        for _ in range(P):
+            o.pass_()
+        ref = o.fill(int(b.R[s]))          # the current (100th) pool's returned values
+        ost = o.stats()
+        ok = (np.array_equal(ref.view(np.uint32), got_out.view(np.uint32))
+              and np.array_equal(o.pool32().view(np.uint32), got_pool.view(np.uint32))
+              and gst.Q == ost.Q and gst.S == ost.S and gst.c == ost.c and gst.c32 == ost.c32
+              and gst.passes == ost.passes == P and gst.lcg == ost.lcg)
+        o.close()
+        return s, ok
+
+    order = np.argsort(-Ns, kind="stable")      # largest pools first: balanced threads
+    with ThreadPoolExecutor() as ex:
+        futs = []
+        for s in (int(v) for v in order):
+            off = b.out_offset(s, 1)
+            got_out = out[off:off + int(b.R[s])].cpu().numpy()
+            futs.append(ex.submit(check, s, got_out, b.pool(s), b.stats(s)))
+        bad = [s for s, ok in (f.result() for f in futs) if not ok]
+    assert not bad, f"{len(bad)} of {Ns.size} generators differ, e.g. N = {[int(Ns[s]) for s in bad[:8]]}"
+    b.close()

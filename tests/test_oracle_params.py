@@ -106,7 +106,7 @@ def test_candidates_reduce_to_fixed_tables(orc):
 
 def test_strides_for_n_divisible_by_3_are_ordered_choices(orc):
     """N = 3 * 4096: candidates {5, 7, 25, 35, 175}; every ordered choice of 4
-    is equally likely and the lcm divides 175 (small for the tiled gather)."""
+    is equally likely and the lcm divides 175 (the tiled gather's lane count)."""
     import itertools
     N = 3 * 4096
     cand = (5, 7, 25, 35, 175)
