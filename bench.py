@@ -731,6 +731,59 @@ def variant_bench(steps: int = 2000, warmup: int = 5):
                       "peak_kind": kind, "steps": steps, "cases": res}), flush=True)
 
 
+def l2_bench(log2_sizes=range(14, 22), frac: float = 0.5, target_ms: float = 150.0,
+             grids=(0,), n: int = 4) -> dict:
+    """Pools that stay in L2 between passes (n = 4 or 8, nu = 4 2^k, seed 7): the
+    multi-pass kernel (every pass of a fill in one cooperative launch)
+    against one launch per pass (the single-generator path AUTO picks
+    otherwise), each timed over one fill of about `target_ms` of passes.
+    Rates are in algorithmic bytes (8 nu + 4 R per pass): an "equivalent"
+    fraction of the HBM peak, since the pool stays on chip."""
+    import torch
+    from paper_1004_3114_gb300 import wallace as W
+    peak, kind = hbm_peak()
+    stream = torch.cuda.Stream()
+    res = {}
+
+    def timed(g, passes):
+        out = torch.empty(passes * g.R, dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(stream):
+            g.fill(out[: 3 * g.R])          # warm-up
+        g.sync()
+        s0 = g.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            g.fill(out)
+            e1.record(stream)
+        e1.synchronize()
+        s1 = g.stats()
+        return e0.elapsed_time(e1) / passes, s1.launches - s0.launches, int(g.sync())
+
+    for k in log2_sizes:
+        N = (1 << k) * 4 // n
+        nu = n * N
+        g = W.Wallace(n, N, SEED, frac, stream=stream)
+        byt = 8 * nu + 4 * g.R
+        # passes for about target_ms at a first estimate of 10 B per ns
+        passes = int(max(200, min(20000, target_ms * 1e6 / max(byt / 10.0, 2000.0))))
+        row = {"nu": nu, "passes": passes}
+        ms, launches, st = timed(g, passes)
+        row["per_pass_launch"] = {"ms_per_pass": ms, "launches": launches, "status": st,
+                                  "equiv_frac": byt / (ms * 1e-3) / 1e9 / peak}
+        for grid in grids:
+            g.set_variant(W.VARIANT_L2RUN)
+            g.set_l2_grid(grid)
+            ms2, launches2, st2 = timed(g, passes)
+            row[f"l2run_grid{grid}"] = {
+                "ms_per_pass": ms2, "launches": launches2, "status": st2,
+                "equiv_frac": byt / (ms2 * 1e-3) / 1e9 / peak, "speedup": ms / ms2}
+        g.close()
+        res[f"nu=2^{k + 2}"] = row
+    return {"metric": "multi-pass L2 kernel vs one launch per pass: ms per pass", "n": n, "frac": frac,
+            "peak_gbs": peak, "peak_kind": kind, "sizes": res}
+
+
 def oracle_skip(g, count: int, chunk: int = 1 << 22):
     """Advance an oracle generator's output stream by `count` values."""
     import numpy as np
@@ -1037,6 +1090,11 @@ def main():
     ap.add_argument("--class-pools", type=int, default=1024)
     ap.add_argument("--class-passes", type=int, default=10)
     ap.add_argument("--class-runs", type=int, default=3)
+    ap.add_argument("--l2", action="store_true",
+                    help="multi-pass L2 kernel against one launch per pass, N = 2^14..2^22")
+    ap.add_argument("--l2-grids", default="0",
+                    help="with --l2: comma-separated grid sizes (0: two CTAs per SM)")
+    ap.add_argument("--l2-n", type=int, default=4, help="with --l2: sub-vectors (4 or 8)")
     ap.add_argument("--no-extras", action="store_true",
                     help="default line only: skip the batched, serving, n = 8 and precision objects")
     ap.add_argument("--tune-cache", default=None,
@@ -1046,6 +1104,10 @@ def main():
     args = ap.parse_args()
     if args.precision_study:
         print(json.dumps(precision_study()), flush=True)
+        return
+    if args.l2:
+        grids = tuple(int(v) for v in args.l2_grids.split(","))
+        print(json.dumps(l2_bench(grids=grids, n=args.l2_n)), flush=True)
         return
     if args.batched:
         print(json.dumps(batched_bench(power_of_two=args.pow2, count=args.batched_count,

@@ -69,7 +69,10 @@ typedef struct wallace wallace_t;
 #define WALLACE_MATRIX_SIGNS 0x200
 
 /* pass kernel selection (wallace_set_variant) */
-#define WALLACE_VARIANT_AUTO    0  /* pick by pool size                                 */
+#define WALLACE_VARIANT_AUTO    0  /* pick by pool size: whole pool in shared memory when
+                                      it fits; else binary32 pools (n = 4, 8) of at most
+                                      2^22 values take WALLACE_VARIANT_L2RUN; else the
+                                      lane-tiled (or two-phase) pass, one per launch     */
 #define WALLACE_VARIANT_GATHER  1  /* direct strided gather from HBM, one pass/launch   */
 #define WALLACE_VARIANT_TILED   2  /* lane-tiled gather staged in shared memory: the
                                       bulk-copy (TMA) pipeline when N % 4 == 0 and
@@ -92,6 +95,16 @@ typedef struct wallace wallace_t;
                                          launches per pass; a third pool-sized buffer
                                          held from creation when every stride N can
                                          draw is at most 16384)                       */
+
+#define WALLACE_VARIANT_L2RUN       7 /* binary32 pools of at most 2^23 values (n = 4 or
+                                         8; (alpha + 1) N < 2^32 for every stride the
+                                         pool can draw): every pass of a fill in ONE
+                                         cooperative launch (up to 2^20 passes), each
+                                         thread gathering its tuples straight from L2,
+                                         CTAs meeting at a grid barrier after each pass,
+                                         where each CTA runs the end of pass (Eq. 3)
+                                         itself; for pools that stay in L2 between
+                                         passes                                        */
 
 /* Scalars of the most recent pass (or of the initial pool after create). */
 typedef struct {
@@ -202,6 +215,14 @@ int wallace_set_variant(wallace_t *h, int variant);
  * Returns WALLACE_OK or WALLACE_EINVAL (NULL handle, interval < 0).
  */
 int wallace_set_restart(wallace_t *h, int64_t interval);
+
+/*
+ * wallace_set_l2_grid -- CTAs of WALLACE_VARIANT_L2RUN's launch (not part of
+ * the paper's method): 0 (the default) is two per SM; larger values are
+ * capped at what the device can keep resident.  Results do not depend on it.
+ * Returns WALLACE_OK or WALLACE_EINVAL (NULL handle, grid < 0).
+ */
+int wallace_set_l2_grid(wallace_t *h, int grid);
 
 /* wallace_set_timing -- when on, every pass kernel is bracketed by CUDA
  * events on the handle's stream; the summed time appears in kernel_ms. */

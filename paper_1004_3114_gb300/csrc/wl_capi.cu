@@ -22,6 +22,8 @@ struct wallace {
     cudaStream_t stream = nullptr;
     void *pool[2] = {nullptr, nullptr};
     void *scratch = nullptr;      // the two-phase pass's j-ordered copy (n = 8, binary64 pools)
+    void *l2sync = nullptr;       // barrier and accumulators of the multi-pass L2 kernel
+    int l2_grid = 0;              // its CTAs (0: two per SM)
     int cur = 0;
     int64_t pass_index = 0;   // passes launched (selects a pass's strides slot)
     uint32_t seed = 0, stream_id = 0;
@@ -111,6 +113,10 @@ int pick_variant(const wallace_t *h)
     if (h->variant != WALLACE_VARIANT_AUTO)
         return h->variant;
     const int fp64 = h->mode == WALLACE_FP64POOL;
+    // pools too large for shared memory but small enough to stay in L2:
+    // every pass of a fill in one launch
+    if (h->l2sync && h->nu <= WL_L2RUN_AUTO_MAX_VALUES && !wl_fused_supported(h->n, h->N, fp64, nullptr))
+        return WALLACE_VARIANT_L2RUN;
     if (wl_tma8_supported(h->n, h->N, fp64) && !wl_fused_supported(h->n, h->N, fp64, nullptr))
         return WALLACE_VARIANT_TILED;
     // a handle with the two-phase buffer has strides the tiled kernels cannot
@@ -159,6 +165,11 @@ cudaError_t maybe_restart(wallace_t *h)
                              h->sm_count, h->stream);
 }
 
+int l2_grid(const wallace_t *h)
+{
+    return h->l2_grid > 0 ? h->l2_grid : wl_l2run_grid(h->nu, h->sm_count);
+}
+
 int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, double sigma)
 {
     const int fp64 = h->mode == WALLACE_FP64POOL;
@@ -166,6 +177,15 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
     cudaError_t e = maybe_restart(h);
     if (e != cudaSuccess)
         return cuda_fail(h, e);
+    if (v == WALLACE_VARIANT_L2RUN) {
+        KernelTimer t(h);
+        // one pass of the multi-pass kernel: output window is a prefix
+        e = wl_launch_l2run(h->pool[0], h->pool[1], h->cur, h->n, h->N, h->Np, h->st, h->l2sync, 1, h->R,
+                            w1 - w0, out, mu, sigma, l2_grid(h), h->msigns, h->stream);
+        h->pass_index += 1;
+        h->cur = 1 - h->cur;
+        return cuda_fail(h, e);
+    }
     if (v == WALLACE_VARIANT_FUSED) {
         KernelTimer t(h);
         // a single fused pass: output window must start at 0 (a prefix)
@@ -239,6 +259,32 @@ int fill_impl(wallace_t *h, void *out, int64_t count, double mu, double sigma)
     if (done >= count)
         return WALLACE_OK;
     int64_t remaining = count - done;
+    if (pick_variant(h) == WALLACE_VARIANT_L2RUN && h->restart == 0) {
+        // all remaining passes in cooperative launches of up to 2^20 passes
+        int64_t passes = (remaining + h->R - 1) / h->R;
+        while (passes > 0) {
+            const int64_t P = passes < ((int64_t)1 << 20) ? passes : ((int64_t)1 << 20);
+            const int64_t take_last = P < passes ? h->R : remaining - (passes - 1) * h->R;
+            cudaError_t e;
+            {
+                KernelTimer t(h);
+                e = wl_launch_l2run(h->pool[0], h->pool[1], h->cur, h->n, h->N, h->Np, h->st, h->l2sync, P,
+                                    h->R, take_last, o + done * es, mu, sigma, l2_grid(h), h->msigns,
+                                    h->stream);
+            }
+            if (e != cudaSuccess)
+                return cuda_fail(h, e);
+            h->pass_index += P;
+            if (P & 1)
+                h->cur = 1 - h->cur;
+            const int64_t got = (P - 1) * h->R + take_last;
+            done += got;
+            remaining -= got;
+            passes -= P;
+            h->cursor = take_last;
+        }
+        return WALLACE_OK;
+    }
     if (pick_variant(h) == WALLACE_VARIANT_FUSED && h->restart == 0) {
         // all remaining passes in one launch (pass by pass when refills are due)
         int64_t passes = (remaining + h->R - 1) / h->R;
@@ -358,6 +404,11 @@ int wallace_create_ex(int n, int64_t N, uint32_t seed, uint32_t stream_id, doubl
         wallace_destroy(h);
         return WALLACE_ENOMEM;
     }
+    if (wl_l2run_supported(n, N, mode == WALLACE_FP64POOL, max_stride(n, N)) &&
+        cudaMalloc(&h->l2sync, wl_l2run_sync_bytes()) != cudaSuccess) {
+        wallace_destroy(h);
+        return WALLACE_ENOMEM;
+    }
     e = cudaMemsetAsync(h->pool[0], 0, bytes, h->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(h->pool[1], 0, bytes, h->stream);
@@ -387,6 +438,7 @@ void wallace_destroy(wallace_t *h)
     if (h->copy_stream)
         cudaStreamSynchronize(h->copy_stream);
     cudaFree(h->scratch);
+    cudaFree(h->l2sync);
     for (int b = 0; b < 2; b++) {
         cudaFree(h->pool[b]);
         cudaFree(h->stage[b]);
@@ -536,10 +588,22 @@ int wallace_set_variant(wallace_t *h, int variant)
         if (!wl_fused_supported(h->n, h->N, fp64, nullptr))
             return WALLACE_EINVAL;
         break;
+    case WALLACE_VARIANT_L2RUN:
+        if (!h->l2sync)
+            return WALLACE_EINVAL;
+        break;
     default:
         return WALLACE_EINVAL;
     }
     h->variant = variant;
+    return WALLACE_OK;
+}
+
+int wallace_set_l2_grid(wallace_t *h, int grid)
+{
+    if (check(h) || grid < 0)
+        return WALLACE_EINVAL;
+    h->l2_grid = grid;
     return WALLACE_OK;
 }
 

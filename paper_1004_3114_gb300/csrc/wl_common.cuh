@@ -124,8 +124,19 @@ __device__ __forceinline__ uint64_t wl_lcg_jump(uint64_t s, uint64_t m)
 // (Section 8): alpha from {3, 5} for x and beta from {7, 11} for y, those
 // coprime to N; with none free, the smallest free odd number > 1 coprime to
 // N.  The offset is floor(U N / 2^32), uniform on {0..N-1}.
+// (32-bit remainders when both fit: a 64-bit remainder costs several hundred
+// cycles on this part, a 32-bit one a few dozen)
 __device__ __forceinline__ int64_t wl_gcd(int64_t a, int64_t b)
 {
+    if (((uint64_t)a | (uint64_t)b) >> 32 == 0) {
+        uint32_t x = (uint32_t)a, y = (uint32_t)b;
+        while (y) {
+            const uint32_t t = x % y;
+            x = y;
+            y = t;
+        }
+        return (int64_t)x;
+    }
     while (b) {
         int64_t t = a % b;
         a = b;
@@ -722,6 +733,69 @@ __device__ inline void wl_finalise_par(WlDevState *st, int n, int64_t N, int64_t
     }
 }
 
+// One of the three independent chains of a pass's end, run by one thread
+// each, on a state no other thread writes meanwhile:
+//   role 0 -- the scale: q from the pass's exact sum of squares (lo, hi, bad
+//             totals), S from the withheld value x (Eq. 3, or the Wilson-
+//             Hilferty sample), c = sqrt(S / q), and the next pass's c32;
+//   role 1 -- the pass count and the strides: `next` takes the next pass's
+//             strides and the pass after it draws its own;
+//   role 2 -- the drift q / S_prev - 1 (Section 8), then S_prev = S.
+// Roles 0 and 2 write disjoint fields and add corruption flags atomically.
+// The caller copies st->last = st->next at the start of the pass (nothing
+// writes `next` during it); for n = 2 the rotation with the scale folded in
+// is left to wl_fold_rotation after the three.
+__device__ inline void wl_end_pass_role(WlDevState *st, int n, int64_t N, int64_t nu, double rnu, uint64_t lo,
+                                        uint64_t hi, uint32_t bad, double x, int role, int msigns, bool fp64)
+{
+    if (role == 1) {
+        st->passes += 1;
+        wl_advance_strides(st, n, N, st->lcg, st->lcg_pend, msigns);
+        return;
+    }
+    if (!fp64 && hi != 0)
+        bad = 1u;
+    const double q = fp64 ? __dadd_rn(__ull2double_rn(hi),
+                                      __dmul_rn(__ull2double_rn(lo), 1.0 / 18446744073709551616.0))
+                          : __dmul_rn(__ull2double_rn(lo), 1.0 / 4294967296.0);
+    const int chi = st->chi;
+    double S;
+    if (!chi && rnu > 0.0) {
+        const double xr = __dadd_rn(x, rnu);
+        S = __dmul_rn(__dmul_rn(xr, xr), 0.5);
+    } else {
+        S = wl_chi_sample(chi, nu, x);
+    }
+    int32_t f = 0;
+    if (role == 0) {
+        double c = 1.0;
+        if (bad || (chi && !(S > 0.0)) || !(q > 0.0))
+            f = WL_ECORRUPT;
+        else
+            c = __dsqrt_rn(__ddiv_rn(S, q));
+        st->q_lo = lo;
+        st->q_hi = hi;
+        st->q = q;
+        st->S = S;
+        st->c = c;
+        st->bad = (int32_t)bad;
+        st->next.c64 = c;
+        st->next.c32 = __double2float_rn(c);
+    } else {
+        double drift = 0.0;
+        if (st->have_prev) {
+            drift = __dsub_rn(__ddiv_rn(q, st->S_prev), 1.0);
+            if (!(fabs(drift) <= 1e-3))
+                f = WL_ECORRUPT;
+        }
+        st->drift = drift;
+        st->S_prev = S;
+        st->have_prev = 1;
+    }
+    if (f)
+        atomicOr(&st->status, f);
+}
+
 // End of a pass that one CTA ran over the whole pool (the CTA's sum is Q):
 // the same update as wl_finalise_par with two barriers.  Per-warp partial
 // sums go to `red` (3 words per warp); warps 0 and 2 each complete Q and S
@@ -763,53 +837,10 @@ __device__ inline void wl_end_pass_cta(WlDevState *st, int n, int64_t N, int64_t
             wl_add128(lo, hi, olo, ohi);
         }
         bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
-        if (lane == 0) {
-            if (!fp64 && hi != 0)
-                bad = 1u;
-            const double q = fp64 ? __dadd_rn(__ull2double_rn(hi),
-                                              __dmul_rn(__ull2double_rn(lo), 1.0 / 18446744073709551616.0))
-                                  : __dmul_rn(__ull2double_rn(lo), 1.0 / 4294967296.0);
-            const int chi = st->chi;
-            const double x = xf();
-            double S;
-            if (!chi && rnu > 0.0) {
-                const double xr = __dadd_rn(x, rnu);
-                S = __dmul_rn(__dmul_rn(xr, xr), 0.5);
-            } else {
-                S = wl_chi_sample(chi, nu, x);
-            }
-            int32_t f = 0;
-            if (warp == 0) {
-                double c = 1.0;
-                if (bad || (chi && !(S > 0.0)) || !(q > 0.0))
-                    f = WL_ECORRUPT;
-                else
-                    c = __dsqrt_rn(__ddiv_rn(S, q));
-                st->q_lo = lo;
-                st->q_hi = hi;
-                st->q = q;
-                st->S = S;
-                st->c = c;
-                st->bad = (int32_t)bad;
-                st->next.c64 = c;
-                st->next.c32 = __double2float_rn(c);
-            } else {
-                double drift = 0.0;
-                if (st->have_prev) {
-                    drift = __dsub_rn(__ddiv_rn(q, st->S_prev), 1.0);
-                    if (!(fabs(drift) <= 1e-3))
-                        f = WL_ECORRUPT;
-                }
-                st->drift = drift;
-                st->S_prev = S;
-                st->have_prev = 1;
-            }
-            if (f)
-                atomicOr(&st->status, f);
-        }
+        if (lane == 0)
+            wl_end_pass_role(st, n, N, nu, rnu, lo, hi, bad, xf(), warp, msigns, fp64);
     } else if (warp == 1 && lane == 0) {
-        st->passes += 1;
-        wl_advance_strides(st, n, N, st->lcg, st->lcg_pend, msigns);
+        wl_end_pass_role(st, n, N, nu, rnu, 0, 0, 0, 0.0, 1, msigns, fp64);
     }
     __syncthreads();
 }
@@ -879,9 +910,16 @@ __device__ __forceinline__ bool wl_last_cta(WlDevState *st)
     return s_last;
 }
 
-// physical offset of logical pool index q (sub-vector-major, row pitch Np)
+// physical offset of logical pool index q (sub-vector-major, row pitch Np);
+// pools hold at most 2^30 values, so the division is a 32-bit one
 __device__ __forceinline__ int64_t wl_phys(int64_t q, int64_t N, int64_t Np)
 {
-    int64_t i = q / N;
-    return i * Np + (q - i * N);
+    const uint32_t i = (uint32_t)q / (uint32_t)N;
+    return (int64_t)i * Np + (q - (int64_t)i * N);
+}
+
+// physical offset of the pool's last value (the value Eq. 3 withholds)
+__device__ __forceinline__ int64_t wl_last_phys(int n, int64_t N, int64_t Np)
+{
+    return (int64_t)(n - 1) * Np + (N - 1);
 }

@@ -1,0 +1,316 @@
+// Many passes of one generator in ONE launch, for pools that stay in L2
+// between passes (Section 2: a pass is a few vector operations over the pool;
+// for pools of a few MB the fixed cost of a launch and of the end-of-pass
+// round trip is most of a pass).
+//
+// A cooperative grid of G CTAs (all resident) runs P passes.  In pass p each
+// thread takes tuples j = t, t + T, ... (t its index in the grid, T the
+// grid's thread count) and gathers g_i[j] = x_i[(alpha_i j + gamma_i) mod N]
+// straight from L2 (loads that bypass L1: the previous pass's pool was
+// written by other SMs), transforms, stores the new pool and the returned
+// prefix with unit stride, and sums its exact squares.  The CTA adds its sum
+// to accumulator set p mod 3 and arrives at a grid barrier.  After the
+// barrier every CTA runs the end of pass itself -- the chi-squared rescale
+// (Eq. 3), the strides drawn a pass ahead, the drift check (Section 8) -- on
+// its own shared-memory copy of the generator's state, three threads at
+// once, from the summed Q and the withheld value read together.  The
+// arithmetic is the same in every CTA, so the copies stay identical and
+// nothing is broadcast; CTA 0 writes its copy back at the end.
+//
+// Why a plain gather here: staging spans in shared memory (the pass kernels
+// for pools in HBM) saves DRAM bytes, but a pool in L2 has none to save,
+// while the staging pipeline's set-up and tile latency would be most of a
+// pass.  Index arithmetic is 32-bit (pools of at most 2^23 values, strides
+// small enough that alpha N < 2^32), since a 64-bit remainder costs hundreds
+// of cycles on this part.
+//
+// Accumulator set (p + 1) mod 3 is cleared by CTA 0 during pass p: its last
+// readers (after barrier p - 2) have all arrived at barrier p - 1 by then.
+// The barrier counter only grows: pass p's barrier completes at (p + 1) G
+// arrivals.  Every wait is bounded (about a second); a CTA that gives up
+// raises the grid's abort flag, the others stop at their next barrier, and
+// the generator's status gets WALLACE_ETIMEOUT.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "wl_common.cuh"
+#include "wl_launch.h"
+
+#define L2_THREADS 512
+#define L2_WAIT_CYCLES 2000000000ll   /* about one second */
+
+namespace {
+
+struct L2Acc {
+    alignas(128) unsigned long long a0, a1, a2;   // Q limbs: bits 0-31, 32-63, 64-127 of CTA sums
+    unsigned int bad;
+};
+
+// Device scratch of one launch (zeroed by the host before it).
+struct L2Sync {
+    alignas(128) unsigned int arrived;   // barrier arrivals so far
+    alignas(128) int abort;              // a CTA gave up waiting
+    L2Acc acc[3];                        // sum of squares of pass p in set p mod 3
+};
+
+struct L2Args {
+    float *buf[2];
+    int cur;
+    WlDevState *st;
+    L2Sync *sy;
+    int64_t N, Np, R;
+    int64_t passes;
+    float *out;           // pass p writes its first take values to out + p R (may be null)
+    int64_t last_take;    // values the last pass returns (the others return R)
+    float mu, sigma;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Arrival at the grid barrier (thread 0, after a CTA barrier that follows
+// the CTA's writes of the pass): its release publishes them.
+__device__ __forceinline__ void l2_arrive(L2Sync *sy)
+{
+    if (threadIdx.x == 0)
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(&sy->arrived) : "memory");
+}
+
+// Bounded wait for `target` arrivals: true when every CTA has arrived, false
+// when the wait gave up or another CTA did.  Every thread calls.
+__device__ bool l2_wait(L2Sync *sy, unsigned int target)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        int ok = 1;
+        while (ld_acquire_u32(&sy->arrived) < target) {
+            if (*(volatile int *)&sy->abort || clock64() - t0 > L2_WAIT_CYCLES) {
+                ok = 0;
+                atomicExch(&sy->abort, 1);
+                break;
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// CTA sum of (lo, hi, bad) into one accumulator set (every thread calls).
+__device__ void l2_reduce_to(uint64_t lo, uint64_t hi, uint32_t bad, L2Acc *acc, uint64_t *red)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const uint64_t olo = __shfl_down_sync(0xffffffffu, lo, off);
+        const uint64_t ohi = __shfl_down_sync(0xffffffffu, hi, off);
+        wl_add128(lo, hi, olo, ohi);
+    }
+    bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        red[warp] = lo;
+        red[nw + warp] = hi;
+        red[2 * nw + warp] = bad;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        lo = lane < nw ? red[lane] : 0ull;
+        hi = lane < nw ? red[nw + lane] : 0ull;
+        bad = lane < nw ? (uint32_t)red[2 * nw + lane] : 0u;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const uint64_t olo = __shfl_down_sync(0xffffffffu, lo, off);
+            const uint64_t ohi = __shfl_down_sync(0xffffffffu, hi, off);
+            wl_add128(lo, hi, olo, ohi);
+        }
+        bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
+        if (lane == 0) {
+            atomicAdd(&acc->a0, (unsigned long long)(lo & 0xffffffffull));
+            atomicAdd(&acc->a1, (unsigned long long)(lo >> 32));
+            if (hi)
+                atomicAdd(&acc->a2, (unsigned long long)hi);
+            if (bad)
+                atomicOr(&acc->bad, 1u);
+        }
+    }
+    __syncthreads();
+}
+
+
+// SG: the generator draws a sign pattern each pass (matrix A D_k).
+template <int NSUB, bool SG>
+__global__ void __launch_bounds__(L2_THREADS, 2) l2run_kernel(L2Args a)
+{
+    __shared__ uint64_t red[3 * (L2_THREADS / 32)];
+    __shared__ WlDevState sst;   // this CTA's copy of the generator's state
+    wl_state_load(&sst, a.st);
+    WlDevState *st = &sst;
+    L2Sync *sy = a.sy;
+    const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
+    const uint32_t N = (uint32_t)a.N;
+    const int64_t Np = a.Np, nu = NSUB * a.N;
+    const double rnu = wl_rnu(nu);
+    const uint32_t gt = (uint32_t)b * blockDim.x + tid, GT = (uint32_t)G * blockDim.x;
+    const float mu = a.mu, sigma = a.sigma;
+    int cur = a.cur;
+    for (int64_t p = 0; p < a.passes; p++) {
+        // this pass's parameters become the most recent pass's (warp 0, word
+        // by word; nothing reads `last` during the pass)
+        if (tid < 32) {
+            const uint32_t *from = (const uint32_t *)&st->next;
+            uint32_t *to = (uint32_t *)&st->last;
+            for (int w = tid; w < (int)(sizeof(WlParams) / 4); w += 32)
+                to[w] = from[w];
+        }
+        // 32-bit index arithmetic: (alpha + 1) N < 2^32 (checked by the host)
+        uint32_t idx[NSUB], stp[NSUB];
+#pragma unroll
+        for (int i = 0; i < NSUB; i++) {
+            const uint32_t al = (uint32_t)st->next.alpha[i], ga = (uint32_t)st->next.gamma[i];
+            idx[i] = (al * (gt < N ? gt : 0u) + ga) % N;
+            stp[i] = (al * (GT % N)) % N;
+        }
+        const float c = st->next.c32;
+        const uint32_t signs = SG ? st->next.signs : 0u;
+        const float *src = a.buf[cur];
+        float *dst = a.buf[1 - cur];
+        float *o = a.out ? a.out + p * a.R : nullptr;
+        const uint32_t w1 = o ? (uint32_t)(p + 1 < a.passes ? a.R : a.last_take) : 0u;
+        uint64_t lo = 0, hi = 0;
+        uint32_t bad = 0;
+        for (uint32_t j = gt; j < N; j += GT) {
+            float g[NSUB], y[NSUB];
+#pragma unroll
+            for (int i = 0; i < NSUB; i++) {
+                g[i] = __ldcg(src + i * Np + idx[i]);
+                if (SG)
+                    g[i] = wl_sgn(g[i], signs, i);
+                idx[i] += stp[i];
+                idx[i] -= idx[i] >= N ? N : 0u;
+            }
+            if constexpr (NSUB == 4)
+                wl_xform4(g, c, y);
+            else
+                wl_xform8(g, c, y);
+#pragma unroll
+            for (int k = 0; k < NSUB; k++) {
+                dst[k * Np + j] = y[k];
+                wl_add128(lo, hi, wl_term32(y[k], bad), 0);
+                const uint32_t q = (uint32_t)k * N + j;
+                if (q < w1)
+                    o[q] = __fadd_rn(mu, __fmul_rn(sigma, y[k]));
+            }
+        }
+        L2Acc *acc = &sy->acc[p % 3];
+        l2_reduce_to(lo, hi, bad, acc, red);
+        if (b == 0 && tid == 0) {
+            L2Acc *nx = &sy->acc[(p + 1) % 3];
+            nx->a0 = 0;
+            nx->a1 = 0;
+            nx->a2 = 0;
+            nx->bad = 0;
+        }
+        l2_arrive(sy);
+        if (!l2_wait(sy, (unsigned int)((p + 1) * G)))
+            break;
+        // end of pass from the summed Q: scale (thread 0), strides (32),
+        // drift (64), each reading Q and the withheld value together
+        if (tid == 0 || tid == 64) {
+            const unsigned long long a0 = __ldcg(&acc->a0), a1 = __ldcg(&acc->a1), a2 = __ldcg(&acc->a2);
+            const uint32_t qbad = __ldcg(&acc->bad);
+            const double x = (double)__ldcg(&dst[wl_last_phys(NSUB, a.N, Np)]);
+            const unsigned long long t = a0 + (a1 << 32);
+            const uint64_t qhi = a2 + (a1 >> 32) + (t < a0 ? 1ull : 0ull);
+            wl_end_pass_role(st, NSUB, a.N, nu, rnu, t, qhi, qbad, x, tid == 0 ? 0 : 2, SG ? 1 : 0, false);
+        } else if (tid == 32) {
+            wl_end_pass_role(st, NSUB, a.N, nu, rnu, 0, 0, 0, 0.0, 1, SG ? 1 : 0, false);
+        }
+        __syncthreads();
+        cur = 1 - cur;
+    }
+    if (b == 0) {
+        __syncthreads();
+        if (tid == 0 && *(volatile int *)&sy->abort)
+            st->status |= WL_ETIMEOUT;
+        wl_state_store(a.st, st);
+    }
+}
+
+int g_l2_max_grid = 0;   // co-resident CTAs of the kernel on this device (0: not looked up)
+
+} // namespace
+
+bool wl_l2run_supported(int n, int64_t N, int fp64, int64_t max_stride)
+{
+    // 32-bit indices: (alpha + 1) N < 2^32 and n N <= 2^23
+    return (n == 4 || n == 8) && !fp64 && N >= 4 && (int64_t)n * N <= ((int64_t)1 << 23) &&
+           (max_stride + 1) * N < ((int64_t)1 << 32);
+}
+
+size_t wl_l2run_sync_bytes() { return sizeof(L2Sync); }
+
+int wl_l2run_grid(int64_t nu, int sm_count)
+{
+    // measured: one CTA per SM is fastest up to 2^22 values (a pass is mostly
+    // barrier and end-of-pass latency there); two per SM above
+    return nu <= ((int64_t)1 << 22) ? sm_count : 2 * sm_count;
+}
+
+cudaError_t wl_launch_l2run(void *buf0, void *buf1, int cur, int n, int64_t N, int64_t Np, WlDevState *st,
+                            void *sync, int64_t passes, int64_t R, int64_t last_take, void *out, double mu,
+                            double sigma, int grid, int signs, cudaStream_t stream)
+{
+    auto kern = n == 8 ? (signs ? l2run_kernel<8, true> : l2run_kernel<8, false>)
+                       : (signs ? l2run_kernel<4, true> : l2run_kernel<4, false>);
+    if (!g_l2_max_grid) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // every instantiation has the same shape; the <8, true> one has the most registers
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, l2run_kernel<8, true>, L2_THREADS, 0);
+        if (e != cudaSuccess)
+            return e;
+        g_l2_max_grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    if (grid > g_l2_max_grid)
+        grid = g_l2_max_grid;
+    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(L2Sync), stream);
+    if (e != cudaSuccess)
+        return e;
+    L2Args a;
+    a.buf[0] = (float *)buf0;
+    a.buf[1] = (float *)buf1;
+    a.cur = cur;
+    a.st = st;
+    a.sy = (L2Sync *)sync;
+    a.N = N;
+    a.Np = Np;
+    a.R = R;
+    a.passes = passes;
+    a.out = (float *)out;
+    a.last_take = last_take;
+    a.mu = (float)mu;
+    a.sigma = (float)sigma;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(L2_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident: they wait on one another
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, a);
+    if (e != cudaSuccess)
+        return e;
+    return cudaGetLastError();
+}

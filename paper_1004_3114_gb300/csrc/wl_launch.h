@@ -64,6 +64,24 @@ bool wl_tma8_supported(int n, int64_t N, int fp64);
 bool wl_tma8_return_kernel(const WlPassArgs &a);
 cudaError_t wl_launch_tma8(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream);
 
+// many passes of one n = 4 or 8 binary32 pool of at most 2^23 values in one
+// cooperative launch of `grid` CTAs (capped at what can be resident), with a
+// bounded grid barrier per pass (pools that stay in L2 between passes); every
+// stride must satisfy (alpha + 1) N < 2^32 (max_stride: the largest the pool
+// can draw).  `sync` is a device block of wl_l2run_sync_bytes() bytes, zeroed
+// here before the launch.  The pool is in buffer `cur` of (buf0, buf1); pass k
+// writes its values [0, take_k) to out + k R (take_k = R, last_take for the
+// last).  The final pool is in the other buffer when `passes` is odd.
+// signs: the generator draws a sign pattern per pass (matrix A D_k).
+bool wl_l2run_supported(int n, int64_t N, int fp64, int64_t max_stride);
+size_t wl_l2run_sync_bytes();
+int wl_l2run_grid(int64_t nu, int sm_count);
+// pools AUTO sends to it: above the shared-memory size, at most this many values
+#define WL_L2RUN_AUTO_MAX_VALUES ((int64_t)1 << 22)
+cudaError_t wl_launch_l2run(void *buf0, void *buf1, int cur, int n, int64_t N, int64_t Np, WlDevState *st,
+                            void *sync, int64_t passes, int64_t R, int64_t last_take, void *out, double mu,
+                            double sigma, int grid, int signs, cudaStream_t stream);
+
 // whole pool resident in shared memory for `passes` passes in one launch.
 // Pass k (0-based) writes its values [0, take_k) to out + out_off_k where
 // take_k = R for k < passes-1 and last_take for the final pass.

@@ -187,7 +187,7 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
             wl_gather_range_n<NSUB>(src, dst, N, d.Np, alpha, gam, c, o, w1, d.mu, d.sigma, lo, hi,
                                     bad);
         }
-        const float *xp = &dst[wl_phys(nu - 1, N, d.Np)];
+        const float *xp = &dst[wl_last_phys(NSUB, N, d.Np)];
         wl_end_pass_cta(st, NSUB, N, nu, rnu, lo, hi, bad, red, [xp]() { return (double)__ldcg(xp); },
                         st->msigns, false);
         cur = 1 - cur;

@@ -65,7 +65,8 @@ __device__ __forceinline__ void tl_cp_async_wait_all()
 // (the error f (ceil(2^32/d) - 2^32/d) / 2^32 < f / 2^32 < 1/d); d = 1 is passed through.
 __device__ __forceinline__ uint32_t tl_magic(uint32_t d)
 {
-    return d > 1 ? (uint32_t)((0x100000000ull + d - 1) / d) : 0u;
+    // ceil(2^32 / d) = floor((2^32 - 1) / d) + 1 for d >= 2 (a 32-bit division)
+    return d > 1 ? 0xffffffffu / d + 1u : 0u;
 }
 __device__ __forceinline__ uint32_t tl_div(uint32_t f, uint32_t d, uint32_t m)
 {
@@ -74,11 +75,19 @@ __device__ __forceinline__ uint32_t tl_div(uint32_t f, uint32_t d, uint32_t m)
 
 __device__ __forceinline__ int wl_lcm4(const int *alpha)
 {
-    int L = alpha[0];
+    // 32-bit gcd: strides and their lcm stay far below 2^31
+    uint32_t L = (uint32_t)alpha[0];
 #pragma unroll
-    for (int i = 1; i < 4; i++)
-        L = L / (int)wl_gcd(L, alpha[i]) * alpha[i];
-    return L;
+    for (int i = 1; i < 4; i++) {
+        uint32_t x = L, y = (uint32_t)alpha[i];
+        while (y) {
+            const uint32_t t = x % y;
+            x = y;
+            y = t;
+        }
+        L = L / x * (uint32_t)alpha[i];
+    }
+    return (int)L;
 }
 
 __device__ __forceinline__ bool wl_tiled_ok(int L, int64_t N)
@@ -174,7 +183,7 @@ __device__ inline void wl_tiled4_tiles(const WlTileJob &a, int L, int tile0, int
         int64_t r = (int64_t)a.alpha[i] * J[l] - (int64_t)w * N - spanC[sb[i] + p];
         lanebase[i * TL_LMAX + l] = slot0[i] + p * SL[i] + (int)r;
     }
-    const int maxlen = (int)((N + L - 1) / L);
+    const int maxlen = (int)(((uint32_t)N + (uint32_t)L - 1u) / (uint32_t)L);
     const int ntiles_all = (maxlen + T - 1) / T;
     const int tbeg = (int)((int64_t)ntiles_all * part / nparts);
     const int ntiles = (int)((int64_t)ntiles_all * (part + 1) / nparts);

@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) tma_kernel(WlPassArgs a, double
 
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st))
-        wl_finalise_cta(st, NSUB, N, a.nu, rnu, &dst[wl_phys(a.nu - 1, N, Np)], SG ? 1 : 0);
+        wl_finalise_cta(st, NSUB, N, a.nu, rnu, &dst[wl_last_phys(NSUB, N, Np)], SG ? 1 : 0);
 }
 
 bool g_tma_configured[3] = {false, false, false};

@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(T8_THREADS, 1) tma8_kernel(WlPassArgs a, doubl
 
     wl_cta_reduce_to_state(lo, hi, bad, st, red);
     if (wl_last_cta(st))
-        wl_finalise_cta(st, 8, N, a.nu, rnu, &dst[wl_phys(a.nu - 1, N, Np)], SG ? 1 : 0);
+        wl_finalise_cta(st, 8, N, a.nu, rnu, &dst[wl_last_phys(8, N, Np)], SG ? 1 : 0);
 }
 
 // out[q - w0] = mu + sigma pool[q] for the returned window [w0, w1) of the

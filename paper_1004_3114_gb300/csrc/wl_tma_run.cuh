@@ -100,6 +100,62 @@ __host__ __device__ inline bool wl_tma_run_eligible(int n, int64_t N)
     return n == 4 && N >= TM_MIN_N && N <= ((int64_t)1 << 28);
 }
 
+// Lane tables of one pass into `tab` (a tr_common_words() area): J[L + 1]
+// lane starts, lanebase[4][TR_LMAX] (slot position of each lane's first
+// value, before its span's lead, in bits 8.., its span in bits 0..7) and
+// spanC[spans] (span starts).  They depend on N, the strides (their lcm L)
+// and the tile length T only.  Every thread of the CTA calls; the caller
+// orders the previous readers of `tab` before the call and the new readers
+// after it (barriers).
+__device__ inline void wl_tma_tables(int64_t N, int L, int T, const int32_t *alpha, int *tab)
+{
+    using namespace wl_tma;
+    const int tid = threadIdx.x;
+    int m[4], sb[5], SL[4], slot0[4];
+    sb[0] = 0;
+    slot0[0] = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        m[i] = tm_divc(L, alpha[i]);
+        sb[i + 1] = sb[i] + m[i];
+        SL[i] = (alpha[i] * T + TR_SPAN_PAD) & ~3;
+        if (i < 3)
+            slot0[i + 1] = slot0[i] + m[i] * ((alpha[i] * T + TR_SPAN_PAD) & ~3);
+    }
+    const int nspans = sb[4];
+    int *J = tab;
+    int *lanebase = J + (TR_LMAX + 1);
+    int *spanC = lanebase + 4 * TR_LMAX;
+    const int N32 = (int)N;
+    for (int l = tid; l <= L; l += blockDim.x) {
+        const int qN = tm_divc(N32, L), rN = N32 - qN * L;
+        J[l] = l * qN + tm_divc(l * rN + L - 1, L);
+    }
+    for (int s = tid; s < nspans; s += blockDim.x) {
+        const int i = tm_sub<4>(s, sb);
+        const int p = s - sb[i], mi = m[i];
+        const int qN = tm_divc(N32, mi), rN = N32 - qN * mi;
+        spanC[s] = p * qN + tm_divc(p * rN + mi - 1, mi);
+    }
+    __syncthreads();
+    for (int e = tid; e < 4 * L; e += blockDim.x) {
+        int i = tm_divc(e, L), l = e - i * L;
+        int w = tm_divc(l, m[i]), p = l - w * m[i];
+        int64_t r = (int64_t)alpha[i] * J[l] - (int64_t)w * N - spanC[sb[i] + p];
+        lanebase[i * TR_LMAX + l] = ((slot0[i] + p * SL[i] + (int)r) << 8) | (sb[i] + p);
+    }
+    __syncthreads();
+}
+
+// Tile length (lane times) of a pass with L lanes: the ring's memory as two
+// stages, or as one stage of twice the length from TR_ONE_STAGE_L lanes on
+// (see wl_tma_pass_cta), capped at tcap.
+__device__ __forceinline__ int wl_tma_tile_T(int L, int tcap)
+{
+    const int S = L >= TR_ONE_STAGE_L ? 1 : TR_STAGES;
+    return min(wl_tma::tm_divc(TR_ETARGET * TR_STAGES / S, L), tcap);
+}
+
 // One pass src -> dst of an n = 4 pool (a pool wl_tma_run_eligible accepts)
 // whose strides have lcm L <= TR_LMAX.  Every thread of the CTA calls; the
 // terms of its values are added to (lo, hi) and its bad-value flag to `bad`.
@@ -113,10 +169,18 @@ __host__ __device__ inline bool wl_tma_run_eligible(int n, int64_t N)
 // at slot positions from N - as on therefore sit N4 - N further on: each span
 // records that threshold and shift, and the consumers add the shift to
 // positions at or past the threshold (the shift is 0 when 4 divides N).
+//
+// tile0, tstep, tcap: this CTA takes tiles tile0, tile0 + tstep, ... of the
+// pass (a grid of CTAs sharing one pool), each of at most tcap lane times;
+// the defaults take every tile at the ring's full length.  pre: the pass's
+// lane tables already built by wl_tma_tables (same L and T), else they are
+// built here in the ring's own table area.
 __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, int64_t Np, int L,
                                        const int32_t *alpha, const int64_t *gam, float c, float *o,
                                        int64_t w1, float mu, float sigma, float *smem, WlTmaRing &ring,
-                                       WlDevState *st, uint64_t &lo, uint64_t &hi, uint32_t &bad)
+                                       WlDevState *st, uint64_t &lo, uint64_t &hi, uint32_t &bad,
+                                       int tile0 = 0, int tstep = 1, int tcap = 1 << 30,
+                                       const int *pre = nullptr)
 {
     using namespace wl_tma;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -135,7 +199,7 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
     const int S = L >= TR_ONE_STAGE_L ? 1 : TR_STAGES;
     const int SW = TR_STAGES * tr_stage_words() / S;   // words per stage
     const int SDW = SW - 2 * TR_MAXSPANS;               // span data words per stage
-    const int T = tm_divc(TR_ETARGET * TR_STAGES / S, L);
+    const int T = wl_tma_tile_T(L, tcap);
     int SL[4], slot0[4];
     slot0[0] = 0;
 #pragma unroll
@@ -145,37 +209,21 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
             slot0[i + 1] = slot0[i] + m[i] * SL[i];
     }
     float *stage0 = smem;
-    int *common = (int *)(smem + TR_STAGES * tr_stage_words());
-    int *J = common;
-    int *lanebase = J + (TR_LMAX + 1);
-    int *spanC = lanebase + 4 * TR_LMAX;
-
-    // the previous pass's readers of the tables are done
-    __syncthreads();
+    int *common = pre ? (int *)pre : (int *)(smem + TR_STAGES * tr_stage_words());
+    const int *J = common;
+    const int *lanebase = J + (TR_LMAX + 1);
+    const int *spanC = lanebase + 4 * TR_LMAX;
     const int N32 = (int)N;
-    for (int l = tid; l <= L; l += TM_THREADS) {
-        const int qN = tm_divc(N32, L), rN = N32 - qN * L;
-        J[l] = l * qN + tm_divc(l * rN + L - 1, L);
+    if (!pre) {
+        // the previous pass's readers of the tables are done
+        __syncthreads();
+        wl_tma_tables(N, L, T, alpha, common);
     }
-    for (int s = tid; s < nspans; s += TM_THREADS) {
-        const int i = tm_sub<4>(s, sb);
-        const int p = s - sb[i], mi = m[i];
-        const int qN = tm_divc(N32, mi), rN = N32 - qN * mi;
-        spanC[s] = p * qN + tm_divc(p * rN + mi - 1, mi);
-    }
-    __syncthreads();
-    // lane l, sub-vector i: slot position of its first value (before the
-    // span's lead) in bits 8.., its span in bits 0..7
-    for (int e = tid; e < 4 * L; e += TM_THREADS) {
-        int i = tm_divc(e, L), l = e - i * L;
-        int w = tm_divc(l, m[i]), p = l - w * m[i];
-        int64_t r = (int64_t)alpha[i] * J[l] - (int64_t)w * N - spanC[sb[i] + p];
-        lanebase[i * TR_LMAX + l] = ((slot0[i] + p * SL[i] + (int)r) << 8) | (sb[i] + p);
-    }
-    __syncthreads();
     const int maxlen = tm_divc(N32 + L - 1, L);
     const int ntiles = (maxlen + T - 1) / T;
-    // tile k uses stage k % S for the (uses[s] + k / S)-th time
+    // this CTA's kt-th tile (tile0 + kt tstep) uses stage kt % S for the
+    // (uses[s] + kt / S)-th time
+    const int nmine = ntiles > tile0 ? (ntiles - tile0 + tstep - 1) / tstep : 0;
     const int use0 = ring.uses[0], use1 = TR_STAGES > 1 ? ring.uses[TR_STAGES - 1] : 0;
     const int N4 = (N32 + 3) & ~3;
 
@@ -215,8 +263,9 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
 #pragma unroll
             for (int q = 0; q < TR_STAGES; q++)
                 issued[q] = 0;
-            for (int tile = 0; tile < ntiles; tile++) {
-                const int s = S == 1 ? 0 : tile & 1, u = (s == 0 ? use0 : use1) + (S == 1 ? tile : tile >> 1);
+            for (int kt = 0; kt < nmine; kt++) {
+                const int tile = tile0 + kt * tstep;
+                const int s = S == 1 ? 0 : kt & 1, u = (s == 0 ? use0 : use1) + (S == 1 ? kt : kt >> 1);
                 if (*ring.abort_flag)
                     break;
                 if (u > 0 && !mbar_wait(smem_u32(&ring.empty[s]), (uint32_t)((u - 1) & 1))) {
@@ -326,8 +375,9 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         uint32_t emax = 0;
         const bool shifted = N4 != N32;   // wrapped spans sit shifted past their threshold
         {
-            for (int tile = 0; tile < ntiles; tile++) {
-                const int s = S == 1 ? 0 : tile & 1, u = (s == 0 ? use0 : use1) + (S == 1 ? tile : tile >> 1);
+            for (int kt = 0; kt < nmine; kt++) {
+                const int tile = tile0 + kt * tstep;
+                const int s = S == 1 ? 0 : kt & 1, u = (s == 0 ? use0 : use1) + (S == 1 ? kt : kt >> 1);
                 if (*ring.abort_flag)
                     break;
                 if (!mbar_wait(smem_u32(&ring.full[s]), (uint32_t)(u & 1))) {
@@ -443,9 +493,9 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         asm volatile("fence.proxy.async.global;\n" ::: "memory");
     }
     // the uses every thread counted, the same in all of them
-    ring.uses[0] = use0 + (S == 1 ? ntiles : (ntiles + 1) >> 1);
+    ring.uses[0] = use0 + (S == 1 ? nmine : (nmine + 1) >> 1);
     if (S > 1)
-        ring.uses[TR_STAGES - 1] = use1 + (ntiles >> 1);
+        ring.uses[TR_STAGES - 1] = use1 + (nmine >> 1);
 }
 
 // out[q] = mu + sigma pool[q] for q < w1 (logical positions; rows of N at
@@ -533,7 +583,7 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
             // the next pass may read this pool with bulk copies
             asm volatile("fence.proxy.async.global;\n" ::: "memory");
         }
-        const float *xp = &dst[wl_phys(nu - 1, N, d.Np)];
+        const float *xp = &dst[wl_last_phys(4, N, d.Np)];
         wl_end_pass_cta(st, 4, N, nu, rnu, lo, hi, bad, red, [xp]() { return (double)__ldcg(xp); }, st->msigns,
                         false);
         if (copy_back)

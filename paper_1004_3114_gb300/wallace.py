@@ -23,7 +23,7 @@ FP32, FP64POOL = 0, 1
 CHI_WH = 0x100   # mode flag: Wilson-Hilferty chi-squared sample
 MATRIX_SIGNS = 0x200   # mode flag: random sign pattern per pass (matrix A D_k)
 VARIANT_AUTO, VARIANT_GATHER, VARIANT_TILED, VARIANT_FUSED = 0, 1, 2, 3
-VARIANT_TILED_ASYNC, VARIANT_TILED_TMA, VARIANT_TWOPHASE = 4, 5, 6
+VARIANT_TILED_ASYNC, VARIANT_TILED_TMA, VARIANT_TWOPHASE, VARIANT_L2RUN = 4, 5, 6, 7
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -84,6 +84,7 @@ _SIGS = {
     "wallace_set_variant": (C.c_int, [_h, C.c_int]),
     "wallace_set_timing": (C.c_int, [_h, C.c_int]),
     "wallace_set_restart": (C.c_int, [_h, C.c_int64]),
+    "wallace_set_l2_grid": (C.c_int, [_h, C.c_int]),
     "wallace_sync": (C.c_int, [_h]),
     "wallace_stats": (C.c_int, [_h, C.POINTER(Stats)]),
     "wallace_get_pool": (C.c_int, [_h, C.c_void_p]),
@@ -458,6 +459,10 @@ class Wallace:
         """Refill the pool by Box-Muller before every pass that follows a
         multiple of `interval` passes (0: never)."""
         _check(_lib.wallace_set_restart(self._h, interval), "wallace_set_restart")
+
+    def set_l2_grid(self, grid: int = 0) -> None:
+        """CTAs of VARIANT_L2RUN's launch (0: two per SM)."""
+        _check(_lib.wallace_set_l2_grid(self._h, grid), "wallace_set_l2_grid")
 
     def sync(self) -> int:
         return _check(_lib.wallace_sync(self._h), "wallace_sync", allow=ECORRUPT)

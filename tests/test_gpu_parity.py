@@ -174,11 +174,11 @@ def test_fp64_pool_mode_bit_exact(orc, n, N):
 
 @pytest.mark.parametrize("n,N,frac,variant,mode", [
     (8, 20000, 0.5, W.VARIANT_TWOPHASE, W.FP32),
-    (8, 100003, 1 / 3, W.VARIANT_AUTO, W.FP32),       # AUTO picks the two-phase pass
+    (8, 100003, 1 / 3, W.VARIANT_TWOPHASE, W.FP32),
     (8, 1 << 16, 1.0, W.VARIANT_TWOPHASE, W.FP32),
     (8, 9000, 0.25, W.VARIANT_TWOPHASE, W.FP32),      # 3 and 5 divide N: strides up to 7^2 11 13
     (8, 16385, 0.5, W.VARIANT_TWOPHASE, W.FP32),      # N % 4 == 1: blocks that wrap unaligned
-    (4, 15 * 4099, 0.5, W.VARIANT_AUTO, W.FP32),      # n = 4, 15 | N: 539 lanes, AUTO two-phase
+    (4, 15 * 4099, 0.5, W.VARIANT_TWOPHASE, W.FP32),  # n = 4, 15 | N: 539 lanes
     (4, 105 * 1001, 1.0, W.VARIANT_TWOPHASE, W.FP32), # 105 | N: strides up to 11^2 13
 ])
 def test_twophase_pass_bit_exact(orc, n, N, frac, variant, mode):
@@ -197,7 +197,7 @@ def test_twophase_pass_bit_exact(orc, n, N, frac, variant, mode):
             assert_same(g.pool64(), o.pool64(), f"pass {k + 1} pool")
         assert_stats_equal(g, o, f"pass {k + 1}")
     st = g.stats()
-    assert st.launches >= 2 * 5   # two kernels a pass (AUTO picks the two-phase pass here)
+    assert st.launches >= 2 * 5   # two kernels a pass
     # fills that start mid-pass: returned values land at unaligned addresses
     for cnt in (1001, 3 * g.R + 5, 7):
         assert_same(fill_dev(g, cnt, 0.25, 3.0), o.fill(cnt, 0.25, 3.0), f"fill of {cnt}")
@@ -213,11 +213,12 @@ def test_twophase_pass_bit_exact(orc, n, N, frac, variant, mode):
     ((1 << 21) + 32, 0.3, 23),
 ])
 def test_tma8_pass_bit_exact(orc, N, frac, seed):
-    """n = 8 with N coprime to 105: every pass has 315 lanes, and AUTO runs the
-    bulk-copy lane-tiled kernel (pools over 64 MB: then the returned values'
-    kernel).  Pools, returned values and state scalars against the oracle,
-    pass by pass, then fills that start mid-pass."""
+    """n = 8 with N coprime to 105: every pass has 315 lanes, and the tiled
+    variant runs the bulk-copy lane-tiled kernel (pools over 64 MB: then the
+    returned values' kernel).  Pools, returned values and state scalars
+    against the oracle, pass by pass, then fills that start mid-pass."""
     g = W.Wallace(8, N, seed, frac)
+    g.set_variant(W.VARIANT_TILED)
     o = orc.Generator(8, N, seed, frac)
     before = g.stats().launches
     for k in range(5):
@@ -283,6 +284,7 @@ def test_fill_host_matches_device(orc):
 def test_streams_and_timing(orc):
     s = torch.cuda.Stream()
     g = W.Wallace(4, 1 << 16, 2, 0.5, stream=s)
+    g.set_variant(W.VARIANT_TILED)     # one pass kernel per pass
     g.set_timing(True)
     o = orc.Generator(4, 1 << 16, 2, 0.5)
     with torch.cuda.stream(s):
@@ -486,3 +488,64 @@ def test_rann4_full_size(orc):
         assert_same(fill_dev(g, g.R), o.fill(g.R), f"pass {k + 1} output")
         assert_stats_equal(g, o, f"pass {k + 1}")
     assert_same(g.pool(), o.pool32(), "pool")
+
+
+@pytest.mark.parametrize("n,N,frac,mode", [
+    (4, 16384, 0.5, 0),
+    (4, 16387, 1 / 3, 0),            # N = 3 mod 4
+    (4, 1 << 16, 0.5, 0),
+    (4, 45060, 1.0, 0),              # 2^2 3 5 751: strides from the divisors of 7^2 11
+    (4, 21000, 0.5, 0),              # 2^3 3 5^3 7: strides up to 11^2 13
+    (4, 1 << 21, 0.25, 0),           # 2^23 values (32 MB), the largest pool it takes
+    (8, 1 << 17, 0.5, 0),            # A = J/4 - I
+    (8, 3001, 1.0, 0),
+    (4, 100003, 0.5, W.MATRIX_SIGNS),   # a sign pattern per pass (A D_k)
+    (8, 50000, 0.5, W.MATRIX_SIGNS | W.CHI_WH),
+])
+def test_l2_multipass_100_passes_bit_exact(orc, n, N, frac, mode):
+    """The multi-pass L2 kernel (one cooperative launch per fill, a grid
+    barrier per pass): 100 passes in four fills of 25, every returned value,
+    the pool and the pass's scalars against the oracle after each fill."""
+    g = W.Wallace(n, N, 23, frac, mode=W.FP32 | mode)
+    g.set_variant(W.VARIANT_L2RUN)
+    o = orc.Generator(n, N, 23, frac, mode=orc.FP32 | mode)
+    R = g.R
+    for k in range(4):
+        st0 = g.stats()
+        got = fill_dev(g, 25 * R, -1.25, 0.75)
+        assert g.stats().launches - st0.launches == 1, "one launch per fill"
+        assert_same(got, o.fill(25 * R, -1.25, 0.75), f"fill {k + 1} values")
+        assert_same(g.pool(), o.pool32(), f"pool after {25 * (k + 1)} passes")
+        assert_stats_equal(g, o, f"after {25 * (k + 1)} passes")
+
+
+def test_l2_multipass_split_fills_single_passes_and_grids(orc):
+    """Fills that end mid-pass (the rest drained by the next fill), single
+    passes through wallace_pass, the Wilson-Hilferty sample, and grids of 1,
+    7, 152 and (capped) 100000 CTAs give one stream."""
+    n, N = 4, 100004
+    g = W.Wallace(n, N, 29, 1 / 3, mode=W.FP32 | W.CHI_WH)
+    g.set_variant(W.VARIANT_L2RUN)
+    o = orc.Generator(n, N, 29, 1 / 3, mode=orc.FP32 | orc.CHI_WH)
+    R = g.R
+    for grid, count in ((0, 3 * R + R // 3), (1, R - R // 3 + 5), (7, 4 * R), (152, 2 * R + 17),
+                        (100000, 3 * R), (0, 0)):
+        g.set_l2_grid(grid)
+        assert_same(fill_dev(g, count, 0.5, 2.0), o.fill(count, 0.5, 2.0), f"grid {grid}")
+    g.pass_()
+    o.pass_()
+    g.pass_()
+    o.pass_()
+    assert_same(g.pool(), o.pool32(), "after single passes")
+    assert_stats_equal(g, o, "after single passes")
+    assert_same(fill_dev(g, 2 * R), o.fill(2 * R), "fill after single passes")
+    assert g.sync() == 0
+
+
+def test_l2_multipass_refuses_pools_it_cannot_index():
+    """Beyond 2^23 values, and n = 2, the variant is refused."""
+    for n, N in ((4, (1 << 21) + 4), (2, 1 << 16)):
+        g = W.Wallace(n, N, 3, 0.5)
+        with pytest.raises(RuntimeError):
+            g.set_variant(W.VARIANT_L2RUN)
+        g.close()
