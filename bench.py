@@ -1004,7 +1004,7 @@ def batched_classes_bench(names=None, pools: int = 1024, passes: int = 10, runs:
 
 def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float = 50_000.0,
                 budget_gb: float = 40.0, passes_per_tick: int = 2, ctas_per_sm: int = 0,
-                cpu_baseline: bool = True) -> dict:
+                cpu_baseline: bool = True, tick=None, parity: bool = True) -> dict:
     """Serving loop: n_clients generators (n = 4, N log-uniform on
     [2^10, 2^20], frac = 1/3), Poisson arrivals at `rate`, counts log-uniform
     on [2^10, 2^24], mu ~ U[-10, 10], sigma ~ U[0.1, 10], admitted against a
@@ -1019,7 +1019,11 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
     t0 = time.perf_counter()
     srv = W.Server(4, Ns, seeds, 1 / 3, int(budget_gb * (1 << 30)), stream=stream)
     create_s = time.perf_counter() - t0
-    srv.set_tuning(passes_per_tick, 4096, ctas_per_sm)
+    # pools of up to 24576 values stay in shared memory (the bulk-copy
+    # runner's block holds them; 8192 with the 256-thread kernel only)
+    srv.set_tuning(passes_per_tick, 24576 if ctas_per_sm == 0 else 4096, ctas_per_sm)
+    if tick:
+        srv.set_tick(*tick)
     tr = serving_requests(n_requests, n_clients, rate)
     t0 = time.perf_counter()
     lat = srv.run_trace(tr["arrival_s"], tr["client"], tr["count"], tr["mu"], tr["sigma"])
@@ -1028,7 +1032,7 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
     values = int(tr["count"].sum())
     peak, kind = hbm_peak()
     bytes_moved = 28 * values        # per returned value at f = 3: 3 x 8 B pool read+write + 4 B out
-    parity = serve_sampled_parity(srv, Ns, seeds, tr)
+    parity = serve_sampled_parity(srv, Ns, seeds, tr) if parity else None
     srv.close()
     cpu = serve_cpu_baseline(Ns, seeds, tr) if cpu_baseline else None
     offered = values / float(tr["arrival_s"][-1])
@@ -1042,10 +1046,12 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
         "mean_ms": float(lat.mean()), "values": values, "elapsed_s": st.elapsed_s, "wall_s": wall,
         "offered_values_per_s": offered, "served_over_offered": values / st.elapsed_s / offered,
         "ticks": int(st.ticks), "hbm_peak_gb": st.hbm_peak / 2**30, "hbm_budget_gb": st.hbm_budget / 2**30,
+        "host_tick_s": st.host_tick_s, "host_wait_s": st.host_wait_s, "items": int(st.items),
+        "mean_admit_wait_ms": st.mean_admit_wait_ms,
         "roofline": {"bound": "hbm", "achieved": bytes_moved / st.elapsed_s / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": bytes_moved / st.elapsed_s / 1e9 / peak, "peak_kind": kind,
                      "bytes_per_value": 28},
-        "passes_per_tick": passes_per_tick, "ctas_per_sm": ctas_per_sm,
+        "passes_per_tick": passes_per_tick, "ctas_per_sm": ctas_per_sm, "tick": tick,
         "runner": "bulk-copy for one-CTA requests on 16384 <= N (n=4)" if ctas_per_sm == 0
                   else "async-copy", "create_s": create_s, "sampled_parity": parity,
         "status": int(st.status)}
@@ -1081,6 +1087,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=20_000)
     ap.add_argument("--serve-rate", type=float, default=50_000.0)
     ap.add_argument("--serve-ppt", type=int, default=2)
+    ap.add_argument("--serve-tick", default=None,
+                    help="with --serve: semicolon-separated one_cta_max:values_per_tick settings to sweep")
     ap.add_argument("--serve-ctas", type=int, default=0,
                     help="CTAs per SM of the one-CTA requests; 0: bulk-copy runner where it applies")
     ap.add_argument("--batched-classes", action="store_true",
@@ -1095,6 +1103,8 @@ def main():
     ap.add_argument("--l2-grids", default="0",
                     help="with --l2: comma-separated grid sizes (0: two CTAs per SM)")
     ap.add_argument("--l2-n", type=int, default=4, help="with --l2: sub-vectors (4 or 8)")
+    ap.add_argument("--l2-sizes", default="14-21",
+                    help="with --l2: log2 of nu / 4, a range a-b or a comma-separated list")
     ap.add_argument("--no-extras", action="store_true",
                     help="default line only: skip the batched, serving, n = 8 and precision objects")
     ap.add_argument("--tune-cache", default=None,
@@ -1107,7 +1117,12 @@ def main():
         return
     if args.l2:
         grids = tuple(int(v) for v in args.l2_grids.split(","))
-        print(json.dumps(l2_bench(grids=grids, n=args.l2_n)), flush=True)
+        if "-" in args.l2_sizes:
+            lo, hi = (int(v) for v in args.l2_sizes.split("-"))
+            sizes = range(lo, hi + 1)
+        else:
+            sizes = [int(v) for v in args.l2_sizes.split(",")]
+        print(json.dumps(l2_bench(log2_sizes=sizes, grids=grids, n=args.l2_n)), flush=True)
         return
     if args.batched:
         print(json.dumps(batched_bench(power_of_two=args.pow2, count=args.batched_count,
@@ -1127,9 +1142,13 @@ def main():
         variant_bench(steps=args.variants_steps)
         return
     if args.serve:
-        print(json.dumps(serve_bench(n_requests=args.serve_requests, rate=args.serve_rate,
-                                     passes_per_tick=args.serve_ppt, ctas_per_sm=args.serve_ctas)),
-              flush=True)
+        ticks = [None] if not args.serve_tick else [
+            tuple(int(v) for v in t.split(":")) for t in args.serve_tick.split(";")]
+        for tk in ticks:
+            print(json.dumps(serve_bench(n_requests=args.serve_requests, rate=args.serve_rate,
+                                         passes_per_tick=args.serve_ppt, ctas_per_sm=args.serve_ctas,
+                                         tick=tk, cpu_baseline=len(ticks) == 1, parity=len(ticks) == 1)),
+                  flush=True)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -362,6 +362,10 @@ typedef struct {
     double elapsed_s;           /* first submit to last completion            */
     int32_t status;
     int32_t pad_;
+    double host_tick_s;         /* host time spent building and enqueueing ticks */
+    double host_wait_s;         /* host time blocked waiting for a tick         */
+    int64_t items;              /* requests summed over ticks (work items)      */
+    double mean_admit_wait_ms;  /* mean time from submit to admission           */
 } wallace_server_stats_t;
 
 /*
@@ -384,6 +388,14 @@ void wallace_server_destroy(wallace_server_t *s);
  * the others.  Only while idle. */
 int wallace_server_set_tuning(wallace_server_t *s, int passes_per_tick, int64_t fused_max,
                               int ctas_per_sm);
+
+/* wallace_server_set_tick -- what one scheduler tick gives a request (not
+ * part of the paper's method): pools of up to one_cta_max_values values run on
+ * one CTA per request, for up to values_per_tick / (n N) passes a tick (at
+ * least one); larger pools run pass-major over all CTAs, passes_per_tick
+ * passes a tick.  Defaults 2^22 and 2^20.  Only while idle; WALLACE_EINVAL
+ * otherwise or on a negative value. */
+int wallace_server_set_tick(wallace_server_t *s, int64_t one_cta_max_values, int64_t values_per_tick);
 
 /* wallace_server_submit -- queue a request; returns its id (host, no GPU work). */
 int wallace_server_submit(wallace_server_t *s, int client, int64_t count, float mu, float sigma,

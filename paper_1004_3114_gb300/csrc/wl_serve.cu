@@ -8,10 +8,11 @@
 // pool buffer -- fit in the device-memory budget.  A scheduler tick turns
 // every active request into one work item (first the values left in the
 // client's current pool, then passes whose returned prefixes go straight into
-// the request's output).  Pools of up to 2^18 values run in one persistent
-// kernel, a CTA per request doing many passes in a row (in shared memory when
-// the pool fits, else from global memory that the L2 cache mostly holds), up
-// to a per-tick budget of pool values.  Larger pools run pass-major: each of up to
+// the request's output).  Pools of up to a set size (2^22 values by default:
+// wallace_server_set_tick) run in one persistent kernel, a CTA per request
+// doing many passes in a row (in shared memory when the pool fits -- up to
+// 24576 values in the bulk-copy kernel's block -- else from global memory),
+// up to a per-tick budget of pool values.  Larger pools run pass-major: each of up to
 // `passes_per_tick` launches does one pass of every large request, split
 // into units of about 2^17 pool values spread over all CTAs; the last unit
 // of a request (by ticket) runs its chi-squared rescale (Eq. 3), so no CTA
@@ -19,11 +20,14 @@
 // next tick as slots and memory free up, so their work shares launches with
 // requests already in flight.
 //
-// Ticks are enqueued back to back on the server's stream: the host's view of
-// every client (cursor, which buffer holds the pool) is updated when a tick
-// is enqueued, which the stream order makes exact.  A tick's event tells when
-// its finishing requests are done; memory that a tick still reads is freed
-// only after that event.
+// Each tick slot has its own stream, and a tick takes only the active
+// requests that are not in a tick still in flight, so a long item (a pass
+// over a large pool) does not hold up the other requests: they go on in the
+// next ticks on other streams.  A request is in at most one tick in flight,
+// and its client stays busy until that tick's event, so the host's view of
+// every client (cursor, which buffer holds the pool) -- updated when a tick is
+// enqueued -- is exact.  A tick's event tells when its finishing requests are
+// done; memory that a tick still reads is freed only after that event.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -339,6 +343,7 @@ struct Request {
     float *scratch = nullptr;   // second pool buffer (global-memory path)
     int loc = 0;                // 0: pool in the client's buffer, 1: in scratch
     bool finished = false, reaped = false, released = false;
+    bool busy = false;          // in a tick still in flight
     double t_submit = 0, t_done = 0;
 };
 
@@ -351,6 +356,7 @@ struct CopyBack {
 struct Tick {
     cudaEvent_t ev;
     int slot;
+    std::vector<int64_t> members;     // requests with work in this tick
     std::vector<int64_t> finishing;
     std::vector<void *> deferred_free;
     std::vector<CopyBack> copies;   // pools that end in a scratch buffer, copied home
@@ -367,9 +373,10 @@ double now_s()
 struct wallace_server {
     int n = 4, nclients = 0;
     double frac = 1.0;
-    cudaStream_t stream = nullptr;
-    cudaStream_t aux = nullptr;             // the bulk-copy runner's stream (forked per tick)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t stream = nullptr;          // creation and the final synchronisation
+    std::vector<cudaStream_t> sstream;      // one per tick slot
+    std::vector<cudaStream_t> aux;          // per slot: the bulk-copy runner's stream (forked per tick)
+    std::vector<cudaEvent_t> ev_fork, ev_join;
     bool bulk = false;                      // one-CTA requests of large enough pools use the bulk-copy runner
     int sm_count = 1, max_ctas_per_sm = 1;
     char *pool_mem = nullptr;
@@ -384,7 +391,7 @@ struct wallace_server {
     std::vector<int64_t> completed_unpolled;
     int64_t held_outputs = 0;   // completed requests whose output is not yet released
     // tick slots: device work arrays and work counters
-    int nslots = 4;
+    int nslots = 8;
     std::vector<char *> d_work;
     std::vector<size_t> work_cap;
     int *d_queues = nullptr;   // kQueuesPerSlot counters per slot
@@ -392,13 +399,16 @@ struct wallace_server {
     // tuning
     int passes_per_tick = 2;          // large pools: passes per request per tick
     int64_t small_values_per_tick = 1 << 20;   // one-CTA pools: pool values per request per tick
-    int64_t onchip_max_values = 1 << 18;       // pools up to this run one CTA per request
+    int64_t onchip_max_values = 1 << 22;       // pools up to this run one CTA per request (measured:
+                                               // every pool of the serving mix; pass-major above)
     int64_t unit_values = 1 << 17;    // large pools: pool values per CTA work unit
     int64_t fused_max = 4096;
     int ctas_per_sm = 3;
     // statistics
     int64_t submitted = 0, admitted = 0, completed = 0, ticks = 0, values = 0;
     std::vector<double> latencies;
+    double host_tick_s = 0, host_wait_s = 0, admit_wait_s = 0;
+    int64_t items = 0;
     double t_first = -1, t_last = 0;
     int status = 0;
 };
@@ -414,9 +424,15 @@ int sfail(wallace_server_t *s, cudaError_t e)
     return WALLACE_ECUDA;
 }
 
+// Shared-memory capacity (floats) of the kernel that runs a one-CTA item:
+// with the bulk-copy runner on, pools that fit its larger block but not the
+// 256-thread kernel's stay in shared memory there too.
+int64_t small_smem_values() { return (int64_t)(tl_smem_bytes() / sizeof(float)); }
+int64_t big_smem_values() { return (int64_t)(wl_tma::tr_smem_bytes() / sizeof(float)); }
+
 bool uses_fused(const wallace_server_t *s, const Client &c)
 {
-    return wl_run_is_fused(s->n, c.N, s->fused_max, (int64_t)(tl_smem_bytes() / sizeof(float)));
+    return wl_run_is_fused(s->n, c.N, s->fused_max, s->bulk ? big_smem_values() : small_smem_values());
 }
 
 size_t pool_bytes(const wallace_server_t *s, const Client &c)
@@ -456,6 +472,7 @@ void admit(wallace_server_t *s)
         r.out = out;
         r.scratch = scr;
         r.loc = 0;
+        s->admit_wait_s += now_s() - r.t_submit;
         c.active = true;
         s->active.push_back(c.waiting.front());
         c.waiting.pop_front();
@@ -473,21 +490,35 @@ int acquire_slot(wallace_server_t *s)
     return -1;
 }
 
+// Finish the ticks whose events have completed (in any order: each slot has
+// its own stream); with `block`, wait for the oldest first when none has.
 void reap(wallace_server_t *s, bool block)
 {
-    while (!s->inflight.empty()) {
-        Tick &t = s->inflight.front();
-        cudaError_t q = block ? cudaEventSynchronize(t.ev) : cudaEventQuery(t.ev);
-        if (q == cudaErrorNotReady)
-            return;
+    bool done_any = false;
+    for (size_t k = 0; k < s->inflight.size();) {
+        Tick &t = s->inflight[k];
+        cudaError_t q = cudaEventQuery(t.ev);
+        if (q == cudaErrorNotReady && block && !done_any && k == 0) {
+            const double w0 = now_s();
+            q = cudaEventSynchronize(t.ev);
+            s->host_wait_s += now_s() - w0;
+        }
+        if (q == cudaErrorNotReady) {
+            k++;
+            continue;
+        }
         if (q != cudaSuccess) {
             s->status |= WALLACE_ECUDA;
             return;
         }
+        done_any = true;
         const double tn = now_s();
+        for (int64_t id : t.members)
+            s->reqs[id].busy = false;
         for (int64_t id : t.finishing) {
             Request &r = s->reqs[id];
             r.reaped = true;
+            s->clients[r.client].active = false;   // its pool is settled: the next request may start
             if (r.out)
                 s->held_outputs++;
             r.t_done = tn;
@@ -501,16 +532,33 @@ void reap(wallace_server_t *s, bool block)
             s->arena.free(p);
         s->slot_busy[t.slot] = false;
         cudaEventDestroy(t.ev);
-        s->inflight.pop_front();
+        s->inflight.erase(s->inflight.begin() + (std::ptrdiff_t)k);
     }
 }
 
 // Build and enqueue one tick over every active request: one on-chip kernel
 // for the shared-memory pools, then one pass-major launch per pass for the
 // large pools.
+int enqueue_tick_impl(wallace_server_t *s);
+
 int enqueue_tick(wallace_server_t *s)
 {
-    if (s->active.empty())
+    const double t0 = now_s();
+    const int rc = enqueue_tick_impl(s);
+    s->host_tick_s += now_s() - t0;
+    return rc;
+}
+
+int enqueue_tick_impl(wallace_server_t *s)
+{
+    // the active requests not in a tick still in flight
+    bool any = false;
+    for (int64_t id : s->active)
+        if (!s->reqs[id].busy) {
+            any = true;
+            break;
+        }
+    if (!any)
         return WALLACE_OK;
     int slot = acquire_slot(s);
     if (slot < 0) {
@@ -527,6 +575,12 @@ int enqueue_tick(wallace_server_t *s)
     std::vector<int64_t> still;
     for (int64_t id : s->active) {
         Request &r = s->reqs[id];
+        if (r.busy) {
+            still.push_back(id);   // its previous tick has not finished
+            continue;
+        }
+        r.busy = true;
+        t.members.push_back(id);
         Client &c = s->clients[r.client];
         float *bufs[2] = {c.buf, r.scratch ? r.scratch : c.buf};
         const int64_t nu = (int64_t)s->n * c.N;
@@ -622,7 +676,7 @@ int enqueue_tick(wallace_server_t *s)
                 r.scratch = nullptr;
                 r.loc = 0;
             }
-            c.active = false;
+            // the client stays busy until this tick completes (see reap)
         } else {
             still.push_back(id);
         }
@@ -636,7 +690,10 @@ int enqueue_tick(wallace_server_t *s)
     if (s->bulk) {
         const int64_t tma_values = (int64_t)(wl_tma::tr_smem_bytes() / sizeof(float));
         auto mid = std::stable_partition(small.begin(), small.end(), [&](const ServeItem &it) {
-            return !sv_bulk_eligible(it.spec.n, it.spec.N, it.spec.passes, s->fused_max, tma_values);
+            const int64_t nu = (int64_t)it.spec.n * it.spec.N;
+            const bool big_fused = it.spec.passes > 0 && wl_run_is_fused(it.spec.n, it.spec.N, s->fused_max, tma_values) &&
+                                   2 * nu > small_smem_values();
+            return !(sv_bulk_eligible(it.spec.n, it.spec.N, it.spec.passes, s->fused_max, tma_values) || big_fused);
         });
         nrest = (int)(mid - small.begin());
     }
@@ -672,28 +729,30 @@ int enqueue_tick(wallace_server_t *s)
     }
     char *dw = s->d_work[slot];
     int *dq = s->d_queues + slot * SV_QUEUES_PER_SLOT;
+    cudaStream_t st = s->sstream[slot], aux = s->aux[slot];
+    cudaEvent_t ev_fork = s->ev_fork[slot], ev_join = s->ev_join[slot];
     if (e == cudaSuccess && bytes)
-        e = cudaMemcpyAsync(dw, host.data(), bytes, cudaMemcpyHostToDevice, s->stream);
+        e = cudaMemcpyAsync(dw, host.data(), bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(dq, 0, sizeof(int) * SV_QUEUES_PER_SLOT, s->stream);
+        e = cudaMemsetAsync(dq, 0, sizeof(int) * SV_QUEUES_PER_SLOT, st);
     const int ctas = s->sm_count * std::min(s->ctas_per_sm, s->max_ctas_per_sm);
     // bulk-copy items (placed after the others) run on the aux stream, beside the rest
     const int nbulk = (int)small.size() - nrest;
     if (e == cudaSuccess && nbulk > 0) {
-        e = cudaEventRecord(s->ev_fork, s->stream);
+        e = cudaEventRecord(ev_fork, st);
         if (e == cudaSuccess)
-            e = cudaStreamWaitEvent(s->aux, s->ev_fork, 0);
+            e = cudaStreamWaitEvent(aux, ev_fork, 0);
         if (e == cudaSuccess) {
-            serve_tma_kernel<<<std::min(s->sm_count, nbulk), TM_THREADS, wl_tma::tr_smem_bytes(), s->aux>>>(
+            serve_tma_kernel<<<std::min(s->sm_count, nbulk), TM_THREADS, wl_tma::tr_smem_bytes(), aux>>>(
                 (const ServeItem *)dw + nrest, nbulk, dq + SV_MAX_PPT + 1, s->fused_max);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess)
-            e = cudaEventRecord(s->ev_join, s->aux);
+            e = cudaEventRecord(ev_join, aux);
     }
     if (e == cudaSuccess && nrest > 0) {
         const int grid = std::min(ctas, nrest);
-        serve_kernel<<<grid, SV_THREADS, tl_smem_bytes(), s->stream>>>((const ServeItem *)dw, nrest, dq,
+        serve_kernel<<<grid, SV_THREADS, tl_smem_bytes(), st>>>((const ServeItem *)dw, nrest, dq,
                                                                     s->fused_max);
         e = cudaGetLastError();
     }
@@ -701,23 +760,24 @@ int enqueue_tick(wallace_server_t *s)
         if (punits[p].empty())
             continue;
         const int grid = std::min(ctas, (int)punits[p].size());
-        pass_units_kernel<<<grid, SV_THREADS, tl_smem_bytes(), s->stream>>>(
+        pass_units_kernel<<<grid, SV_THREADS, tl_smem_bytes(), st>>>(
             (const PassItem *)(dw + off_items[p]), (const PassUnit *)(dw + off_units[p]),
             (int)punits[p].size(), dq + 1 + p);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && nbulk > 0)
-        e = cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+        e = cudaStreamWaitEvent(st, ev_join, 0);
     for (size_t k = 0; k < t.copies.size() && e == cudaSuccess; k++)
         e = cudaMemcpyAsync(t.copies[k].dst, t.copies[k].src, t.copies[k].bytes, cudaMemcpyDeviceToDevice,
-                            s->stream);
+                            st);
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming);
     if (e == cudaSuccess)
-        e = cudaEventRecord(t.ev, s->stream);
+        e = cudaEventRecord(t.ev, st);
     if (e != cudaSuccess)
         return sfail(s, e);
     s->slot_busy[slot] = true;
+    s->items += (int64_t)t.members.size();
     s->inflight.push_back(std::move(t));
     s->ticks++;
     return WALLACE_OK;
@@ -798,12 +858,19 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(serve_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)wl_tma::tr_smem_bytes());
-    if (e == cudaSuccess)
-        e = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking);
-    if (e == cudaSuccess)
-        e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess)
-        e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
+    s->sstream.assign(s->nslots, nullptr);
+    s->aux.assign(s->nslots, nullptr);
+    s->ev_fork.assign(s->nslots, nullptr);
+    s->ev_join.assign(s->nslots, nullptr);
+    for (int k = 0; k < s->nslots && e == cudaSuccess; k++) {
+        e = cudaStreamCreateWithFlags(&s->sstream[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&s->aux[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&s->ev_fork[k], cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&s->ev_join[k], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) {
         int per = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, serve_kernel, SV_THREADS, tl_smem_bytes());
@@ -852,14 +919,20 @@ void wallace_server_destroy(wallace_server_t *s)
     if (!s)
         return;
     cudaStreamSynchronize(s->stream);
-    if (s->aux) {
-        cudaStreamSynchronize(s->aux);
-        cudaStreamDestroy(s->aux);
+    for (size_t k = 0; k < s->sstream.size(); k++) {
+        if (s->sstream[k]) {
+            cudaStreamSynchronize(s->sstream[k]);
+            cudaStreamDestroy(s->sstream[k]);
+        }
+        if (s->aux[k]) {
+            cudaStreamSynchronize(s->aux[k]);
+            cudaStreamDestroy(s->aux[k]);
+        }
+        if (s->ev_fork[k])
+            cudaEventDestroy(s->ev_fork[k]);
+        if (s->ev_join[k])
+            cudaEventDestroy(s->ev_join[k]);
     }
-    if (s->ev_fork)
-        cudaEventDestroy(s->ev_fork);
-    if (s->ev_join)
-        cudaEventDestroy(s->ev_join);
     for (auto &t : s->inflight)
         cudaEventDestroy(t.ev);
     for (auto *p : s->d_work)
@@ -879,6 +952,15 @@ int wallace_server_set_tuning(wallace_server_t *s, int passes_per_tick, int64_t 
     s->fused_max = fused_max;
     s->bulk = ctas_per_sm == 0;
     s->ctas_per_sm = ctas_per_sm == 0 ? 3 : ctas_per_sm;
+    return WALLACE_OK;
+}
+
+int wallace_server_set_tick(wallace_server_t *s, int64_t one_cta_max_values, int64_t values_per_tick)
+{
+    if (!s || one_cta_max_values < 0 || values_per_tick < 1 || !s->active.empty() || !s->inflight.empty())
+        return WALLACE_EINVAL;
+    s->onchip_max_values = one_cta_max_values;
+    s->small_values_per_tick = values_per_tick;
     return WALLACE_OK;
 }
 
@@ -941,11 +1023,15 @@ int wallace_server_drain(wallace_server_t *s)
             reap(s, true);
             continue;
         }
+        const int64_t before = s->ticks;
         int rc = enqueue_tick(s);
         if (rc)
             return rc;
+        if (s->ticks == before)
+            reap(s, true);   // every active request is in a tick in flight
     }
-    reap(s, true);
+    while (!s->inflight.empty() && !(s->status & WALLACE_ECUDA))
+        reap(s, true);
     cudaError_t e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? s->status : sfail(s, e);
 }
@@ -1076,6 +1162,10 @@ int wallace_server_stats(wallace_server_t *s, wallace_server_stats_t *out)
     percentile(s->latencies, &out->p50_ms, &out->p99_ms, &out->mean_ms);
     out->elapsed_s = s->t_first >= 0 ? s->t_last - s->t_first : 0.0;
     out->status = s->status;
+    out->host_tick_s = s->host_tick_s;
+    out->host_wait_s = s->host_wait_s;
+    out->items = s->items;
+    out->mean_admit_wait_ms = s->admitted ? 1e3 * s->admit_wait_s / (double)s->admitted : 0.0;
     return WALLACE_OK;
 }
 

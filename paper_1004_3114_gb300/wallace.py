@@ -52,7 +52,8 @@ class ServerStats(C.Structure):
         ("values_delivered", C.c_int64), ("hbm_budget", C.c_int64), ("hbm_in_use", C.c_int64),
         ("hbm_peak", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
         ("mean_ms", C.c_double), ("elapsed_s", C.c_double), ("status", C.c_int32),
-        ("pad_", C.c_int32),
+        ("pad_", C.c_int32), ("host_tick_s", C.c_double), ("host_wait_s", C.c_double),
+        ("items", C.c_int64), ("mean_admit_wait_ms", C.c_double),
     ]
 
 
@@ -110,6 +111,7 @@ _SIGS = {
                                         C.c_int64, C.c_void_p, C.POINTER(C.c_void_p)]),
     "wallace_server_destroy": (None, [C.c_void_p]),
     "wallace_server_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int]),
+    "wallace_server_set_tick": (C.c_int, [_h, C.c_int64, C.c_int64]),
     "wallace_server_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_float, C.c_float,
                                         C.POINTER(C.c_int64)]),
     "wallace_server_progress": (C.c_int, [C.c_void_p]),
@@ -240,6 +242,10 @@ class Server:
     def set_tuning(self, passes_per_tick: int, fused_max: int, ctas_per_sm: int) -> None:
         _check(_lib.wallace_server_set_tuning(self._h, passes_per_tick, fused_max, ctas_per_sm),
                "wallace_server_set_tuning")
+
+    def set_tick(self, one_cta_max_values: int, values_per_tick: int) -> None:
+        _check(_lib.wallace_server_set_tick(self._h, one_cta_max_values, values_per_tick),
+               "wallace_server_set_tick")
 
     def submit(self, client: int, count: int, mu: float = 0.0, sigma: float = 1.0) -> int:
         rid = C.c_int64()

@@ -46,8 +46,10 @@ def _serve(Ns, seeds, reqs, frac, budget, tuning=None, interleave=True):
 
 
 @pytest.mark.parametrize("frac,tuning", [(1 / 3, None), (1.0, (1, 2048, 2)), (0.5, (3, 0, 1)),
-                                         (1 / 3, (2, 4096, 0))])
+                                         (1 / 3, (2, 4096, 0)), (1 / 3, (2, 24576, 0))])
 def test_server_outputs_match_oracle(orc, frac, tuning):
+    """(2, 24576, 0): pools of up to 24576 values stay in shared memory, those
+    above the 256-thread kernel's capacity in the bulk-copy kernel's block."""
     Ns, seeds, reqs = _mix(7, 24, 160, 40000)
     outs, st = _serve(Ns, seeds, reqs, frac, 256 << 20, tuning)
     oracles = {c: orc.Generator(4, int(Ns[c]), int(seeds[c]), frac) for c in set(r[0] for r in reqs)}
@@ -128,6 +130,7 @@ def test_server_large_pools_split_into_units(orc, ppt):
     seeds = np.array([21, 22, 23, 24, 25, 26], dtype=np.uint32)
     srv = W.Server(4, Ns, seeds, 1 / 3, 1 << 30)
     srv.set_tuning(ppt, 4096, 3)
+    srv.set_tick(1 << 18, 1 << 20)     # pools above 2^18 values run pass-major
     rng = np.random.default_rng(9)
     reqs = [(int(rng.integers(0, 6)), int(rng.integers(1, 400000)), float(rng.uniform(-2, 2)), 1.5)
             for _ in range(40)]
@@ -167,3 +170,28 @@ def test_server_bulk_copy_runner(orc, ppt):
         ref = oracles[c].fill(cnt, np.float32(mu), np.float32(sg))
         got = srv.result_host(rid)
         assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (c, int(Ns[c]), cnt)
+
+
+@pytest.mark.parametrize("tick", [(1 << 22, 1 << 20), (1 << 22, 1 << 16)])
+def test_server_every_pool_on_one_cta(orc, tick):
+    """wallace_server_set_tick: every pool (up to 2^22 values) on one CTA per
+    request, a tick's share of work per request from 2^16 to 2^20 pool
+    values; several ticks in flight on their own streams.  Every value exact."""
+    Ns = np.array([1 << 16, 100003, 45060, 3001, 300, 16387, 6000, 1 << 18], dtype=np.int64)
+    seeds = np.arange(41, 41 + Ns.size, dtype=np.uint32)
+    srv = W.Server(4, Ns, seeds, 1 / 3, 1 << 30)
+    srv.set_tuning(2, 24576, 0)
+    srv.set_tick(*tick)
+    rng = np.random.default_rng(13)
+    reqs = [(int(rng.integers(0, Ns.size)), int(rng.integers(1, 600000)), float(rng.uniform(-2, 2)),
+             float(rng.uniform(0.5, 2))) for _ in range(60)]
+    ids = []
+    for k, (c, cnt, mu, sg) in enumerate(reqs):
+        ids.append(srv.submit(c, cnt, mu, sg))
+        if k % 3 == 2:
+            srv.progress()
+    srv.drain()
+    oracles = [orc.Generator(4, int(N), int(sd), 1 / 3) for N, sd in zip(Ns, seeds)]
+    for rid, (c, cnt, mu, sg) in zip(ids, reqs):
+        ref = oracles[c].fill(cnt, np.float32(mu), np.float32(sg))
+        assert np.array_equal(srv.result_host(rid).view(np.uint32), ref.view(np.uint32)), (c, int(Ns[c]), cnt)
