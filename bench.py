@@ -735,8 +735,8 @@ def l2_bench(log2_sizes=range(14, 22), frac: float = 0.5, target_ms: float = 150
              grids=(0,), n: int = 4) -> dict:
     """Pools that stay in L2 between passes (n = 4 or 8, nu = 4 2^k, seed 7): the
     multi-pass kernel (every pass of a fill in one cooperative launch)
-    against one launch per pass (the single-generator path AUTO picks
-    otherwise), each timed over one fill of about `target_ms` of passes.
+    against one launch per pass (the lane-tiled pass), each timed over one
+    fill of about `target_ms` of passes.
     Rates are in algorithmic bytes (8 nu + 4 R per pass): an "equivalent"
     fraction of the HBM peak, since the pool stays on chip."""
     import torch
@@ -764,6 +764,10 @@ def l2_bench(log2_sizes=range(14, 22), frac: float = 0.5, target_ms: float = 150
         N = (1 << k) * 4 // n
         nu = n * N
         g = W.Wallace(n, N, SEED, frac, stream=stream)
+        try:
+            g.set_variant(W.VARIANT_TILED)   # one launch per pass (AUTO takes the L2 kernel here)
+        except W.WallaceError:
+            g.set_variant(W.VARIANT_GATHER)  # n = 8 pools below 2^14 x 8: no tiled kernel
         byt = 8 * nu + 4 * g.R
         # passes for about target_ms at a first estimate of 10 B per ns
         passes = int(max(200, min(20000, target_ms * 1e6 / max(byt / 10.0, 2000.0))))
