@@ -281,6 +281,31 @@ typedef struct wallace_batch wallace_batch_t;
 int wallace_batch_create(int count, int n, const int64_t *N, const uint32_t *seed, double frac,
                          void *cuda_stream, wallace_batch_t **out);
 
+/*
+ * wallace_batch_create_ex -- as wallace_batch_create, with a mode for every
+ * generator: WALLACE_FP32 optionally OR-ed with WALLACE_CHI_WH (Wilson and
+ * Hilferty's chi-squared sample) and/or WALLACE_MATRIX_SIGNS (a different
+ * orthogonal matrix A D_k each pass, Section 3).  Each generator then
+ * produces exactly what wallace_create_ex(n, N[s], seed[s], 0, frac, mode,
+ * ...) would.  WALLACE_EINVAL for any other mode.
+ */
+int wallace_batch_create_ex(int count, int n, const int64_t *N, const uint32_t *seed, double frac, int mode,
+                            void *cuda_stream, wallace_batch_t **out);
+
+/*
+ * wallace_batch_set_restart -- Section 5 (restarting) for every generator:
+ * before the pass that follows each multiple of `interval` passes (counted
+ * from creation; all generators advance together), every pool is refilled
+ * by Box-Muller from the uniforms its restart takes (as wallace_set_restart
+ * describes) and the scale and drift history start afresh.  A run that
+ * crosses restart points is split into several launches around the refills
+ * (one refill launch per generator, after reading back which buffer holds
+ * each pool: synchronous), with the output laid out as for one launch.
+ * interval = 0 (the default) never restarts.  WALLACE_EINVAL on a NULL batch
+ * or interval < 0.
+ */
+int wallace_batch_set_restart(wallace_batch_t *b, int64_t interval);
+
 /* wallace_batch_destroy -- synchronise and free everything.  NULL-safe. */
 void wallace_batch_destroy(wallace_batch_t *b);
 
@@ -376,6 +401,25 @@ typedef struct {
  */
 int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t *seed, double frac,
                           int64_t hbm_budget_bytes, void *cuda_stream, wallace_server_t **out);
+
+/*
+ * wallace_server_create_ex -- as wallace_server_create, with a mode for every
+ * client's generator: WALLACE_FP32 optionally OR-ed with WALLACE_CHI_WH and/or
+ * WALLACE_MATRIX_SIGNS (as for wallace_create_ex).  A client then receives
+ * exactly the values of wallace_create_ex(n, N[c], seed[c], 0, frac, mode, ...).
+ */
+int wallace_server_create_ex(int n_clients, int n, const int64_t *N, const uint32_t *seed, double frac,
+                             int mode, int64_t hbm_budget_bytes, void *cuda_stream, wallace_server_t **out);
+
+/*
+ * wallace_server_set_restart -- Section 5 (restarting) for every client, as
+ * wallace_set_restart for a handle: before the pass that follows each
+ * multiple of `interval` of a client's passes, its pool is refilled (on the
+ * tick's stream, before the tick's kernels) after any values of its current
+ * pool still owed to the request have been handed out.  interval = 0 (the
+ * default) never restarts.  Only while idle; WALLACE_EINVAL otherwise.
+ */
+int wallace_server_set_restart(wallace_server_t *s, int64_t interval);
 
 /* wallace_server_destroy -- synchronise and free everything.  NULL-safe. */
 void wallace_server_destroy(wallace_server_t *s);

@@ -58,8 +58,13 @@ struct BatchArgs {
     int64_t fused_max;   // pools with n*N <= this stay in shared memory
     float *out;
     float mu, sigma;
+    // output layout of the whole run this launch belongs to (a run split at
+    // restart points): generator s writes pass p of the launch to
+    // out + out_passes * pref_s + (pass0 + p) * R_s
+    int64_t out_passes, pass0;
 };
 
+template <bool SG>   // the batch's generators draw a sign pattern each pass
 __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
 {
     extern __shared__ __align__(128) float smem[];
@@ -87,14 +92,14 @@ __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
         r.R = d.R;
         r.n = d.n;
         r.passes = a.passes;
-        r.out = a.out ? a.out + a.passes * d.out_pref : nullptr;
+        r.out = a.out ? a.out + a.out_passes * d.out_pref + a.pass0 * d.R : nullptr;
         r.last_take = d.R;
         r.mu = a.mu;
         r.sigma = a.sigma;
         r.etarget = a.etarget;
         wl_state_load(&sst, d.st);
         r.st = &sst;
-        const int cur = wl_run_spec(r, a.fused_max, smem_values, smem, red);
+        const int cur = wl_run_spec<SG>(r, a.fused_max, smem_values, smem, red);
         wl_state_store(d.st, &sst);
         if (tid == 0)
             a.streams[a.order[k]].cur = cur;
@@ -104,6 +109,8 @@ __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
 // The same work with the CTA-local bulk-copy runner for the pools it takes
 // (wl_tma_run_eligible: n = 4, N >= TM_MIN_N): one CTA of TM_THREADS threads
 // per SM; the other pools as in batch_kernel.
+// SG: the batch's generators draw a sign pattern each pass (matrix A D_k)
+template <bool SG>
 __global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
 {
     extern __shared__ __align__(128) float smem[];
@@ -139,7 +146,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
         r.R = d.R;
         r.n = d.n;
         r.passes = a.passes;
-        r.out = a.out ? a.out + a.passes * d.out_pref : nullptr;
+        r.out = a.out ? a.out + a.out_passes * d.out_pref + a.pass0 * d.R : nullptr;
         r.last_take = d.R;
         r.mu = a.mu;
         r.sigma = a.sigma;
@@ -148,9 +155,9 @@ __global__ void __launch_bounds__(TM_THREADS, 1) batch_tma_kernel(BatchArgs a)
         wl_state_load(&sst, d.st);
         r.st = &sst;
         if (wl_tma_run_eligible(d.n, d.N) && !wl_run_is_fused(4, d.N, a.fused_max, smem_values))
-            cur = wl_run_tma(r, smem, red, ring);
+            cur = wl_run_tma<SG>(r, smem, red, ring);
         else
-            cur = wl_run_spec(r, a.fused_max, smem_values, smem, red);
+            cur = wl_run_spec<SG>(r, a.fused_max, smem_values, smem, red);
         wl_state_store(d.st, &sst);
         if (tid == 0)
             a.streams[a.order[k]].cur = cur;
@@ -188,6 +195,11 @@ struct wallace_batch {
     int graph_runner = -1;
     int status = 0;
     double last_run_ms = 0.0;
+    std::vector<uint32_t> seed;
+    int opts = 0;                 // wl_launch_init options: Wilson-Hilferty sample, sign patterns
+    int64_t restart = 0;          // refill every generator before the pass after each multiple of this
+    int64_t passes_done = 0;      // passes every generator has run (all advance together)
+    int64_t restarted_at = 0;
 };
 
 namespace {
@@ -199,6 +211,22 @@ int bfail(wallace_batch_t *b, cudaError_t e)
     if (b)
         b->status |= WALLACE_ECUDA;
     return WALLACE_ECUDA;
+}
+
+// Restart r of every generator: its current pool refilled by Box-Muller
+// from uniforms [r 2^40, r 2^40 + nu) of its sequence, the scale and drift
+// history taken afresh (the single-generator refill, one launch each; the
+// buffer each pool is in is read back from the device first).
+cudaError_t refill_all(wallace_batch_t *b, int64_t r)
+{
+    std::vector<BatchStream> hs(b->count);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(hs.data(), b->d_streams, sizeof(BatchStream) * (size_t)b->count, cudaMemcpyDeviceToHost);
+    for (int s = 0; s < b->count && e == cudaSuccess; s++)
+        e = wl_launch_restart(hs[s].pool[hs[s].cur], 0, b->n, b->N[s], b->Np[s], b->seed[s], 0, r, hs[s].st,
+                              b->sm_count, b->stream);
+    return e;
 }
 
 BatchArgs make_args(wallace_batch_t *b, int64_t passes, float *out, float mu, float sigma)
@@ -214,6 +242,8 @@ BatchArgs make_args(wallace_batch_t *b, int64_t passes, float *out, float mu, fl
     a.out = out;
     a.mu = mu;
     a.sigma = sigma;
+    a.out_passes = passes;
+    a.pass0 = 0;
     return a;
 }
 
@@ -222,10 +252,16 @@ cudaError_t ensure_configured()
     static bool done = false;
     if (done)
         return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tl_smem_bytes());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tl_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)wl_tma::tr_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)wl_tma::tr_smem_bytes());
     if (e == cudaSuccess)
         done = true;
@@ -244,7 +280,8 @@ cudaError_t launch_graph(wallace_batch_t *b, const BatchArgs &args)
     BatchArgs a = args;
     void *params[] = {&a};
     cudaKernelNodeParams kp = {};
-    kp.func = tma ? (void *)batch_tma_kernel : (void *)batch_kernel;
+    kp.func = tma ? ((b->opts & 2) ? (void *)batch_tma_kernel<true> : (void *)batch_tma_kernel<false>)
+                  : ((b->opts & 2) ? (void *)batch_kernel<true> : (void *)batch_kernel<false>);
     kp.gridDim = dim3(ctas);
     kp.blockDim = dim3(tma ? TM_THREADS : BT_THREADS);
     kp.sharedMemBytes = (unsigned)(tma ? wl_tma::tr_smem_bytes() : tl_smem_bytes());
@@ -346,7 +383,14 @@ extern "C" {
 int wallace_batch_create(int count, int n, const int64_t *N, const uint32_t *seed, double frac,
                          void *cuda_stream, wallace_batch_t **out)
 {
-    if (!out || count < 1 || !N || !seed || (n != 4 && n != 8) || !(frac > 0.0 && frac <= 1.0))
+    return wallace_batch_create_ex(count, n, N, seed, frac, WALLACE_FP32, cuda_stream, out);
+}
+
+int wallace_batch_create_ex(int count, int n, const int64_t *N, const uint32_t *seed, double frac, int mode,
+                            void *cuda_stream, wallace_batch_t **out)
+{
+    if (!out || count < 1 || !N || !seed || (n != 4 && n != 8) || !(frac > 0.0 && frac <= 1.0) ||
+        (mode & ~(WALLACE_CHI_WH | WALLACE_MATRIX_SIGNS)) != WALLACE_FP32)
         return WALLACE_EINVAL;
     *out = nullptr;
     wallace_batch_t *b = new (std::nothrow) wallace_batch;
@@ -355,6 +399,8 @@ int wallace_batch_create(int count, int n, const int64_t *N, const uint32_t *see
     b->count = count;
     b->n = n;
     b->frac = frac;
+    b->seed.assign(seed, seed + count);
+    b->opts = ((mode & WALLACE_CHI_WH) ? 1 : 0) | ((mode & WALLACE_MATRIX_SIGNS) ? 2 : 0);
     b->stream = (cudaStream_t)cuda_stream;
     b->N.resize(count);
     b->Np.resize(count);
@@ -396,7 +442,7 @@ int wallace_batch_create(int count, int n, const int64_t *N, const uint32_t *see
         e = ensure_configured();
     if (e == cudaSuccess) {
         int per = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel, BT_THREADS, tl_smem_bytes());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<true>, BT_THREADS, tl_smem_bytes());
         b->max_ctas_per_sm = per > 0 ? per : 1;
     }
     if (e != cudaSuccess) {
@@ -435,7 +481,7 @@ int wallace_batch_create(int count, int n, const int64_t *N, const uint32_t *see
                             cudaMemcpyHostToDevice, b->stream);
     for (int s = 0; s < count && e == cudaSuccess; s++)
         e = wl_launch_init(hs[s].pool[0], 0, n, b->N[s], b->Np[s], seed[s], 0, b->states + s,
-                           b->sm_count, b->stream);
+                           b->sm_count, b->stream, b->opts);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
@@ -485,10 +531,43 @@ int wallace_batch_run(wallace_batch_t *b, int64_t passes, float *out, float mu, 
         return WALLACE_EINVAL;
     if (passes == 0)
         return b->status;
-    cudaError_t e = launch_graph(b, make_args(b, passes, out, mu, sigma));
-    if (e != cudaSuccess)
-        return bfail(b, e);
+    if (b->restart <= 0) {
+        cudaError_t e = launch_graph(b, make_args(b, passes, out, mu, sigma));
+        if (e != cudaSuccess)
+            return bfail(b, e);
+        b->passes_done += passes;
+        return b->status;
+    }
+    // Section 5 (restarting): the run is split at the restart points; before
+    // the pass that follows each multiple of the interval every pool is
+    // refilled, and the launches write into the whole run's output layout
+    const int64_t K = b->restart;
+    for (int64_t p = 0; p < passes;) {
+        if (b->passes_done > 0 && b->passes_done % K == 0 && b->restarted_at != b->passes_done) {
+            cudaError_t e = refill_all(b, b->passes_done / K);
+            if (e != cudaSuccess)
+                return bfail(b, e);
+            b->restarted_at = b->passes_done;
+        }
+        const int64_t seg = std::min(passes - p, K - b->passes_done % K);
+        BatchArgs a = make_args(b, seg, out, mu, sigma);
+        a.out_passes = passes;
+        a.pass0 = p;
+        cudaError_t e = launch_graph(b, a);
+        if (e != cudaSuccess)
+            return bfail(b, e);
+        p += seg;
+        b->passes_done += seg;
+    }
     return b->status;
+}
+
+int wallace_batch_set_restart(wallace_batch_t *b, int64_t interval)
+{
+    if (!b || interval < 0)
+        return WALLACE_EINVAL;
+    b->restart = interval;
+    return WALLACE_OK;
 }
 
 int wallace_batch_sync(wallace_batch_t *b)
@@ -537,6 +616,7 @@ int wallace_batch_stats(wallace_batch_t *b, int s, wallace_stats_t *out)
     }
     out->R = b->R[s];
     out->cursor = b->R[s];
+    out->signs = x.last.signs;
     out->kernel_ms = b->last_run_ms;
     return out->status;
 }

@@ -22,11 +22,12 @@ struct WlRunSpec {
 
 // plain strided gather of j in [j0, j_end) (j_end < 0: N), thread t taking
 // j0 + t, j0 + t + blockDim, ...
+// signs: the pass's sign pattern (bit i negates g_i; 0 for the fixed matrix)
 template <int NSUB>
 __device__ void wl_gather_range_n(const float *src, float *dst, int64_t N, int64_t Np,
                                   const int32_t *alpha, const int64_t *gam, float c, float *out,
                                   int64_t w1, float mu, float sigma, uint64_t &lo, uint64_t &hi,
-                                  uint32_t &bad, int64_t j0 = 0, int64_t j_end = -1)
+                                  uint32_t &bad, int64_t j0 = 0, int64_t j_end = -1, uint32_t signs = 0)
 {
     const int64_t G = blockDim.x;
     int64_t j = j0 + threadIdx.x;
@@ -41,7 +42,7 @@ __device__ void wl_gather_range_n(const float *src, float *dst, int64_t N, int64
         float g[NSUB], y[NSUB];
 #pragma unroll
         for (int i = 0; i < NSUB; i++) {
-            g[i] = src[i * Np + idx[i]];
+            g[i] = wl_sgn(src[i * Np + idx[i]], signs, i);
             idx[i] += stp[i];
             if (idx[i] >= N)
                 idx[i] -= N;
@@ -63,7 +64,9 @@ __device__ void wl_gather_range_n(const float *src, float *dst, int64_t N, int64
 
 // All passes with the pool in shared memory (2 n N floats of `sm`); the pool
 // is written back to buf[cur] at the end.
-template <int NSUB>
+// SG (here and below): the generator draws a sign pattern each pass (matrix
+// A D_k); without it the runner carries no sign code.
+template <int NSUB, bool SG>
 __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red)
 {
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -83,6 +86,7 @@ __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red)
         if (tid == 0)
             st->last = st->next;
         const float c = st->next.c32;
+        const uint32_t signs = SG ? st->next.signs : 0u;   // the pass's sign pattern (matrix A D_k)
         // 32-bit index arithmetic: a pool in shared memory has N < 2^13 and
         // alpha * blockDim < 2^32
         int32_t al[NSUB];
@@ -102,7 +106,7 @@ __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red)
             float g[NSUB], y[NSUB];
 #pragma unroll
             for (int i = 0; i < NSUB; i++) {
-                g[i] = src[i * N + idx[i]];
+                g[i] = SG ? wl_sgn(src[i * N + idx[i]], signs, i) : src[i * N + idx[i]];
                 idx[i] += stp[i];
                 if (idx[i] >= N)
                     idx[i] -= N;
@@ -136,7 +140,7 @@ __device__ void wl_run_fused(const WlRunSpec &d, float *sm, uint64_t *red)
 
 // All passes from global memory, alternating buf[cur] and buf[1 - cur];
 // returns the index of the buffer holding the final pool.
-template <int NSUB>
+template <int NSUB, bool SG>
 __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
 {
     const int tid = threadIdx.x;
@@ -173,6 +177,7 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
                 job.gam[i] = gam[i];
             }
             job.c = c;
+            job.signs = SG ? st->next.signs : 0u;
             job.out = o;
             job.w0 = 0;
             job.w1 = w1;
@@ -185,7 +190,7 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
                 wl_gather4_range(job, tid, blockDim.x, lo, hi, bad);
         } else {
             wl_gather_range_n<NSUB>(src, dst, N, d.Np, alpha, gam, c, o, w1, d.mu, d.sigma, lo, hi,
-                                    bad);
+                                    bad, 0, -1, SG ? st->next.signs : 0u);
         }
         const float *xp = &dst[wl_last_phys(NSUB, N, d.Np)];
         wl_end_pass_cta(st, NSUB, N, nu, rnu, lo, hi, bad, red, [xp]() { return (double)__ldcg(xp); },
@@ -198,18 +203,19 @@ __device__ int wl_run_global(const WlRunSpec &d, float *sm, uint64_t *red)
 // Runs the spec on the fused path when the pool fits the shared memory the
 // caller has (smem_values floats) and n N <= fused_max; returns the final
 // buffer index (unchanged for the fused path, which writes back in place).
+template <bool SG = false>
 __device__ inline int wl_run_spec(const WlRunSpec &d, int64_t fused_max, int64_t smem_values, float *sm,
                                   uint64_t *red)
 {
     const int64_t nu = (int64_t)d.n * d.N;
     if (nu <= fused_max && 2 * nu <= smem_values) {
         if (d.n == 4)
-            wl_run_fused<4>(d, sm, red);
+            wl_run_fused<4, SG>(d, sm, red);
         else
-            wl_run_fused<8>(d, sm, red);
+            wl_run_fused<8, SG>(d, sm, red);
         return d.cur;
     }
-    return d.n == 4 ? wl_run_global<4>(d, sm, red) : wl_run_global<8>(d, sm, red);
+    return d.n == 4 ? wl_run_global<4, SG>(d, sm, red) : wl_run_global<8, SG>(d, sm, red);
 }
 
 // Whether wl_run_spec takes the fused path (the host uses the same rule to

@@ -57,6 +57,7 @@ struct ServeItem {
     float *drain_out;
 };
 
+template <bool SG>   // the clients draw a sign pattern each pass (matrix A D_k)
 __global__ void __launch_bounds__(SV_THREADS, 3) serve_kernel(const ServeItem *items, int count,
                                                              int *queue, int64_t fused_max)
 {
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(SV_THREADS, 3) serve_kernel(const ServeItem *i
             WlRunSpec r = it.spec;
             wl_state_load(&sst, it.spec.st);
             r.st = &sst;
-            wl_run_spec(r, fused_max, smem_values, smem, red);
+            wl_run_spec<SG>(r, fused_max, smem_values, smem, red);
             wl_state_store(it.spec.st, &sst);
         }
     }
@@ -99,6 +100,7 @@ __host__ __device__ inline bool sv_bulk_eligible(int n, int64_t N, int64_t passe
 
 // The same items with the CTA-local bulk-copy runner: one 608-thread CTA per
 // SM, running beside serve_kernel's CTAs on another stream.
+template <bool SG>   // the clients draw a sign pattern each pass (matrix A D_k)
 __global__ void __launch_bounds__(TM_THREADS, 1) serve_tma_kernel(const ServeItem *items, int count,
                                                                   int *queue, int64_t fused_max)
 {
@@ -134,9 +136,9 @@ __global__ void __launch_bounds__(TM_THREADS, 1) serve_tma_kernel(const ServeIte
             wl_state_load(&sst, it.spec.st);
             r.st = &sst;
             if (sv_bulk_eligible(it.spec.n, it.spec.N, it.spec.passes, fused_max, smem_values))
-                wl_run_tma(r, smem, red, ring);
+                wl_run_tma<SG>(r, smem, red, ring);
             else
-                wl_run_spec(r, fused_max, smem_values, smem, red);
+                wl_run_spec<SG>(r, fused_max, smem_values, smem, red);
             wl_state_store(it.spec.st, &sst);
         }
     }
@@ -220,6 +222,7 @@ __global__ void __launch_bounds__(SV_THREADS, 3) pass_units_kernel(const PassIte
                 job.gam[i] = gam[i];
             }
             job.c = c;
+            job.signs = it.st->next.signs;
             job.out = it.out;
             job.w0 = 0;
             job.w1 = it.out ? it.w1 : 0;
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(SV_THREADS, 3) pass_units_kernel(const PassIte
                 wl_gather4_range(job, jb + tid, blockDim.x, lo, hi, bad, je);
         } else {
             wl_gather_range_n<8>(it.src, it.dst, N, it.Np, alpha, gam, c, it.out, it.out ? it.w1 : 0,
-                                 it.mu, it.sigma, lo, hi, bad, jb, je);
+                                 it.mu, it.sigma, lo, hi, bad, jb, je, it.st->next.signs);
         }
         wl_cta_reduce_to_state(lo, hi, bad, it.st, red);
         if (last_unit(it.st, it.nunits) && tid == 0)
@@ -330,6 +333,9 @@ struct Client {
     int64_t N, Np, R;
     float *buf;           // resident pool buffer
     WlDevState *st;
+    uint32_t seed = 0;
+    int64_t passes = 0;         // passes run (host count, exact by the tick order)
+    int64_t restarted_at = 0;   // pass count of the last refill (Section 5)
     int64_t cursor;       // next value of the current pool to hand out
     bool active = false;
     std::deque<int64_t> waiting;   // this client's requests not yet admitted, in order
@@ -404,6 +410,8 @@ struct wallace_server {
     int64_t unit_values = 1 << 17;    // large pools: pool values per CTA work unit
     int64_t fused_max = 4096;
     int ctas_per_sm = 3;
+    int opts = 0;           // wl_launch_init options: Wilson-Hilferty sample, sign patterns
+    int64_t restart = 0;    // refill a client's pool before the pass after each multiple of this
     // statistics
     int64_t submitted = 0, admitted = 0, completed = 0, ticks = 0, values = 0;
     std::vector<double> latencies;
@@ -573,6 +581,14 @@ int enqueue_tick_impl(wallace_server_t *s)
     Tick t;
     t.slot = slot;
     std::vector<int64_t> still;
+    struct Refill {
+        float *pool;
+        int64_t N, Np;
+        uint32_t seed;
+        int64_t r;
+        WlDevState *st;
+    };
+    std::vector<Refill> refills;   // pools refilled on this tick's stream before its kernels
     for (int64_t id : s->active) {
         Request &r = s->reqs[id];
         if (r.busy) {
@@ -598,6 +614,22 @@ int enqueue_tick_impl(wallace_server_t *s)
         const int64_t cap = one_cta ? std::max<int64_t>(1, s->small_values_per_tick / nu) : s->passes_per_tick;
         if (P > cap)
             P = cap;
+        if (s->restart > 0 && P > 0) {
+            // Section 5: refill before the pass that follows a multiple of the
+            // interval; values of the current pool still owed go out first
+            // (a drain-only item this tick), and no item crosses a restart point
+            const int64_t K = s->restart;
+            if (c.passes > 0 && c.passes % K == 0 && c.restarted_at != c.passes) {
+                if (drain > 0) {
+                    P = 0;
+                } else {
+                    refills.push_back(Refill{bufs[r.loc], c.N, c.Np, c.seed, c.passes / K, c.st});
+                    c.restarted_at = c.passes;
+                }
+            }
+            P = std::min(P, K - c.passes % K);
+        }
+        c.passes += P;
         const int64_t last = P > 0 ? std::min(c.R, left - (P - 1) * c.R) : 0;
         if (one_cta || P == 0) {
             ServeItem it;
@@ -735,6 +767,9 @@ int enqueue_tick_impl(wallace_server_t *s)
         e = cudaMemcpyAsync(dw, host.data(), bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(dq, 0, sizeof(int) * SV_QUEUES_PER_SLOT, st);
+    for (size_t k = 0; k < refills.size() && e == cudaSuccess; k++)
+        e = wl_launch_restart(refills[k].pool, 0, s->n, refills[k].N, refills[k].Np, refills[k].seed, 0,
+                              refills[k].r, refills[k].st, s->sm_count, st);
     const int ctas = s->sm_count * std::min(s->ctas_per_sm, s->max_ctas_per_sm);
     // bulk-copy items (placed after the others) run on the aux stream, beside the rest
     const int nbulk = (int)small.size() - nrest;
@@ -743,7 +778,8 @@ int enqueue_tick_impl(wallace_server_t *s)
         if (e == cudaSuccess)
             e = cudaStreamWaitEvent(aux, ev_fork, 0);
         if (e == cudaSuccess) {
-            serve_tma_kernel<<<std::min(s->sm_count, nbulk), TM_THREADS, wl_tma::tr_smem_bytes(), aux>>>(
+            auto kern = (s->opts & 2) ? serve_tma_kernel<true> : serve_tma_kernel<false>;
+            kern<<<std::min(s->sm_count, nbulk), TM_THREADS, wl_tma::tr_smem_bytes(), aux>>>(
                 (const ServeItem *)dw + nrest, nbulk, dq + SV_MAX_PPT + 1, s->fused_max);
             e = cudaGetLastError();
         }
@@ -752,8 +788,8 @@ int enqueue_tick_impl(wallace_server_t *s)
     }
     if (e == cudaSuccess && nrest > 0) {
         const int grid = std::min(ctas, nrest);
-        serve_kernel<<<grid, SV_THREADS, tl_smem_bytes(), st>>>((const ServeItem *)dw, nrest, dq,
-                                                                    s->fused_max);
+        auto skern = (s->opts & 2) ? serve_kernel<true> : serve_kernel<false>;
+        skern<<<grid, SV_THREADS, tl_smem_bytes(), st>>>((const ServeItem *)dw, nrest, dq, s->fused_max);
         e = cudaGetLastError();
     }
     for (int p = 0; p < s->passes_per_tick && e == cudaSuccess; p++) {
@@ -806,6 +842,15 @@ extern "C" {
 int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t *seed, double frac,
                           int64_t hbm_budget_bytes, void *cuda_stream, wallace_server_t **out)
 {
+    return wallace_server_create_ex(n_clients, n, N, seed, frac, WALLACE_FP32, hbm_budget_bytes, cuda_stream,
+                                    out);
+}
+
+int wallace_server_create_ex(int n_clients, int n, const int64_t *N, const uint32_t *seed, double frac,
+                             int mode, int64_t hbm_budget_bytes, void *cuda_stream, wallace_server_t **out)
+{
+    if ((mode & ~(WALLACE_CHI_WH | WALLACE_MATRIX_SIGNS)) != WALLACE_FP32)
+        return WALLACE_EINVAL;
     if (!out || n_clients < 1 || !N || !seed || (n != 4 && n != 8) || !(frac > 0.0 && frac <= 1.0) ||
         hbm_budget_bytes <= 0)
         return WALLACE_EINVAL;
@@ -816,6 +861,7 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
     s->n = n;
     s->nclients = n_clients;
     s->frac = frac;
+    s->opts = ((mode & WALLACE_CHI_WH) ? 1 : 0) | ((mode & WALLACE_MATRIX_SIGNS) ? 2 : 0);
     s->stream = (cudaStream_t)cuda_stream;
     s->budget = (size_t)hbm_budget_bytes;
     s->clients.resize(n_clients);
@@ -835,6 +881,7 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
             return WALLACE_EINVAL;
         }
         cl.N = N[c];
+        cl.seed = seed[c];
         cl.Np = ((N[c] + 8 + 63) / 64) * 64;
         cl.R = R;
         cl.cursor = R;   // the initial pool is not returned
@@ -850,13 +897,19 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(serve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tl_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(serve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tl_smem_bytes());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(pass_units_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tl_smem_bytes());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(serve_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(serve_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)wl_tma::tr_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(serve_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)wl_tma::tr_smem_bytes());
     s->sstream.assign(s->nslots, nullptr);
     s->aux.assign(s->nslots, nullptr);
@@ -873,7 +926,7 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
     }
     if (e == cudaSuccess) {
         int per = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, serve_kernel, SV_THREADS, tl_smem_bytes());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, serve_kernel<true>, SV_THREADS, tl_smem_bytes());
         s->max_ctas_per_sm = per > 0 ? per : 1;
     }
     if (e == cudaSuccess && cudaMalloc(&s->pool_mem, s->budget - state_bytes) != cudaSuccess)
@@ -902,7 +955,7 @@ int wallace_server_create(int n_clients, int n, const int64_t *N, const uint32_t
         }
         e = cudaMemsetAsync(cl.buf, 0, pool_bytes(s, cl), s->stream);
         if (e == cudaSuccess)
-            e = wl_launch_init(cl.buf, 0, n, cl.N, cl.Np, seed[c], 0, cl.st, s->sm_count, s->stream);
+            e = wl_launch_init(cl.buf, 0, n, cl.N, cl.Np, seed[c], 0, cl.st, s->sm_count, s->stream, s->opts);
     }
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s->stream);
@@ -952,6 +1005,14 @@ int wallace_server_set_tuning(wallace_server_t *s, int passes_per_tick, int64_t 
     s->fused_max = fused_max;
     s->bulk = ctas_per_sm == 0;
     s->ctas_per_sm = ctas_per_sm == 0 ? 3 : ctas_per_sm;
+    return WALLACE_OK;
+}
+
+int wallace_server_set_restart(wallace_server_t *s, int64_t interval)
+{
+    if (!s || interval < 0 || !s->active.empty() || !s->inflight.empty())
+        return WALLACE_EINVAL;
+    s->restart = interval;
     return WALLACE_OK;
 }
 

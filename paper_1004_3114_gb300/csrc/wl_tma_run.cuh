@@ -174,13 +174,16 @@ __device__ __forceinline__ int wl_tma_tile_T(int L, int tcap)
 // pass (a grid of CTAs sharing one pool), each of at most tcap lane times;
 // the defaults take every tile at the ring's full length.  pre: the pass's
 // lane tables already built by wl_tma_tables (same L and T), else they are
-// built here in the ring's own table area.
+// built here in the ring's own table area.  SG, signs: the generator draws a
+// sign pattern each pass (matrix A D_k; bit i negates g_i); without SG the
+// kernel carries no sign code.
+template <bool SG = false>
 __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, int64_t Np, int L,
                                        const int32_t *alpha, const int64_t *gam, float c, float *o,
                                        int64_t w1, float mu, float sigma, float *smem, WlTmaRing &ring,
                                        WlDevState *st, uint64_t &lo, uint64_t &hi, uint32_t &bad,
                                        int tile0 = 0, int tstep = 1, int tcap = 1 << 30,
-                                       const int *pre = nullptr)
+                                       const int *pre = nullptr, uint32_t signs = 0)
 {
     using namespace wl_tma;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -394,8 +397,9 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                 // long lanes: each warp owns whole lanes, 64 lane times per
                 // step; lane l of tile k goes to warp (k L + l) mod 15, so when
                 // 15 does not divide L the extra lanes rotate over the warps
-                auto lane_loop = [&](auto shc) {
+                auto lane_loop = [&](auto shc, auto sgc) {
                     constexpr bool SH = decltype(shc)::value;
+                    constexpr bool SG = decltype(sgc)::value;
                     int l0 = warp - (int)(((uint32_t)tile * (uint32_t)L) % TM_CONS_WARPS);
                     l0 += l0 < 0 ? TM_CONS_WARPS : 0;
                     for (int l = l0; l < L; l += TM_CONS_WARPS) {
@@ -425,6 +429,10 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                                 }
                                 gv[i] = sdata[q];
                                 hv[i] = v2 ? sdata[q2] : 0.f;
+                                if (SG) {   // the pass's matrix is A D_k
+                                    gv[i] = wl_sgn(gv[i], signs, i);
+                                    hv[i] = wl_sgn(hv[i], signs, i);
+                                }
                             }
                             // both tuples' stores interleaved: each row gets
                             // 256 contiguous bytes per warp at once
@@ -457,9 +465,9 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                 };
                 if (T >= TR_LANE_MIN_T) {
                     if (shifted)
-                        lane_loop(std::true_type{});
+                        lane_loop(std::true_type{}, std::integral_constant<bool, SG>{});
                     else
-                        lane_loop(std::false_type{});
+                        lane_loop(std::false_type{}, std::integral_constant<bool, SG>{});
                 } else {
                     // short tiles: threads take (lane, time) pairs, times fastest
                     const int npairs = L * T;
@@ -476,7 +484,7 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                             const int f0 = info0[lb & 255];
                             int q = (lb >> 8) + (f0 & 3) + alpha[i] * t;
                             q += q >= info1[lb & 255] ? (f0 >> 2) : 0;
-                            gv[i] = sdata[q];
+                            gv[i] = SG ? wl_sgn(sdata[q], signs, i) : sdata[q];
                         }
                         emit(gv, (int64_t)jl + t0 + t, tl, emax);
                     }
@@ -530,6 +538,7 @@ static __device__ __noinline__ void wl_return_copy(const float *pool, int64_t N,
 // memory through the bulk-copy pass; a pass whose strides have lcm above
 // TR_LMAX takes the plain gather.  Returns the index of the buffer holding the
 // final pool.
+template <bool SG = false>
 __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
                                  WlTmaRing &ring)
 {
@@ -561,8 +570,9 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
         // the plain gather below writes its returned values itself
         const bool copy_back = tma && L >= TR_RETURN_COPY_L && o && w1 > 0;
         if (tma) {
-            wl_tma_pass_cta(src, dst, N, d.Np, L, alpha, gam, c, copy_back ? nullptr : o, copy_back ? 0 : w1,
-                            d.mu, d.sigma, smem, ring, d.st, lo, hi, bad);
+            wl_tma_pass_cta<SG>(src, dst, N, d.Np, L, alpha, gam, c, copy_back ? nullptr : o, copy_back ? 0 : w1,
+                                d.mu, d.sigma, smem, ring, d.st, lo, hi, bad, 0, 1, 1 << 30, nullptr,
+                                st->next.signs);
         } else {
             WlTileJob job;
             job.src = src;
@@ -574,6 +584,7 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
                 job.gam[i] = gam[i];
             }
             job.c = c;
+            job.signs = SG ? st->next.signs : 0u;
             job.out = o;
             job.w0 = 0;
             job.w1 = w1;

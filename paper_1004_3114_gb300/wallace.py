@@ -96,6 +96,9 @@ _SIGS = {
     "wallace_strerror": (C.c_char_p, [C.c_int]),
     "wallace_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double,
                                        C.c_void_p, C.POINTER(C.c_void_p)]),
+    "wallace_batch_create_ex": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                          C.c_void_p, C.POINTER(C.c_void_p)]),
+    "wallace_batch_set_restart": (C.c_int, [C.c_void_p, C.c_int64]),
     "wallace_batch_destroy": (None, [C.c_void_p]),
     "wallace_batch_run": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_float, C.c_float]),
     "wallace_batch_out_offset": (C.c_int64, [C.c_void_p, C.c_int, C.c_int64]),
@@ -112,6 +115,9 @@ _SIGS = {
     "wallace_server_destroy": (None, [C.c_void_p]),
     "wallace_server_set_tuning": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int]),
     "wallace_server_set_tick": (C.c_int, [_h, C.c_int64, C.c_int64]),
+    "wallace_server_set_restart": (C.c_int, [_h, C.c_int64]),
+    "wallace_server_create_ex": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                           C.c_int64, C.c_void_p, C.POINTER(C.c_void_p)]),
     "wallace_server_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_float, C.c_float,
                                         C.POINTER(C.c_int64)]),
     "wallace_server_progress": (C.c_int, [C.c_void_p]),
@@ -149,16 +155,16 @@ def header_functions() -> list[str]:
 class Batch:
     """Many generators advanced in one launch (wallace_batch_*)."""
 
-    def __init__(self, n: int, Ns, seeds, frac: float = 1.0, stream=None):
+    def __init__(self, n: int, Ns, seeds, frac: float = 1.0, stream=None, mode: int = FP32):
         Ns = np.ascontiguousarray(Ns, dtype=np.int64)
         seeds = np.ascontiguousarray(seeds, dtype=np.uint32)
         assert Ns.size == seeds.size
         self.n, self.count = n, int(Ns.size)
         self.N = Ns.copy()
         h = C.c_void_p()
-        rc = _lib.wallace_batch_create(self.count, n, Ns.ctypes.data, seeds.ctypes.data, frac,
-                                       _stream_ptr(stream), C.byref(h))
-        _check(rc, "wallace_batch_create")
+        rc = _lib.wallace_batch_create_ex(self.count, n, Ns.ctypes.data, seeds.ctypes.data, frac, mode,
+                                          _stream_ptr(stream), C.byref(h))
+        _check(rc, "wallace_batch_create_ex")
         self._h = h
         self.R = np.array([_lib.wallace_batch_returned_per_pass(h, s) for s in range(self.count)],
                           dtype=np.int64)
@@ -184,6 +190,9 @@ class Batch:
         ptr = C.c_void_p(out.data_ptr()) if out is not None else None
         return _check(_lib.wallace_batch_run(self._h, passes, ptr, mu, sigma), "wallace_batch_run",
                       allow=ECORRUPT)
+
+    def set_restart(self, interval: int) -> None:
+        _check(_lib.wallace_batch_set_restart(self._h, interval), "wallace_batch_set_restart")
 
     def sync(self) -> int:
         return _check(_lib.wallace_batch_sync(self._h), "wallace_batch_sync", allow=ECORRUPT)
@@ -218,13 +227,13 @@ class Batch:
 class Server:
     """Continuous-batching server over many client generators (wallace_server_*)."""
 
-    def __init__(self, n: int, Ns, seeds, frac: float, hbm_budget_bytes: int, stream=None):
+    def __init__(self, n: int, Ns, seeds, frac: float, hbm_budget_bytes: int, stream=None, mode: int = FP32):
         Ns = np.ascontiguousarray(Ns, dtype=np.int64)
         seeds = np.ascontiguousarray(seeds, dtype=np.uint32)
         h = C.c_void_p()
-        rc = _lib.wallace_server_create(int(Ns.size), n, Ns.ctypes.data, seeds.ctypes.data, frac,
-                                        int(hbm_budget_bytes), _stream_ptr(stream), C.byref(h))
-        _check(rc, "wallace_server_create")
+        rc = _lib.wallace_server_create_ex(int(Ns.size), n, Ns.ctypes.data, seeds.ctypes.data, frac, mode,
+                                           int(hbm_budget_bytes), _stream_ptr(stream), C.byref(h))
+        _check(rc, "wallace_server_create_ex")
         self._h = h
         self.n, self.N = n, Ns.copy()
 
@@ -242,6 +251,9 @@ class Server:
     def set_tuning(self, passes_per_tick: int, fused_max: int, ctas_per_sm: int) -> None:
         _check(_lib.wallace_server_set_tuning(self._h, passes_per_tick, fused_max, ctas_per_sm),
                "wallace_server_set_tuning")
+
+    def set_restart(self, interval: int) -> None:
+        _check(_lib.wallace_server_set_restart(self._h, interval), "wallace_server_set_restart")
 
     def set_tick(self, one_cta_max_values: int, values_per_tick: int) -> None:
         _check(_lib.wallace_server_set_tick(self._h, one_cta_max_values, values_per_tick),

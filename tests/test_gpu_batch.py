@@ -149,3 +149,36 @@ def test_config4_all_4096_generators_against_oracle(orc):
         bad = [s for s, ok in (f.result() for f in futs) if not ok]
     assert not bad, f"{len(bad)} of {Ns.size} generators differ, e.g. N = {[int(Ns[s]) for s in bad[:8]]}"
     b.close()
+
+
+@pytest.mark.parametrize("tuning", [(2, 2560, 2048), (0, 2560, 24576)])
+def test_batch_sign_patterns_chi_and_restarts(orc, tuning):
+    """wallace_batch_create_ex with WALLACE_MATRIX_SIGNS | WALLACE_CHI_WH (a
+    different matrix A D_k each pass, Section 3; Wilson-Hilferty's
+    chi-squared sample, Section 4) and wallace_batch_set_restart(4)
+    (Section 5): runs of 3, 2 and 5 passes cross the restart points after
+    passes 4 and 8.  Every returned value, pool, Q and sign pattern against
+    the oracle with the same options, on the per-thread and the bulk-copy
+    runners (shared-memory, lane-tiled and plain-gather pools)."""
+    mode = W.MATRIX_SIGNS | W.CHI_WH
+    Ns = [300, 2000, 9000, 30000, 65536, 5001, 100004, 16384, 45060, 21000]
+    seeds = list(range(51, 51 + len(Ns)))
+    b = W.Batch(4, Ns, seeds, 0.5, mode=mode)
+    b.set_tuning(*tuning)
+    b.set_restart(4)
+    oracles = [orc.Generator(4, int(N), int(sd), 0.5, mode=orc.FP32 | mode) for N, sd in zip(Ns, seeds)]
+    for o in oracles:
+        o.set_restart(4)
+    for P in (3, 2, 5):
+        out = torch.empty(b.out_size(P), dtype=torch.float32, device="cuda")
+        b.run(P, out, 0.25, 1.5)
+        got = out.cpu().numpy()
+        for s, o in enumerate(oracles):
+            off = b.out_offset(s, P)
+            ref = o.fill(P * int(b.R[s]), 0.25, 1.5)
+            assert np.array_equal(got[off:off + ref.size].view(np.uint32), ref.view(np.uint32)), (s, Ns[s], P)
+    for s, o in enumerate(oracles):
+        assert np.array_equal(b.pool(s).view(np.uint32), o.pool32().view(np.uint32)), (s, Ns[s])
+        gs, os_ = b.stats(s), o.stats()
+        assert gs.Q == os_.Q and gs.c32 == os_.c32 and gs.S == os_.S and gs.signs == os_.signs, (s, Ns[s])
+    assert b.sync() == 0

@@ -195,3 +195,31 @@ def test_server_every_pool_on_one_cta(orc, tick):
     for rid, (c, cnt, mu, sg) in zip(ids, reqs):
         ref = oracles[c].fill(cnt, np.float32(mu), np.float32(sg))
         assert np.array_equal(srv.result_host(rid).view(np.uint32), ref.view(np.uint32)), (c, int(Ns[c]), cnt)
+
+
+def test_server_sign_patterns_and_restarts(orc):
+    """wallace_server_create_ex with WALLACE_MATRIX_SIGNS (a matrix A D_k per
+    pass, Section 3) and wallace_server_set_restart(3) (Section 5): a client's
+    pool is refilled before the pass after every third of its passes, after
+    the values of its current pool still owed have gone out.  Every value
+    against the oracle with the same options."""
+    Ns = np.array([1 << 16, 100003, 3001, 300, 16387, 6000, 45060], dtype=np.int64)
+    seeds = np.arange(61, 61 + Ns.size, dtype=np.uint32)
+    srv = W.Server(4, Ns, seeds, 1 / 3, 1 << 30, mode=W.FP32 | W.MATRIX_SIGNS)
+    srv.set_tuning(2, 24576, 0)
+    srv.set_restart(3)
+    rng = np.random.default_rng(17)
+    reqs = [(int(rng.integers(0, Ns.size)), int(rng.integers(1, 300000)), float(rng.uniform(-2, 2)),
+             float(rng.uniform(0.5, 2))) for _ in range(50)]
+    ids = []
+    for k, (c, cnt, mu, sg) in enumerate(reqs):
+        ids.append(srv.submit(c, cnt, mu, sg))
+        if k % 3 == 1:
+            srv.progress()
+    srv.drain()
+    oracles = [orc.Generator(4, int(N), int(sd), 1 / 3, mode=orc.FP32 | orc.SIGNS) for N, sd in zip(Ns, seeds)]
+    for o in oracles:
+        o.set_restart(3)
+    for rid, (c, cnt, mu, sg) in zip(ids, reqs):
+        ref = oracles[c].fill(cnt, np.float32(mu), np.float32(sg))
+        assert np.array_equal(srv.result_host(rid).view(np.uint32), ref.view(np.uint32)), (c, int(Ns[c]), cnt)
