@@ -691,6 +691,7 @@ def variant_bench(steps: int = 2000, warmup: int = 5):
         ("n4_wilson_hilferty", 4, 1 << 24, 0.5, W.FP32 | W.CHI_WH, 0, A),
         ("n4_restart", 4, 1 << 24, 0.5, W.FP32, -1, A),
         ("n8", 8, 1 << 23, 0.5, W.FP32, 0, A),
+        ("n8_cluster", 8, 1 << 23, 0.5, W.FP32, 0, W.VARIANT_TILED_CLUSTER),
         ("n8_twophase", 8, 1 << 23, 0.5, W.FP32, 0, W.VARIANT_TWOPHASE),
         ("n8_N_3x2p21", 8, 3 << 21, 0.5, W.FP32, 0, A),
         ("n4_fp64_pool", 4, 1 << 24, 0.5, W.FP64POOL, 0, A),

@@ -105,6 +105,14 @@ typedef struct wallace wallace_t;
                                          where each CTA runs the end of pass (Eq. 3)
                                          itself; for pools that stay in L2 between
                                          passes                                        */
+#define WALLACE_VARIANT_TILED_CLUSTER 8 /* n = 8, the pools of the n = 8 bulk-copy pass
+                                         (binary32, N % 4 == 0, N coprime to 105) on
+                                         clusters of two CTAs: each holds four of the
+                                         eight sub-vectors of a 315-lane x 16-lane-time
+                                         tile and they exchange each tuple's half-sum
+                                         through distributed shared memory; rejected
+                                         (WALLACE_EINVAL) where the device cannot hold
+                                         a cluster of two such CTAs                    */
 
 /* Scalars of the most recent pass (or of the initial pool after create). */
 typedef struct {

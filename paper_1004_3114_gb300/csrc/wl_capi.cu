@@ -220,6 +220,11 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
             if (wl_tma8_return_kernel(a))
                 h->launches++;   // the returned values' kernel
         }
+        else if (v == WALLACE_VARIANT_TILED_CLUSTER && wl_tma8c_supported(h->n, h->N, fp64)) {
+            e = wl_launch_tma8c(a, h->sm_count, h->msigns, h->stream);
+            if (wl_tma8_return_kernel(a))
+                h->launches++;   // the returned values' kernel
+        }
         else if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_ASYNC ||
                   v == WALLACE_VARIANT_TILED_TMA) &&
                  wl_tiled_supported(h->n, h->N, fp64))
@@ -590,6 +595,10 @@ int wallace_set_variant(wallace_t *h, int variant)
         break;
     case WALLACE_VARIANT_L2RUN:
         if (!h->l2sync)
+            return WALLACE_EINVAL;
+        break;
+    case WALLACE_VARIANT_TILED_CLUSTER:
+        if (!wl_tma8c_supported(h->n, h->N, fp64))
             return WALLACE_EINVAL;
         break;
     default:

@@ -63,6 +63,15 @@ bool wl_tma8_supported(int n, int64_t N, int fp64);
 // kernel (streaming, after the pass): whether this pass takes it
 bool wl_tma8_return_kernel(const WlPassArgs &a);
 cudaError_t wl_launch_tma8(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream);
+// that second kernel alone: out[q - w0] = mu + sigma dst[q] over [w0, w1)
+cudaError_t wl_launch_t8_return(const WlPassArgs &a, int sm_count, cudaStream_t stream);
+
+// n = 8 on clusters of two CTAs, each with four of the eight sub-vectors of
+// a 315-lane x 16-lane-time tile (the same pools as wl_tma8_supported, when
+// a cluster of two fits the device); the grid is every resident cluster
+bool wl_tma8c_supported(int n, int64_t N, int fp64);
+int wl_tma8c_grid();
+cudaError_t wl_launch_tma8c(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream);
 
 // many passes of one n = 4 or 8 binary32 pool of at most 2^23 values in one
 // cooperative launch of `grid` CTAs (capped at what can be resident), with a

@@ -511,14 +511,22 @@ cudaError_t wl_launch_tma8(const WlPassArgs &a, int sm_count, int signs, cudaStr
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, p, rnu);
     if (e != cudaSuccess || !split)
         return e != cudaSuccess ? e : cudaGetLastError();
+    return wl_launch_t8_return(a, sm_count, stream);
+}
+
+cudaError_t wl_launch_t8_return(const WlPassArgs &a, int sm_count, cudaStream_t stream)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t rc = {};
     rc.gridDim = dim3(4 * sm_count);
     rc.blockDim = dim3(256);
     rc.stream = stream;
     rc.attrs = attr;
     rc.numAttrs = 1;
-    e = cudaLaunchKernelEx(&rc, t8_return_kernel, (const float *)a.dst, a.N, a.Np, a.n, a.w0, a.w1, (float *)a.out,
-                           (float)a.mu, (float)a.sigma);
+    cudaError_t e = cudaLaunchKernelEx(&rc, t8_return_kernel, (const float *)a.dst, a.N, a.Np, a.n, a.w0, a.w1,
+                                       (float *)a.out, (float)a.mu, (float)a.sigma);
     if (e != cudaSuccess)
         return e;
     return cudaGetLastError();

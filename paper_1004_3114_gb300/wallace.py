@@ -24,6 +24,7 @@ CHI_WH = 0x100   # mode flag: Wilson-Hilferty chi-squared sample
 MATRIX_SIGNS = 0x200   # mode flag: random sign pattern per pass (matrix A D_k)
 VARIANT_AUTO, VARIANT_GATHER, VARIANT_TILED, VARIANT_FUSED = 0, 1, 2, 3
 VARIANT_TILED_ASYNC, VARIANT_TILED_TMA, VARIANT_TWOPHASE, VARIANT_L2RUN = 4, 5, 6, 7
+VARIANT_TILED_CLUSTER = 8
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with "

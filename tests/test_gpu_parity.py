@@ -212,13 +212,16 @@ def test_twophase_pass_bit_exact(orc, n, N, frac, variant, mode):
     ((1 << 21) + 32, 0.5, 19),  # 32 * 65537: a 64 MB+ pool, returned values from a second kernel
     ((1 << 21) + 32, 0.3, 23),
 ])
-def test_tma8_pass_bit_exact(orc, N, frac, seed):
+@pytest.mark.parametrize("variant", [W.VARIANT_TILED, W.VARIANT_TILED_CLUSTER])
+def test_tma8_pass_bit_exact(orc, N, frac, seed, variant):
     """n = 8 with N coprime to 105: every pass has 315 lanes, and the tiled
-    variant runs the bulk-copy lane-tiled kernel (pools over 64 MB: then the
-    returned values' kernel).  Pools, returned values and state scalars
-    against the oracle, pass by pass, then fills that start mid-pass."""
+    variant runs the bulk-copy lane-tiled kernel, the cluster variant its
+    two-CTA form (tiles of 16 lane times, half-sums exchanged through
+    distributed shared memory); pools over 64 MB then take the returned
+    values' kernel.  Pools, returned values and state scalars against the
+    oracle, pass by pass, then fills that start mid-pass."""
     g = W.Wallace(8, N, seed, frac)
-    g.set_variant(W.VARIANT_TILED)
+    g.set_variant(variant)
     o = orc.Generator(8, N, seed, frac)
     before = g.stats().launches
     for k in range(5):
@@ -412,6 +415,7 @@ def test_restart_bit_exact(orc, n, N, variant, mode):
     (8, 5000, W.VARIANT_GATHER, W.FP32),
     (8, 20000, W.VARIANT_TWOPHASE, W.FP32),
     (8, 1 << 17, W.VARIANT_TILED_TMA, W.FP32),     # n = 8 bulk-copy kernel, with restarts
+    (8, 1 << 17, W.VARIANT_TILED_CLUSTER, W.FP32), # its two-CTA cluster form
     (8, 3001, W.VARIANT_FUSED, W.FP32),
     (4, 1024, W.VARIANT_AUTO, W.FP64POOL),
 ])

@@ -103,3 +103,81 @@ def test_lane_geometry_reads_eq1_positions_once(N):
         gamma = [rng.randrange(N) for _ in range(8)]
         seen = _tile_reads(N, alpha, gamma, c["T8_L"], c["T8_T"], c["T8_SPAN_PAD"])
         assert all(v == 1 for row in seen for v in row)
+
+
+# ---- the two-CTA cluster form (paper_1004_3114_gb300/csrc/wl_tiled_tma8c.cu):
+# each CTA stages four sub-vectors of a 315-lane x 16-lane-time tile
+
+SRC_C = os.path.join(os.path.dirname(__file__), "..", "paper_1004_3114_gb300", "csrc", "wl_tiled_tma8c.cu")
+
+
+def _consts_c():
+    text = open(SRC_C).read()
+    vals = {}
+    for name in ("C8_L", "C8_T", "C8_STAGES", "C8_MAXSPANS", "C8_SPAN_PAD", "C8_CONS_WARPS", "C8_PROD_WARPS"):
+        m = re.search(r"#define %s (\d+)" % name, text)
+        assert m, name
+        vals[name] = int(m.group(1))
+    return vals
+
+
+def test_cluster_halves_fit_the_stage_and_shared_memory():
+    c = _consts_c()
+    L, T, maxsp, pad = c["C8_L"], c["C8_T"], c["C8_MAXSPANS"], c["C8_SPAN_PAD"]
+    cand = orc.stride_candidates(8, 1 << 23)
+    sdw = 4 * L * T + pad * maxsp
+    worst = 0
+    # either CTA may hold any four of the drawn strides
+    for half in itertools.combinations(cand, 4):
+        nspans = sum(L // a for a in half)
+        assert nspans <= maxsp
+        worst = max(worst, nspans)
+        assert sum((L // a) * (T * a + pad) for a in half) <= sdw
+        assert all((T * a + pad) % 4 == 0 for a in half)
+        # lane-table entries: slot word << 9 | span, in 31 bits
+        assert sdw << 9 < 2 ** 31 and maxsp < 512
+    assert worst == maxsp
+    # the dynamic shared memory the kernel asks for, as its macros compute it
+    groups = (L + 1) // 2
+    ipw = -(-groups // c["C8_CONS_WARPS"])
+    sw = ((sdw + maxsp) + 31) & ~31
+    xw = c["C8_CONS_WARPS"] * 2 * ipw * 32
+    cw = (L + 1) + 4 * L + 3 * maxsp
+    assert 4 * (c["C8_STAGES"] * sw + xw + cw) <= 227 * 1024 - 2048
+    # every producer thread holds at most C8_KS spans
+    ks = -(-maxsp // (32 * c["C8_PROD_WARPS"]))
+    assert 32 * c["C8_PROD_WARPS"] * ks >= maxsp
+
+
+def test_cluster_items_cover_each_tile_once_in_both_ctas():
+    """Items of 2 lanes x 16 lane times, dealt to consumer warp
+    (tile groups + g) mod W; warp w of both CTAs takes items g0 + u W, u <
+    IPW, so the exchange slot (w, u, thread) names the same tuple in both."""
+    c = _consts_c()
+    L, W_ = c["C8_L"], c["C8_CONS_WARPS"]
+    groups = (L + 1) // 2
+    ipw = -(-groups // W_)
+    for tile in range(0, 97):
+        hits = [0] * groups
+        for w in range(W_):
+            g0 = (w - (tile * groups) % W_) % W_
+            for u in range(ipw):
+                g = g0 + u * W_
+                if g < groups:
+                    hits[g] += 1
+        assert hits == [1] * groups
+    # every lane of the tile is in exactly one item
+    lanes = sorted(2 * g + ll for g in range(groups) for ll in (0, 1) if 2 * g + ll < L)
+    assert lanes == list(range(L))
+
+
+@pytest.mark.parametrize("N", [16384, 16388, 20012])
+def test_cluster_lane_geometry_reads_eq1_positions_once(N):
+    c = _consts_c()
+    rng = random.Random(N + 1)
+    cand = orc.stride_candidates(8, N)
+    for trial in range(2):
+        alpha = list(cand[:8]) if trial == 0 else rng.sample(cand, 8)
+        gamma = [rng.randrange(N) for _ in range(8)]
+        seen = _tile_reads(N, alpha, gamma, c["C8_L"], c["C8_T"], c["C8_SPAN_PAD"])
+        assert all(v == 1 for row in seen for v in row)
