@@ -33,8 +33,16 @@
 // partner stored after reading slot (k - 2) mod 2 = k mod 2: two slots need
 // no second barrier.
 //
-// Tiles are assigned statically (cluster c takes tiles c, c + C, ...) so the
-// two CTAs of a cluster need no shared counter.  The sum of squares goes to
+// Tiles come from the generator's counter, one at a time, as in the one-CTA
+// kernel (clusters sweep neighbouring tiles together, which keeps the half
+// sectors at the ends of a lane's runs in L2 until their neighbours arrive;
+// a static deal let the clusters drift apart, and partial sectors then went
+// to DRAM as read-modify-writes).  CTA 0's producer draws the tile for ring
+// slot q = k mod 4 once its stage is free and sends the index to both CTAs
+// (4-byte st.async counted on each CTA's slot barrier, whose expected bytes
+// each CTA's producer posts).  Slot q is written again only for iteration
+// k + 4, after every warp of CTA 1 has passed iteration k + 1 (the half-sum
+// exchange keeps the CTAs' warps within one tile of each other).  The sum of squares goes to
 // the generator's accumulators from both CTAs and the last CTA of the grid
 // (by ticket) runs the end of pass, as in the other pass kernels.  Every wait
 // on an mbarrier is bounded (about a second): on expiry the CTA records
@@ -52,18 +60,21 @@
 #define C8_STAGES 2
 #define C8_MAXSPANS 248          /* a CTA's four sub-vectors: at most 105 + 63 + 45 + 35 spans */
 #define C8_SPAN_PAD 8            /* slot words past 16 alpha: alignment lead and a wrap's rounding */
-#define C8_CONS_WARPS 20
+#define C8_CONS_WARPS 16          /* 20 warps in all: 96 registers a thread (24: 80, spilling) */
 #define C8_PROD_WARPS 4
 #define C8_KS ((C8_MAXSPANS + 32 * C8_PROD_WARPS - 1) / (32 * C8_PROD_WARPS))
 #define C8_THREADS (32 * (C8_CONS_WARPS + C8_PROD_WARPS))
-#define C8_GROUPS ((C8_L + 1) / 2)   /* consumer items per tile: 2 lanes x 16 lane times */
-#define C8_IPW ((C8_GROUPS + C8_CONS_WARPS - 1) / C8_CONS_WARPS)   /* items per warp and tile */
-// a stage: the span slots of four sub-vectors (sum_i m_i (16 alpha_i + 8) <=
-// 4 * 315 * 16 + 8 * 248 words), then each span's alignment lead
+// consumer items: 4 lanes x 16 lane times, a thread taking lane times t and
+// t + 8 of one lane (one table read for both)
+#define C8_ITEMS ((C8_L + 3) / 4)
+#define C8_IPW ((C8_ITEMS + C8_CONS_WARPS - 1) / C8_CONS_WARPS)   /* items per warp and tile */
+#define C8_TPT (2 * C8_IPW)      /* tuples per thread and tile */
+// a stage: the span slots of four sub-vectors, sum_i m_i (16 alpha_i + 8) <=
+// 4 * 315 * 16 + 8 * 248 words
 #define C8_SDW (4 * C8_L * C8_T + C8_SPAN_PAD * C8_MAXSPANS)
-#define C8_SW (((C8_SDW + C8_MAXSPANS) + 31) & ~31)
-// exchange: per consumer warp two slots of IPW items x 32 half-sums
-#define C8_XW (C8_CONS_WARPS * 2 * C8_IPW * 32)
+#define C8_SW ((C8_SDW + 31) & ~31)
+// exchange: per consumer warp two slots of C8_TPT half-sums per thread
+#define C8_XW (C8_CONS_WARPS * 2 * C8_TPT * 32)
 // common area: J[L + 1], lane table [4][L], per span its start, slot and sub-vector
 #define C8_CW ((C8_L + 1) + 4 * C8_L + 3 * C8_MAXSPANS)
 #define C8_SMEM_BYTES (4 * (C8_STAGES * C8_SW + C8_XW + C8_CW))
@@ -71,7 +82,7 @@
 static_assert(C8_SMEM_BYTES <= 227 * 1024 - 2048, "stage ring exceeds shared memory");
 static_assert((C8_SW * 4) % 128 == 0, "stages must stay 128-byte aligned");
 static_assert(32 * C8_PROD_WARPS * C8_KS >= C8_MAXSPANS, "producer threads cannot hold every span");
-static_assert(C8_IPW % 4 == 0, "half-sums travel in groups of four");
+static_assert(C8_T == 16, "a thread takes lane times t and t + 8");
 
 namespace {
 
@@ -92,15 +103,31 @@ __device__ __forceinline__ uint32_t c8_mapa(uint32_t saddr, uint32_t rank)
     return r;
 }
 
-// 16 bytes into the partner's shared memory, counted as transaction bytes on
+// 8 bytes into the partner's shared memory, counted as transaction bytes on
 // the partner's mbarrier `rbar` when they land (no fence in this thread: a
 // release at cluster scope would first wait for every global store this
 // thread still has in flight)
-__device__ __forceinline__ void c8_st_async4(uint32_t raddr, float a, float b, float c, float d, uint32_t rbar)
+__device__ __forceinline__ void c8_st_async2(uint32_t raddr, float a, float b, uint32_t rbar)
 {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];\n" ::"r"(
-                     raddr),
-                 "f"(a), "f"(b), "f"(c), "f"(d), "r"(rbar)
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];\n" ::"r"(raddr),
+                 "f"(a), "f"(b), "r"(rbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void c8_st_async1(uint32_t raddr, int v, uint32_t rbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];\n" ::"r"(raddr), "r"(v),
+                 "r"(rbar)
+                 : "memory");
+}
+
+// the expected bytes of the partner's half-sums: orders nothing of this
+// thread's, so relaxed
+__device__ __forceinline__ void c8_arrive_expect_tx_relaxed(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(
+                     bar),
+                 "r"(bytes)
                  : "memory");
 }
 
@@ -111,24 +138,66 @@ __device__ __forceinline__ void c8_arrive_expect_tx(uint32_t bar, uint32_t bytes
                  : "memory");
 }
 
-// bounded wait on a local mbarrier phase, acquiring at cluster scope the
-// partner's stores counted on it
-__device__ __forceinline__ bool c8_wait_cluster(uint32_t bar, uint32_t parity)
+#define C8_SUSPEND_NS 20000u   /* longest suspension of one try_wait */
+
+// one try_wait on a phase of a local mbarrier; CL: acquire at cluster scope
+// (what the partner CTA's stores counted on it wrote), else at CTA scope
+template <bool CL>
+__device__ __forceinline__ bool c8_try(uint32_t bar, uint32_t parity, uint32_t ns)
 {
-    const long long start = clock64();
-    while (true) {
-        uint32_t done;
+    uint32_t done;
+    if (CL)
         asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                     "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity), "r"(ns)
+                     : "memory");
+    else
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity), "r"(ns)
+                     : "memory");
+    return done != 0;
+}
+
+// whether a phase of a local mbarrier has completed, without waiting
+template <bool CL>
+__device__ __forceinline__ bool c8_test(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    if (CL)
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}\n"
                      : "=r"(done)
                      : "r"(bar), "r"(parity)
                      : "memory");
-        if (done)
-            return true;
+    else
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+    return done != 0;
+}
+
+// bounded wait on a phase of a local mbarrier: true once it has completed,
+// false after about a second.  A phase already complete costs one try_wait;
+// otherwise each try_wait may suspend the thread until the phase completes.
+template <bool CL>
+__device__ __forceinline__ bool c8_wait(uint32_t bar, uint32_t parity)
+{
+    if (c8_test<CL>(bar, parity))
+        return true;
+    const long long start = clock64();
+    while (!c8_try<CL>(bar, parity, C8_SUSPEND_NS))
         if (clock64() - start > TM_WAIT_CYCLES)
             return false;
-    }
+    return true;
 }
 
 __device__ __forceinline__ void c8_cluster_sync()
@@ -148,8 +217,11 @@ __device__ __forceinline__ float c8_wait_prev(WlDevState *st, volatile float *s_
     return *s_c;
 }
 
-// SG: the generator draws a sign pattern each pass (matrix A D_k).
-template <bool SG>
+// SG: the generator draws a sign pattern each pass (matrix A D_k).  RET: the
+// pass writes returned values (pools up to 64 MB; larger ones leave them to
+// the streaming kernel), so passes without them carry none of their index
+// arithmetic.
+template <bool SG, bool RET>
 __global__ void __launch_bounds__(C8_THREADS, 1) tma8c_kernel(WlPassArgs a, double rnu)
 {
     extern __shared__ __align__(128) float smem[];
@@ -157,6 +229,9 @@ __global__ void __launch_bounds__(C8_THREADS, 1) tma8c_kernel(WlPassArgs a, doub
     __shared__ __align__(8) uint64_t bar_empty[C8_STAGES];
     // per consumer warp and exchange slot: the partner warp's half-sums are here
     __shared__ __align__(8) uint64_t bar_x[C8_CONS_WARPS][2];
+    // the tile of ring slot q (iterations q, q + 4, ...), drawn by CTA 0 of the cluster
+    __shared__ __align__(8) uint64_t bar_tile[4];
+    __shared__ volatile int s_tile[4];
     __shared__ uint64_t red[3 * (C8_THREADS / 32 + 1)];
     __shared__ volatile int s_abort;
     __shared__ int64_t s_gam[8];
@@ -170,7 +245,6 @@ __global__ void __launch_bounds__(C8_THREADS, 1) tma8c_kernel(WlPassArgs a, doub
     const int64_t N = a.N, Np = a.Np;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int rank = (int)c8_rank();          // this CTA's half: sub-vectors 4 rank .. 4 rank + 3
-    const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
     if (warp == 0) {
         const WlStrides *cur = &st->ahead[a.pass & 1];
         if (lane < 8)
@@ -189,6 +263,8 @@ __global__ void __launch_bounds__(C8_THREADS, 1) tma8c_kernel(WlPassArgs a, doub
             mbar_init(smem_u32(&bar_x[w][0]), 1);
             mbar_init(smem_u32(&bar_x[w][1]), 1);
         }
+        for (int q = 0; q < 4; q++)
+            mbar_init(smem_u32(&bar_tile[q]), 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -252,11 +328,11 @@ __global__ void __launch_bounds__(C8_THREADS, 1) tma8c_kernel(WlPassArgs a, doub
         }
     } else {
         float *stage0 = smem;
-        float *xbuf = smem + C8_STAGES * C8_SW;   // [warp][slot][item][32]: the partner's half-sums
+        float *xbuf = smem + C8_STAGES * C8_SW;   // [warp][slot][group][thread][4]: the partner's half-sums
         int *common = (int *)(xbuf + C8_XW);
         int *J = common;                          // [L + 1] lane starts
-        int *lanetab = J + (C8_L + 1);            // [4][L]: slot word of the lane's first value << 9 | span
-        int *spanC = lanetab + 4 * C8_L;          // [spans]: ceil(p N / m_i)
+        int *offt = J + (C8_L + 1);               // [4][L]: stage word of the lane's first value
+        int *spanC = offt + 4 * C8_L;             // [spans]: ceil(p N / m_i)
         int *spanOff = spanC + C8_MAXSPANS;       // [spans]: slot offset in a stage, words
         int *spanSub = spanOff + C8_MAXSPANS;     // [spans]: sub-vector 0..3 of this CTA
         int slot0[4];
@@ -290,7 +366,11 @@ __global__ void __launch_bounds__(C8_THREADS, 1) tma8c_kernel(WlPassArgs a, doub
         }
         __syncthreads();
         // lane l of sub-vector i reads span p = l mod m_i from offset
-        // r = alpha_i J_l - floor(l / m_i) N - spanC in [0, alpha_i)
+        // r = alpha_i J_l - floor(l / m_i) N - spanC in [0, alpha_i), after
+        // the span's alignment lead: the copy of the span of tile k starts at
+        // s = (spanC + alpha_i 16 k + gamma_i) mod N rounded down to a multiple
+        // of 4, and with 16 k and N multiples of 4 its lead s mod 4 =
+        // (spanC + gamma_i) mod 4 is the same in every tile
         for (int e = tid; e < 4 * C8_L; e += C8_THREADS) {
             const int i = e / C8_L, l = e - i * C8_L;
             int mi = 1, al = 1, s0 = 0;
@@ -304,34 +384,52 @@ __global__ void __launch_bounds__(C8_THREADS, 1) tma8c_kernel(WlPassArgs a, doub
             const int w = l / mi, p = l - w * mi;
             const int sp = s0 + p;
             const int64_t r = (int64_t)al * J[l] - (int64_t)w * N - spanC[sp];
-            lanetab[e] = ((spanOff[sp] + (int)r) << 9) | sp;
+            const int lead = (int)(((int64_t)spanC[sp] + s_gam[4 * rank + i]) & 3);
+            offt[e] = spanOff[sp] + lead + (int)r;
         }
         __syncthreads();
         c = c8_wait_prev(st, &s_c);
         const int maxlen = (N32 + C8_L - 1) / C8_L;
+        const int minlen = N32 / C8_L;   // every lane has minlen or maxlen lane times
         const int ntiles = (maxlen + C8_T - 1) / C8_T;
 
         if (warp >= C8_CONS_WARPS) {
             // ---------------- producer warps ----------------
-            // tiles cid, cid + C, ... (C clusters); both CTAs take the same
             const int pw = warp - C8_CONS_WARPS;
             const int pt = pw + C8_PROD_WARPS * lane;   // spans pt + 32 PW q, q < KS
             const uint32_t stage_base = smem_u32(stage0);
             int issued0 = 0, issued1 = 0;   // per stage: uses issued (phase parity of the last)
             for (int it = 0;; it++) {
-                const int s = it & 1, k = it >> 1;
-                const int tile = cid + it * ncl;
-                if (tile >= ntiles || s_abort)
+                const int s = it & 1, k = it >> 1, ts = it & 3;
+                if (s_abort)
                     break;
-                if (k > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (uint32_t)((k - 1) & 1))) {
+                if (k > 0 && !c8_wait<false>(smem_u32(&bar_empty[s]), (uint32_t)((k - 1) & 1))) {
                     s_abort = 1;
                     atomicOr(&st->status, WL_ETIMEOUT);
                     break;
                 }
+                // the stage is free in this CTA: CTA 0 draws the next tile from
+                // the generator's counter and sends it to both CTAs
+                if (pw == 0 && lane == 0) {
+                    c8_arrive_expect_tx(smem_u32(&bar_tile[ts]), 4u);
+                    if (rank == 0) {
+                        const int t = (int)atomicAdd(&st->tile_ctr, 1u);
+                        const uint32_t a_t = smem_u32((const void *)&s_tile[ts]), a_b = smem_u32(&bar_tile[ts]);
+                        c8_st_async1(c8_mapa(a_t, 0u), t, c8_mapa(a_b, 0u));
+                        c8_st_async1(c8_mapa(a_t, 1u), t, c8_mapa(a_b, 1u));
+                    }
+                }
+                if (!c8_wait<true>(smem_u32(&bar_tile[ts]), (uint32_t)((it >> 2) & 1))) {
+                    s_abort = 1;
+                    atomicOr(&st->status, WL_ETIMEOUT);
+                    break;
+                }
+                const int tile = s_tile[ts];
+                if (tile >= ntiles)
+                    break;
                 const uint32_t full = smem_u32(&bar_full[s]);
                 const int t0 = tile * C8_T;
                 const int Tt = min(C8_T, maxlen - t0);
-                int *lead = (int *)(stage0 + s * C8_SW + C8_SDW);
                 const uint32_t sbase = stage_base + 4u * (uint32_t)(s * C8_SW);
                 int sa[C8_KS], sl[C8_KS], sub[C8_KS], soff[C8_KS];
                 uint32_t total = 0;
@@ -355,7 +453,6 @@ __global__ void __launch_bounds__(C8_THREADS, 1) tma8c_kernel(WlPassArgs a, doub
                         sub[q] = 4 * rank + i;
                         soff[q] = spanOff[sp];
                         const int as = sa[q] & ~3;
-                        lead[sp] = sa[q] - as;
                         total += sa[q] + sl[q] > N32
                                      ? 4u * (uint32_t)(N32 - as) + 4u * (uint32_t)((sa[q] + sl[q] - N32 + 3) & ~3)
                                      : 16u * (uint32_t)((sa[q] - as + sl[q] + 3) >> 2);
@@ -386,115 +483,138 @@ __global__ void __launch_bounds__(C8_THREADS, 1) tma8c_kernel(WlPassArgs a, doub
                 (s ? issued1 : issued0) = k + 1;
             }
             // copies still in flight must land before the CTA leaves
-            if (issued0 > 0 && !mbar_wait(smem_u32(&bar_full[0]), (uint32_t)((issued0 - 1) & 1)))
+            if (issued0 > 0 && !c8_wait<false>(smem_u32(&bar_full[0]), (uint32_t)((issued0 - 1) & 1)))
                 atomicOr(&st->status, WL_ETIMEOUT);
-            if (issued1 > 0 && !mbar_wait(smem_u32(&bar_full[1]), (uint32_t)((issued1 - 1) & 1)))
+            if (issued1 > 0 && !c8_wait<false>(smem_u32(&bar_full[1]), (uint32_t)((issued1 - 1) & 1)))
                 atomicOr(&st->status, WL_ETIMEOUT);
         } else {
             // ---------------- consumer warps ----------------
-            uint32_t all_ret = 0, part_ret = 0;   // this CTA's rows returned whole, in part
+            // a thread's two tuples: lane time tt of lanes 4 g + ll and
+            // 4 g + 2 + ll of item g (a half-warp stores a lane's 16 values:
+            // 64 contiguous bytes per row)
+            const int ll = lane >> 4, tt = lane & 15;
+            int at[4];
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const int64_t q0 = (4 * rank + i) * N, q1 = q0 + N;
-                if (q1 > w0 && q0 < w1) {
-                    if (q0 >= w0 && q1 <= w1)
-                        all_ret |= 1u << i;
-                    else
-                        part_ret |= 1u << i;
-                }
-            }
+            for (int i = 0; i < 4; i++)
+                at[i] = alpha[i] * tt;
             float *drow = dst + (int64_t)(4 * rank) * Np;
-            const int64_t qrow = (int64_t)(4 * rank) * N - w0;   // out index of row 4 rank, j = 0
-            const int ll = lane >> 4, tt = lane & 15;   // lane of the item, lane time
+            const int64_t qrow = (int64_t)(4 * rank) * N - w0, W = w1 - w0;   // out index of row 4 rank, j = 0
             const uint32_t xpart = c8_mapa(smem_u32(xbuf), (uint32_t)(rank ^ 1));
             const uint32_t bxpart = c8_mapa(smem_u32(&bar_x[warp][0]), (uint32_t)(rank ^ 1));
             const uint32_t bxown = smem_u32(&bar_x[warp][0]);
             uint32_t emax = 0;
             for (int it = 0;; it++) {
-                const int s = it & 1, k = it >> 1;
-                const int tile = cid + it * ncl;
-                if (tile >= ntiles || s_abort)
+                const int s = it & 1, k = it >> 1, par = it & 1;
+                if (s_abort)
                     break;
-                if (!mbar_wait(smem_u32(&bar_full[s]), (uint32_t)(k & 1))) {
+                if (!c8_wait<true>(smem_u32(&bar_tile[it & 3]), (uint32_t)((it >> 2) & 1))) {
+                    s_abort = 1;
+                    atomicOr(&st->status, WL_ETIMEOUT);
+                    break;
+                }
+                const int tile = s_tile[it & 3];
+                if (tile >= ntiles)
+                    break;
+                if (!c8_wait<false>(smem_u32(&bar_full[s]), (uint32_t)(k & 1))) {
                     s_abort = 1;
                     atomicOr(&st->status, WL_ETIMEOUT);
                     break;
                 }
                 const int t0 = tile * C8_T;
                 const int Tt = min(C8_T, maxlen - t0);
+                const bool full = t0 + C8_T <= minlen;   // every tuple of the tile exists
                 const float *sdata = stage0 + s * C8_SW;
-                const int *lead = (const int *)(sdata + C8_SDW);
-                // item g of tile k goes to warp (k groups + g) mod C8_CONS_WARPS,
+                // item g of tile k goes to warp (k items + g) mod C8_CONS_WARPS,
                 // in both CTAs alike
-                int g0 = warp - (int)(((uint32_t)tile * (uint32_t)C8_GROUPS) % C8_CONS_WARPS);
+                int g0 = warp - (int)(((uint32_t)tile * (uint32_t)C8_ITEMS) % C8_CONS_WARPS);
                 g0 += g0 < 0 ? C8_CONS_WARPS : 0;
-                // phase 1: this CTA's four values of every tuple and their sum
-                float xv[C8_IPW][4];
+                // which tuples exist: items past the last, the lane past L in
+                // the last item and, in the last tiles, lane times past a
+                // lane's end; lanes past L read lane L - 1 (unused), so the
+                // loads below need no branch
+                int lcs[C8_TPT];   // lane of tuple v = 2 u + h
                 uint32_t ok = 0;
-                // slot layout: [u / 4][thread][u mod 4], 16 bytes per thread and group
-                const uint32_t xslot = xpart + 4u * (uint32_t)(((warp * 2 + (it & 1)) * C8_IPW) * 32 + 4 * lane);
-                const uint32_t xbar = bxpart + 8u * (uint32_t)(it & 1);
-                float hq[4];
+#pragma unroll
+                for (int v = 0; v < C8_TPT; v++) {
+                    const int g = g0 + (v >> 1) * C8_CONS_WARPS;
+                    const int l = 4 * g + 2 * (v & 1) + ll;
+                    lcs[v] = min(l, C8_L - 1);
+                    ok |= (g < C8_ITEMS && l < C8_L ? 1u : 0u) << v;
+                }
+                if (!full) {
+#pragma unroll
+                    for (int v = 0; v < C8_TPT; v++) {
+                        const int lim = min(Tt, J[lcs[v] + 1] - J[lcs[v]] - t0);
+                        ok &= ~((tt < lim ? 0u : 1u) << v);
+                    }
+                }
+                // phase 1: this CTA's four values of each tuple and their sum
+                float x0[C8_IPW][4], x1[C8_IPW][4];
+                // slot layout: [item][thread][2], the thread's two tuples
+                const uint32_t xslot = xpart + 4u * (uint32_t)((warp * 2 + par) * C8_TPT * 32 + 2 * lane);
+                const uint32_t xbar = bxpart + 8u * (uint32_t)par;
 #pragma unroll
                 for (int u = 0; u < C8_IPW; u++) {
-                    const int g = g0 + u * C8_CONS_WARPS;
-                    const int l = 2 * g + ll;
-                    float hs = 0.0f;
-                    if (g < C8_GROUPS && l < C8_L) {
-                        const int jl = J[l];
-                        if (tt < min(Tt, J[l + 1] - jl - t0)) {
-                            ok |= 1u << u;
 #pragma unroll
-                            for (int i = 0; i < 4; i++) {
-                                const int lb = lanetab[i * C8_L + l];
-                                float x = sdata[(lb >> 9) + lead[lb & 511] + alpha[i] * tt];
-                                if (SG)   // the pass's matrix is A D_k
-                                    x = wl_sgn(x, signs, 4 * rank + i);
-                                xv[u][i] = x;
-                            }
-                            hs = __fadd_rn(__fadd_rn(xv[u][0], xv[u][1]), __fadd_rn(xv[u][2], xv[u][3]));
+                    for (int i = 0; i < 4; i++) {
+                        float v0 = sdata[offt[i * C8_L + lcs[2 * u]] + at[i]];
+                        float v1 = sdata[offt[i * C8_L + lcs[2 * u + 1]] + at[i]];
+                        if (SG) {   // the pass's matrix is A D_k
+                            v0 = wl_sgn(v0, signs, 4 * rank + i);
+                            v1 = wl_sgn(v1, signs, 4 * rank + i);
                         }
+                        x0[u][i] = v0;
+                        x1[u][i] = v1;
                     }
-                    hq[u & 3] = hs;
-                    if ((u & 3) == 3)   // every group is sent, used or not: 1 KB per warp and tile
-                        c8_st_async4(xslot + 512u * (uint32_t)(u >> 2), hq[0], hq[1], hq[2], hq[3], xbar);
                 }
-                // stage free; expect the partner warp's 1 KB of half-sums
+#pragma unroll
+                for (int u = 0; u < C8_IPW; u++)   // every item is sent, used or not: the slot's bytes per warp and tile
+                    c8_st_async2(xslot + 256u * (uint32_t)u,
+                                 __fadd_rn(__fadd_rn(x0[u][0], x0[u][1]), __fadd_rn(x0[u][2], x0[u][3])),
+                                 __fadd_rn(__fadd_rn(x1[u][0], x1[u][1]), __fadd_rn(x1[u][2], x1[u][3])), xbar);
+                // stage free; expect the partner warp's half-sums
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive(smem_u32(&bar_empty[s]));
-                    c8_arrive_expect_tx(bxown + 8u * (uint32_t)(it & 1), 32u * 4u * C8_IPW);
+                    c8_arrive_expect_tx_relaxed(bxown + 8u * (uint32_t)par, 4u * 32u * C8_TPT);
                 }
-                if (!c8_wait_cluster(bxown + 8u * (uint32_t)(it & 1), (uint32_t)((it >> 1) & 1))) {
+                if (!c8_wait<true>(bxown + 8u * (uint32_t)par, (uint32_t)((it >> 1) & 1))) {
                     s_abort = 1;
                     atomicOr(&st->status, WL_ETIMEOUT);
                     break;
                 }
-                // phase 2: h = (ab + de) / 4 and this CTA's four outputs
-                const float *xown = xbuf + ((warp * 2 + (it & 1)) * C8_IPW) * 32 + 4 * lane;
-                float4 xo;
-                uint64_t tl = 0;   // at most 8 items x 4 terms per thread, each below 2^48
+                // phase 2: h = (ab + de) / 4 and this CTA's four outputs per tuple
+                const float *xown = xbuf + (warp * 2 + par) * C8_TPT * 32 + 2 * lane;
+                uint64_t tl = 0;   // at most 8 tuples x 4 terms per thread, each below 2^48
 #pragma unroll
                 for (int u = 0; u < C8_IPW; u++) {
-                    if ((u & 3) == 0)   // the partner's half-sums of items u .. u + 3
-                        xo = *(const float4 *)(xown + 128 * (u >> 2));
-                    if (!((ok >> u) & 1u))
-                        continue;
-                    // this CTA's half-sum again (three adds instead of a register per item)
-                    const float hs = __fadd_rn(__fadd_rn(xv[u][0], xv[u][1]), __fadd_rn(xv[u][2], xv[u][3]));
-                    const float o = (u & 3) == 0 ? xo.x : (u & 3) == 1 ? xo.y : (u & 3) == 2 ? xo.z : xo.w;
-                    const float h = __fmul_rn(__fadd_rn(hs, o), 0.25f);
-                    const int j = J[2 * (g0 + u * C8_CONS_WARPS) + ll] + t0 + tt;
+                    const float2 xo = *(const float2 *)(xown + 64 * u);   // the partner's half-sums
+                    const int j0 = J[lcs[2 * u]] + t0 + tt, j1 = J[lcs[2 * u + 1]] + t0 + tt;
+                    const bool ok0 = (ok >> (2 * u)) & 1u, ok1 = (ok >> (2 * u + 1)) & 1u;
+                    // this CTA's half-sums again (three adds instead of registers)
+                    const float s0 = __fadd_rn(__fadd_rn(x0[u][0], x0[u][1]), __fadd_rn(x0[u][2], x0[u][3]));
+                    const float s1 = __fadd_rn(__fadd_rn(x1[u][0], x1[u][1]), __fadd_rn(x1[u][2], x1[u][3]));
+                    const float h0 = __fmul_rn(__fadd_rn(s0, xo.x), 0.25f);
+                    const float h1 = __fmul_rn(__fadd_rn(s1, xo.y), 0.25f);
 #pragma unroll
                     for (int i = 0; i < 4; i++) {
-                        const float y = __fmul_rn(__fsub_rn(h, xv[u][i]), c);
-                        drow[i * Np + j] = y;
-                        tl += term32(y, emax);
-                        const int64_t q = qrow + i * N + j;   // out index
-                        if ((all_ret >> i) & 1u)
-                            out[q] = __fadd_rn(mu, __fmul_rn(sigma, y));
-                        else if (((part_ret >> i) & 1u) && q >= 0 && q < w1 - w0)
-                            out[q] = __fadd_rn(mu, __fmul_rn(sigma, y));
+                        const float y0 = __fmul_rn(__fsub_rn(h0, x0[u][i]), c);
+                        const float y1 = __fmul_rn(__fsub_rn(h1, x1[u][i]), c);
+                        float *p = drow + i * Np;
+                        if (ok0)
+                            p[j0] = y0;
+                        if (ok1)
+                            p[j1] = y1;
+                        // a missing tuple counts as 0 (term32(0) = 0, exponent 0)
+                        tl += term32(ok0 ? y0 : 0.0f, emax);
+                        tl += term32(ok1 ? y1 : 0.0f, emax);
+                        if (RET) {
+                            const int64_t q0 = qrow + i * N + j0, q1 = qrow + i * N + j1;   // out indices
+                            if (ok0 && q0 >= 0 && q0 < W)
+                                out[q0] = __fadd_rn(mu, __fmul_rn(sigma, y0));
+                            if (ok1 && q1 >= 0 && q1 < W)
+                                out[q1] = __fadd_rn(mu, __fmul_rn(sigma, y1));
+                        }
                     }
                 }
                 lo += tl;
@@ -512,18 +632,35 @@ __global__ void __launch_bounds__(C8_THREADS, 1) tma8c_kernel(WlPassArgs a, doub
         wl_finalise_cta(st, 8, N, a.nu, rnu, &dst[wl_last_phys(8, N, Np)], SG ? 1 : 0);
 }
 
-bool g_tma8c_configured[2] = {false, false};
-int g_tma8c_clusters[2] = {0, 0};
+bool g_tma8c_configured[4] = {false, false, false, false};
+int g_tma8c_clusters[4] = {0, 0, 0, 0};
+
+using C8Kernel = void (*)(WlPassArgs, double);
+
+C8Kernel c8_kernel(int which)
+{
+    switch (which) {
+    case 0:
+        return tma8c_kernel<false, false>;
+    case 1:
+        return tma8c_kernel<false, true>;
+    case 2:
+        return tma8c_kernel<true, false>;
+    default:
+        return tma8c_kernel<true, true>;
+    }
+}
 
 } // namespace
 
 // Set the kernel's shared-memory size once and find how many clusters of
 // two can be resident at once (0 when none can: the kernel is then not used).
+// which = 2 signs + returned values in the pass.
 static int c8_configure(int which)
 {
     if (g_tma8c_configured[which])
         return g_tma8c_clusters[which];
-    auto kern = which ? tma8c_kernel<true> : tma8c_kernel<false>;
+    const C8Kernel kern = c8_kernel(which);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C8_SMEM_BYTES) != cudaSuccess) {
         cudaGetLastError();
         g_tma8c_configured[which] = true;
@@ -552,23 +689,35 @@ static int c8_configure(int which)
 
 bool wl_tma8c_supported(int n, int64_t N, int fp64)
 {
-    return wl_tma8_supported(n, N, fp64) && c8_configure(0) > 0 && c8_configure(1) > 0;
+    if (!wl_tma8_supported(n, N, fp64))
+        return false;
+    for (int w = 0; w < 4; w++)
+        if (c8_configure(w) <= 0)
+            return false;
+    return true;
 }
 
 int wl_tma8c_grid()
 {
-    return 2 * min(c8_configure(0), c8_configure(1));
+    int nc = c8_configure(0);
+    for (int w = 1; w < 4; w++)
+        nc = min(nc, c8_configure(w));
+    return 2 * nc;
 }
 
 cudaError_t wl_launch_tma8c(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream)
 {
-    const int which = signs ? 1 : 0;
+    // large pools: the returned values follow in the streaming kernel
+    const bool split = wl_tma8_return_kernel(a);
+    WlPassArgs p = a;
+    if (split)
+        p.w0 = p.w1 = 0;
+    const int which = (signs ? 2 : 0) + (p.w1 > p.w0 ? 1 : 0);
     const int nc = c8_configure(which);
     if (nc <= 0)
         return cudaErrorNotSupported;
-    auto kern = which ? tma8c_kernel<true> : tma8c_kernel<false>;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * nc);   // every cluster resident: tiles are dealt statically
+    cfg.gridDim = dim3(2 * nc);   // every cluster resident
     cfg.blockDim = dim3(C8_THREADS);
     cfg.dynamicSmemBytes = C8_SMEM_BYTES;
     cfg.stream = stream;
@@ -582,12 +731,7 @@ cudaError_t wl_launch_tma8c(const WlPassArgs &a, int sm_count, int signs, cudaSt
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     const double rnu = sqrt(2.0 * (double)a.nu - 1.0);   // IEEE square root: correctly rounded
-    // large pools: the returned values follow in the streaming kernel
-    const bool split = wl_tma8_return_kernel(a);
-    WlPassArgs p = a;
-    if (split)
-        p.w0 = p.w1 = 0;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, p, rnu);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, c8_kernel(which), p, rnu);
     if (e != cudaSuccess || !split)
         return e != cudaSuccess ? e : cudaGetLastError();
     return wl_launch_t8_return(a, sm_count, stream);

@@ -82,6 +82,8 @@ def _tile_reads(N, alpha, gamma, L, T, pad):
                 assert 0 <= r < a
                 start = (C + a * t0 + gamma[i]) % N      # span p of this tile
                 lead = start % 4
+                # T % 4 == 0 and N % 4 == 0: the lead is the same in every tile
+                assert lead == (C + gamma[i]) % 4
                 words = 4 * ((lead + a * Tt + 3) // 4)
                 assert words <= T * a + pad
                 for t in range(min(Tt, J[l + 1] - J[l] - t0)):
@@ -138,37 +140,42 @@ def test_cluster_halves_fit_the_stage_and_shared_memory():
         assert sdw << 9 < 2 ** 31 and maxsp < 512
     assert worst == maxsp
     # the dynamic shared memory the kernel asks for, as its macros compute it
-    groups = (L + 1) // 2
-    ipw = -(-groups // c["C8_CONS_WARPS"])
-    sw = ((sdw + maxsp) + 31) & ~31
-    xw = c["C8_CONS_WARPS"] * 2 * ipw * 32
+    items = (L + 3) // 4
+    ipw = -(-items // c["C8_CONS_WARPS"])
+    sw = (sdw + 31) & ~31
+    xw = c["C8_CONS_WARPS"] * 2 * (2 * ipw) * 32
     cw = (L + 1) + 4 * L + 3 * maxsp
     assert 4 * (c["C8_STAGES"] * sw + xw + cw) <= 227 * 1024 - 2048
+    # a thread reads lane times t and t + 8 of its lane: both inside the slot
+    assert all(3 + (a - 1) + 15 * a < T * a + pad for a in cand)
     # every producer thread holds at most C8_KS spans
     ks = -(-maxsp // (32 * c["C8_PROD_WARPS"]))
     assert 32 * c["C8_PROD_WARPS"] * ks >= maxsp
 
 
 def test_cluster_items_cover_each_tile_once_in_both_ctas():
-    """Items of 2 lanes x 16 lane times, dealt to consumer warp
-    (tile groups + g) mod W; warp w of both CTAs takes items g0 + u W, u <
-    IPW, so the exchange slot (w, u, thread) names the same tuple in both."""
+    """Items of 4 lanes x 16 lane times (a thread: lane time t of lanes
+    4 g + h and 4 g + 2 + h, a half-warp one lane's 16 lane times), dealt to
+    consumer warp (tile items + g) mod W; warp w of both CTAs takes items
+    g0 + u W, u < IPW, so the exchange slot (w, u, thread) names the same two
+    tuples in both."""
     c = _consts_c()
-    L, W_ = c["C8_L"], c["C8_CONS_WARPS"]
-    groups = (L + 1) // 2
-    ipw = -(-groups // W_)
+    L, W_, T = c["C8_L"], c["C8_CONS_WARPS"], c["C8_T"]
+    items = (L + 3) // 4
+    ipw = -(-items // W_)
     for tile in range(0, 97):
-        hits = [0] * groups
+        hits = [0] * items
         for w in range(W_):
-            g0 = (w - (tile * groups) % W_) % W_
+            g0 = (w - (tile * items) % W_) % W_
             for u in range(ipw):
                 g = g0 + u * W_
-                if g < groups:
+                if g < items:
                     hits[g] += 1
-        assert hits == [1] * groups
-    # every lane of the tile is in exactly one item
-    lanes = sorted(2 * g + ll for g in range(groups) for ll in (0, 1) if 2 * g + ll < L)
-    assert lanes == list(range(L))
+        assert hits == [1] * items
+    # every (lane, lane time) of a tile is one thread's, once
+    seen = sorted((4 * g + 2 * h + (th >> 4), th & 15)
+                  for g in range(items) for th in range(32) for h in (0, 1) if 4 * g + 2 * h + (th >> 4) < L)
+    assert seen == sorted((l, t) for l in range(L) for t in range(T))
 
 
 @pytest.mark.parametrize("N", [16384, 16388, 20012])
