@@ -505,12 +505,14 @@ def precision_study(passes: int = 1000, N: int = 1 << 22, seed: int = 3):
     return res
 
 
-def n8_bench(steps: int = 2000, warmup: int = 5, N: int = 1 << 23, frac: float = 0.5) -> dict:
+def n8_bench(steps: int = 2000, warmup: int = 5, N: int = 1 << 23, frac: float = 0.5, variant: int = 0,
+             parity: bool = True) -> dict:
     """n = 8 (A = J/4 - I) on the same 2^26-value pool as the default line
     (N = 2^23, seed 7, frac = 1/2): `steps` back-to-back passes, one step =
-    one pass (the 315-lane bulk-copy kernel, plus the returned values'
-    streaming kernel for pools over 64 MB).  First, one pass is compared with
-    the oracle element by element (returned values and pool)."""
+    one pass (AUTO: the 315-lane bulk-copy pass on clusters of two CTAs for
+    pools over 64 MB, plus the returned values' streaming kernel).  First,
+    one pass is compared with the oracle element by element (returned values
+    and pool)."""
     import numpy as np
     import torch
     from oracle import py_oracle as orc
@@ -518,15 +520,19 @@ def n8_bench(steps: int = 2000, warmup: int = 5, N: int = 1 << 23, frac: float =
     n = 8
     stream = torch.cuda.Stream()
     g = W.Wallace(n, N, SEED, frac, stream=stream)
-    o = orc.Generator(n, N, SEED, frac)
+    g.set_variant(variant)
     out = torch.empty(g.R, dtype=torch.float32, device="cuda")
-    with torch.cuda.stream(stream):
-        g.fill(out)
-    got = out.cpu().numpy()
-    ref = o.fill(g.R)
-    parity = bool(np.array_equal(got.view(np.uint32), ref.view(np.uint32)) and
-                  np.array_equal(g.pool().view(np.uint32), o.pool32().view(np.uint32)))
-    o.close()
+    if parity:
+        o = orc.Generator(n, N, SEED, frac)
+        with torch.cuda.stream(stream):
+            g.fill(out)
+        got = out.cpu().numpy()
+        ref = o.fill(g.R)
+        parity = bool(np.array_equal(got.view(np.uint32), ref.view(np.uint32)) and
+                      np.array_equal(g.pool().view(np.uint32), o.pool32().view(np.uint32)))
+        o.close()
+    else:
+        parity = None
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             g.fill(out)
@@ -1110,6 +1116,13 @@ def main():
     ap.add_argument("--l2-n", type=int, default=4, help="with --l2: sub-vectors (4 or 8)")
     ap.add_argument("--l2-sizes", default="14-21",
                     help="with --l2: log2 of nu / 4, a range a-b or a comma-separated list")
+    ap.add_argument("--n8", action="store_true",
+                    help="n = 8 pass alone (A = J/4 - I, seed 7, frac = 1/2)")
+    ap.add_argument("--n8-log2N", type=int, default=23, help="with --n8: N = 2^k")
+    ap.add_argument("--n8-variant", default="auto", choices=["auto", "tiled_tma", "tiled_cluster"],
+                    help="with --n8: pass kernel")
+    ap.add_argument("--n8-steps", type=int, default=2000, help="with --n8: timed passes")
+    ap.add_argument("--n8-no-parity", action="store_true", help="with --n8: skip the first-pass oracle check")
     ap.add_argument("--no-extras", action="store_true",
                     help="default line only: skip the batched, serving, n = 8 and precision objects")
     ap.add_argument("--tune-cache", default=None,
@@ -1145,6 +1158,13 @@ def main():
         return
     if args.variants:
         variant_bench(steps=args.variants_steps)
+        return
+    if args.n8:
+        from paper_1004_3114_gb300 import wallace as W
+        var = {"auto": W.VARIANT_AUTO, "tiled_tma": W.VARIANT_TILED_TMA,
+               "tiled_cluster": W.VARIANT_TILED_CLUSTER}[args.n8_variant]
+        print(json.dumps(n8_bench(steps=args.n8_steps, N=1 << args.n8_log2N, variant=var,
+                                  parity=not args.n8_no_parity)), flush=True)
         return
     if args.serve:
         ticks = [None] if not args.serve_tick else [

@@ -77,15 +77,16 @@ typedef struct wallace wallace_t;
 #define WALLACE_VARIANT_TILED   2  /* lane-tiled gather staged in shared memory: the
                                       bulk-copy (TMA) pipeline when N % 4 == 0 and
                                       N is coprime to 15 (n = 4) or 105 (n = 8: 315
-                                      lanes; pools over 64 MB write the returned
-                                      values in a second, streaming kernel), else
-                                      per-thread 16-byte async copies (n = 4)        */
+                                      lanes; pools over 64 MB take the two-CTA
+                                      cluster form and write the returned values in
+                                      a second, streaming kernel), else per-thread
+                                      16-byte async copies (n = 4)                  */
 #define WALLACE_VARIANT_FUSED   3  /* whole pool in shared memory, many passes/launch   */
 #define WALLACE_VARIANT_TILED_ASYNC 4 /* lane-tiled, per-thread 16-byte async copies      */
 #define WALLACE_VARIANT_TILED_TMA   5 /* lane-tiled, warp-specialised bulk (TMA) copies
-                                         into a stage ring; needs N % 4 == 0 and N
-                                         coprime to 15 (n = 4; else the per-thread-copy
-                                         kernel runs) or to 105 (n = 8)                 */
+                                         into a stage ring, one CTA per tile; needs
+                                         N % 4 == 0 and N coprime to 15 (n = 4; else the
+                                         per-thread-copy kernel runs) or to 105 (n = 8) */
 #define WALLACE_VARIANT_TWOPHASE    6 /* binary32 pools the lane-tiled kernels cannot
                                          tile (n = 8 with N a multiple of 3, 5 or 7, or
                                          N % 4 != 0; n = 4 with 15 dividing N), and any

@@ -214,14 +214,16 @@ int launch_pass(wallace_t *h, void *out, int64_t w0, int64_t w1, double mu, doub
         if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_TMA) &&
             wl_tma_supported(h->n, h->N, fp64, h->sm_count))
             e = wl_launch_tma(a, h->sm_count, h->msigns, h->stream);
-        else if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_TMA) &&
-                 wl_tma8_supported(h->n, h->N, fp64)) {
-            e = wl_launch_tma8(a, h->sm_count, h->msigns, h->stream);
+        else if ((v == WALLACE_VARIANT_TILED_CLUSTER ||
+                  (v == WALLACE_VARIANT_TILED && wl_tma8c_preferred(h->n, h->N, fp64))) &&
+                 wl_tma8c_supported(h->n, h->N, fp64)) {
+            e = wl_launch_tma8c(a, h->sm_count, h->msigns, h->stream);
             if (wl_tma8_return_kernel(a))
                 h->launches++;   // the returned values' kernel
         }
-        else if (v == WALLACE_VARIANT_TILED_CLUSTER && wl_tma8c_supported(h->n, h->N, fp64)) {
-            e = wl_launch_tma8c(a, h->sm_count, h->msigns, h->stream);
+        else if ((v == WALLACE_VARIANT_TILED || v == WALLACE_VARIANT_TILED_TMA) &&
+                 wl_tma8_supported(h->n, h->N, fp64)) {
+            e = wl_launch_tma8(a, h->sm_count, h->msigns, h->stream);
             if (wl_tma8_return_kernel(a))
                 h->launches++;   // the returned values' kernel
         }

@@ -70,6 +70,8 @@ cudaError_t wl_launch_t8_return(const WlPassArgs &a, int sm_count, cudaStream_t 
 // a 315-lane x 16-lane-time tile (the same pools as wl_tma8_supported, when
 // a cluster of two fits the device); the grid is every resident cluster
 bool wl_tma8c_supported(int n, int64_t N, int fp64);
+// whether WALLACE_VARIANT_TILED (and AUTO) takes the cluster form for this pool
+bool wl_tma8c_preferred(int n, int64_t N, int fp64);
 int wl_tma8c_grid();
 cudaError_t wl_launch_tma8c(const WlPassArgs &a, int sm_count, int signs, cudaStream_t stream);
 

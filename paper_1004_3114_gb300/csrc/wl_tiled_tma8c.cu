@@ -82,7 +82,8 @@
 static_assert(C8_SMEM_BYTES <= 227 * 1024 - 2048, "stage ring exceeds shared memory");
 static_assert((C8_SW * 4) % 128 == 0, "stages must stay 128-byte aligned");
 static_assert(32 * C8_PROD_WARPS * C8_KS >= C8_MAXSPANS, "producer threads cannot hold every span");
-static_assert(C8_T == 16, "a thread takes lane times t and t + 8");
+static_assert(C8_T == 16, "a half-warp takes a lane's 16 lane times");
+#define T8C_PREFER_BYTES (64ll << 20)
 
 namespace {
 
@@ -695,6 +696,14 @@ bool wl_tma8c_supported(int n, int64_t N, int fp64)
         if (c8_configure(w) <= 0)
             return false;
     return true;
+}
+
+bool wl_tma8c_preferred(int n, int64_t N, int fp64)
+{
+    // pools whose returned values go to the streaming kernel (over 64 MB):
+    // there the cluster pass measured 2-10% faster than the one-CTA pass;
+    // below, with the returned values in the pass, they tie
+    return n == 8 && !fp64 && (int64_t)sizeof(float) * 8 * N > T8C_PREFER_BYTES;
 }
 
 int wl_tma8c_grid()

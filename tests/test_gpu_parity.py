@@ -212,14 +212,15 @@ def test_twophase_pass_bit_exact(orc, n, N, frac, variant, mode):
     ((1 << 21) + 32, 0.5, 19),  # 32 * 65537: a 64 MB+ pool, returned values from a second kernel
     ((1 << 21) + 32, 0.3, 23),
 ])
-@pytest.mark.parametrize("variant", [W.VARIANT_TILED, W.VARIANT_TILED_CLUSTER])
+@pytest.mark.parametrize("variant", [W.VARIANT_TILED_TMA, W.VARIANT_TILED_CLUSTER, W.VARIANT_TILED])
 def test_tma8_pass_bit_exact(orc, N, frac, seed, variant):
-    """n = 8 with N coprime to 105: every pass has 315 lanes, and the tiled
-    variant runs the bulk-copy lane-tiled kernel, the cluster variant its
+    """n = 8 with N coprime to 105: every pass has 315 lanes; the TMA variant
+    runs the one-CTA bulk-copy lane-tiled kernel, the cluster variant its
     two-CTA form (tiles of 16 lane times, half-sums exchanged through
-    distributed shared memory); pools over 64 MB then take the returned
-    values' kernel.  Pools, returned values and state scalars against the
-    oracle, pass by pass, then fills that start mid-pass."""
+    distributed shared memory), and the tiled variant the cluster form for
+    pools over 64 MB, else the one-CTA kernel; pools over 64 MB then take the
+    returned values' kernel.  Pools, returned values and state scalars
+    against the oracle, pass by pass, then fills that start mid-pass."""
     g = W.Wallace(8, N, seed, frac)
     g.set_variant(variant)
     o = orc.Generator(8, N, seed, frac)
