@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(BT_THREADS, 3) batch_kernel(BatchArgs a)
 }
 
 // The same work with the CTA-local bulk-copy runner for the pools it takes
-// (wl_tma_run_eligible: n = 4, N >= TM_MIN_N): one CTA of TM_THREADS threads
+// (wl_tma_run_eligible: n = 4, N >= TR_MIN_N): one CTA of TM_THREADS threads
 // per SM; the other pools as in batch_kernel.
 // SG: the batch's generators draw a sign pattern each pass (matrix A D_k)
 template <bool SG>

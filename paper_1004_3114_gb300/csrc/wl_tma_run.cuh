@@ -4,7 +4,7 @@
 // ring as the grid-wide kernel (wl_tiled_tma.cu) -- 4 producer warps issue
 // one bulk copy per span into TR_STAGES shared-memory stages, 15 consumer
 // warps own whole lanes (T >= TR_LANE_MIN_T) or take (lane, time) pairs --
-// but over all tiles of the pool in order, for any N >= TM_MIN_N and lane
+// but over all tiles of the pool in order, for any N >= TR_MIN_N and lane
 // counts up to TR_LMAX, with the sum of squares and the chi-squared rescale
 // (Eq. 3 of Brent's RANN4 paper) done by the CTA itself (wl_end_pass_cta),
 // so no CTA waits for another.
@@ -21,7 +21,7 @@
 #include "wl_run_body.cuh"
 #include "wl_tma_common.cuh"
 
-// Ring shape: two stages of up to TR_ETARGET values per sub-vector.  Longer
+// Ring shape: TR_STAGES stages of up to TR_ETARGET values per sub-vector.  Longer
 // tiles than the grid-wide kernel's (2880 in three stages) give lane counts
 // above 45 lanes of at least 24 values (L <= 220), hence whole-lane
 // consumers and fewer, longer bulk copies; the whole shared-memory block
@@ -29,7 +29,7 @@
 #ifndef TR_STAGES
 #define TR_STAGES 2
 #endif
-static_assert(TR_STAGES == 2, "the runner's ring alternates two stages (or uses them as one)");
+static_assert(TR_STAGES >= 2 && TR_STAGES <= 4, "the runner's ring rotates 2 to 4 stages (or uses them as one)");
 #ifndef TR_ETARGET
 #define TR_ETARGET 5280  /* values per sub-vector per tile: L T <= this */
 #endif
@@ -91,13 +91,19 @@ __host__ __device__ constexpr size_t tr_smem_bytes()
 
 } // namespace wl_tma
 
-// Pools the bulk-copy runner takes: n = 4 and N in [TM_MIN_N, 2^28] (32-bit
-// lane, span and slot offsets; a span of at most TR_ETARGET values wraps at
-// most once).  A pass whose strides have lcm above TR_LMAX runs the plain
-// gather instead.  Other pools take the per-thread runners.
+// Pools the bulk-copy runner takes: n = 4 and N in [TR_MIN_N, 2^28] (32-bit
+// lane, span and slot offsets; a span of alpha T <= N values wraps at most
+// once: wl_run_tma caps T at N / max alpha, which binds only below 16384).
+// A pass whose strides have lcm above TR_LMAX runs the plain gather instead.
+// Other pools take the per-thread runners.  From 4096 on the runner beat the
+// per-thread path (pools of 2^8 to 2^14, frac = 1: 0.0738 against 0.0945 ms
+// per batched pass; 2048 timed the same).
+#ifndef TR_MIN_N
+#define TR_MIN_N 4096
+#endif
 __host__ __device__ inline bool wl_tma_run_eligible(int n, int64_t N)
 {
-    return n == 4 && N >= TM_MIN_N && N <= ((int64_t)1 << 28);
+    return n == 4 && N >= TR_MIN_N && N <= ((int64_t)1 << 28);
 }
 
 // Lane tables of one pass into `tab` (a tr_common_words() area): J[L + 1]
@@ -227,7 +233,10 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
     // this CTA's kt-th tile (tile0 + kt tstep) uses stage kt % S for the
     // (uses[s] + kt / S)-th time
     const int nmine = ntiles > tile0 ? (ntiles - tile0 + tstep - 1) / tstep : 0;
-    const int use0 = ring.uses[0], use1 = TR_STAGES > 1 ? ring.uses[TR_STAGES - 1] : 0;
+    int use[TR_STAGES];
+#pragma unroll
+    for (int q = 0; q < TR_STAGES; q++)
+        use[q] = ring.uses[q];
     const int N4 = (N32 + 3) & ~3;
 
     if (warp >= TM_CONS_WARPS) {
@@ -268,7 +277,12 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                 issued[q] = 0;
             for (int kt = 0; kt < nmine; kt++) {
                 const int tile = tile0 + kt * tstep;
-                const int s = S == 1 ? 0 : kt & 1, u = (s == 0 ? use0 : use1) + (S == 1 ? kt : kt >> 1);
+                const int s = S == 1 ? 0 : kt % TR_STAGES;
+                int u = use[0];
+#pragma unroll
+                for (int q = 1; q < TR_STAGES; q++)
+                    u = s == q ? use[q] : u;   // (constant indices: no local memory)
+                u += S == 1 ? kt : kt / TR_STAGES;
                 if (*ring.abort_flag)
                     break;
                 if (u > 0 && !mbar_wait(smem_u32(&ring.empty[s]), (uint32_t)((u - 1) & 1))) {
@@ -330,10 +344,10 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
                     }
                 }
                 mbar_arrive(full);
-                if (s == 0)
-                    issued[0] = u + 1;
-                else
-                    issued[TR_STAGES - 1] = u + 1;
+#pragma unroll
+                for (int q = 0; q < TR_STAGES; q++)
+                    if (s == q)
+                        issued[q] = u + 1;
             }
             if (*ring.abort_flag) {
                 // copies still in flight must land before the CTA moves on
@@ -380,7 +394,12 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         {
             for (int kt = 0; kt < nmine; kt++) {
                 const int tile = tile0 + kt * tstep;
-                const int s = S == 1 ? 0 : kt & 1, u = (s == 0 ? use0 : use1) + (S == 1 ? kt : kt >> 1);
+                const int s = S == 1 ? 0 : kt % TR_STAGES;
+                int u = use[0];
+#pragma unroll
+                for (int q = 1; q < TR_STAGES; q++)
+                    u = s == q ? use[q] : u;
+                u += S == 1 ? kt : kt / TR_STAGES;
                 if (*ring.abort_flag)
                     break;
                 if (!mbar_wait(smem_u32(&ring.full[s]), (uint32_t)(u & 1))) {
@@ -501,9 +520,10 @@ __device__ inline void wl_tma_pass_cta(const float *src, float *dst, int64_t N, 
         asm volatile("fence.proxy.async.global;\n" ::: "memory");
     }
     // the uses every thread counted, the same in all of them
-    ring.uses[0] = use0 + (S == 1 ? nmine : (nmine + 1) >> 1);
-    if (S > 1)
-        ring.uses[TR_STAGES - 1] = use1 + (nmine >> 1);
+    // stage q served the tiles kt = q, q + S, ... of this pass
+#pragma unroll
+    for (int q = 0; q < TR_STAGES; q++)
+        ring.uses[q] = use[q] + (q < S ? (nmine + S - 1 - q) / S : 0);
 }
 
 // out[q] = mu + sigma pool[q] for q < w1 (logical positions; rows of N at
@@ -567,11 +587,14 @@ __device__ inline int wl_run_tma(const WlRunSpec &d, float *smem, uint64_t *red,
         uint32_t bad = 0;
         const int L = wl_lcm4(alpha);
         const bool tma = L <= TR_LMAX && !*ring.abort_flag;
+        // a span of a tile holds alpha T values: at most N, so it wraps at most once
+        const int amax = max(max(alpha[0], alpha[1]), max(alpha[2], alpha[3]));
+        const int tcap = max(1, (int)(N / amax));
         // the plain gather below writes its returned values itself
         const bool copy_back = tma && L >= TR_RETURN_COPY_L && o && w1 > 0;
         if (tma) {
             wl_tma_pass_cta<SG>(src, dst, N, d.Np, L, alpha, gam, c, copy_back ? nullptr : o, copy_back ? 0 : w1,
-                                d.mu, d.sigma, smem, ring, d.st, lo, hi, bad, 0, 1, 1 << 30, nullptr,
+                                d.mu, d.sigma, smem, ring, d.st, lo, hi, bad, 0, 1, tcap, nullptr,
                                 st->next.signs);
         } else {
             WlTileJob job;

@@ -78,6 +78,22 @@ def test_batch_bulk_runner_any_n_and_lane_count(orc, tuning):
     _check_batch(orc, b, Ns, seeds, 0.5, 4, runs=[2, 3], mu=-1.0, sigma=0.5)
 
 
+@pytest.mark.parametrize("tuning", [(0, 2560, 2048), (2, 2560, 2048)])
+def test_batch_bulk_runner_small_pools(orc, tuning):
+    """The bulk-copy runner below N = 16384, where a tile's span of alpha T
+    values would exceed N: T is capped at N / max alpha (4096 at 45 lanes: T
+    91 of 117; 4098, divisors of 175: T 23, the (lane, time) pair path;
+    10005 = 3 5 23 29, 539 lanes: T 18), every residue mod 4, the 63-lane and
+    153-lane (5005 = 5 7 11 13: p = 3, q = 17) sets and a plain-gather set
+    (8190, lcm 2057).  The per-thread runner on the same pools gives the same
+    streams."""
+    Ns = [4096, 4099, 4098, 5005, 6010, 8190, 10005, 12289, 4100]
+    seeds = [31, 32, 33, 34, 35, 36, 37, 38, 39]
+    b = W.Batch(4, Ns, seeds, 1.0)
+    b.set_tuning(*tuning)
+    _check_batch(orc, b, Ns, seeds, 1.0, 4, runs=[2, 3], mu=0.5, sigma=2.0)
+
+
 def test_batch_n8(orc):
     Ns = [128, 1000, 3000, 9000]
     seeds = [1, 2, 3, 4]
