@@ -1063,7 +1063,7 @@ def serve_bench(n_clients: int = 10_000, n_requests: int = 20_000, rate: float =
                      "unit": "GB/s", "frac": bytes_moved / st.elapsed_s / 1e9 / peak, "peak_kind": kind,
                      "bytes_per_value": 28},
         "passes_per_tick": passes_per_tick, "ctas_per_sm": ctas_per_sm, "tick": tick,
-        "runner": "bulk-copy for one-CTA requests on 16384 <= N (n=4)" if ctas_per_sm == 0
+        "runner": "bulk-copy for one-CTA requests on 4096 <= N (n=4)" if ctas_per_sm == 0
                   else "async-copy", "create_s": create_s, "sampled_parity": parity,
         "status": int(st.status)}
 
