@@ -227,6 +227,111 @@ cudaError_t wl_launch_gather(const WlPassArgs &a, int fp64, int sm_count, cudaSt
     return cudaGetLastError();
 }
 
+// Phase 2 of the two-phase pass for binary32 pools: the transform streamed
+// over the j-ordered copy, four consecutive j per thread (16-byte loads and
+// stores: the copy's and the pool's rows start on 256-byte boundaries), the
+// returned values as 16-byte stores where a row's output offset is a multiple
+// of 4, and the exact sum of squares of the four tuples added into 128 bits
+// once.  The same arithmetic, in the same order, as gather_kernel<NSUB,
+// float, true>.
+template <int NSUB>
+__global__ void __launch_bounds__(256) stream_kernel(WlPassArgs a)
+{
+    __shared__ uint64_t red[3 * 8];
+    WlDevState *st = a.st;
+    const float *__restrict__ src = (const float *)a.src;
+    float *__restrict__ dst = (float *)a.dst;
+    const int64_t N = a.N, Np = a.Np, w0 = a.w0, w1 = a.w1;
+    const float c = st->next.c32, rC = st->next.rc32, rS = st->next.rs32;
+    const uint32_t signs = st->next.signs;
+    float *out = (float *)a.out;
+    const float mu = (float)a.mu, sigma = (float)a.sigma;
+    // row k's returned values: j in [r0[k], r1[k]) go to out[ofs[k] + j],
+    // 16 bytes at a time when vec[k] (kept in shared memory: registers go to
+    // the values)
+    __shared__ int64_t r0[NSUB], r1[NSUB], ofs[NSUB];
+    __shared__ bool vec[NSUB];
+    if (threadIdx.x < NSUB) {
+        const int k = threadIdx.x;
+        r0[k] = max((int64_t)0, min(N, w0 - k * N));
+        r1[k] = max(r0[k], min(N, w1 - k * N));
+        ofs[k] = k * N - w0;
+        vec[k] = ((ofs[k] & 3) == 0) && out != nullptr && (((uintptr_t)out & 15) == 0);
+    }
+    __syncthreads();
+    uint64_t lo = 0, hi = 0;
+    uint32_t bad = 0;
+    const int64_t N4 = N & ~(int64_t)3;
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    auto xform = [&](const float *g, float *y) {
+        if constexpr (NSUB == 2)
+            wl_xform2(g, rC, rS, y);
+        else if constexpr (NSUB == 4)
+            wl_xform4(g, c, y);
+        else
+            wl_xform8(g, c, y);
+    };
+    for (int64_t j = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); j < N4; j += 4 * G) {
+        float4 g4[NSUB];
+#pragma unroll
+        for (int i = 0; i < NSUB; i++)
+            g4[i] = *(const float4 *)(src + i * Np + j);
+        float y[4][NSUB];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            float g[NSUB];
+#pragma unroll
+            for (int i = 0; i < NSUB; i++) {
+                const float v = u == 0 ? g4[i].x : u == 1 ? g4[i].y : u == 2 ? g4[i].z : g4[i].w;
+                g[i] = wl_sgn(v, signs, i);
+            }
+            xform(g, y[u]);
+        }
+        uint64_t t = 0;   // 4 NSUB terms, each below 2^48
+#pragma unroll
+        for (int k = 0; k < NSUB; k++) {
+            *(float4 *)(dst + k * Np + j) = make_float4(y[0][k], y[1][k], y[2][k], y[3][k]);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                t += wl_term32(y[u][k], bad);
+            if (j + 4 <= r0[k] || j >= r1[k])
+                continue;
+            if (vec[k] && j >= r0[k] && j + 4 <= r1[k]) {
+                *(float4 *)(out + ofs[k] + j) =
+                    make_float4(__fadd_rn(mu, __fmul_rn(sigma, y[0][k])), __fadd_rn(mu, __fmul_rn(sigma, y[1][k])),
+                                __fadd_rn(mu, __fmul_rn(sigma, y[2][k])), __fadd_rn(mu, __fmul_rn(sigma, y[3][k])));
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (j + u >= r0[k] && j + u < r1[k])
+                        out[ofs[k] + j + u] = __fadd_rn(mu, __fmul_rn(sigma, y[u][k]));
+            }
+        }
+        wl_add128(lo, hi, t, 0);
+    }
+    // the last N mod 4 values, one thread each
+    const int64_t jt = N4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (jt < N) {
+        float g[NSUB], y[NSUB];
+#pragma unroll
+        for (int i = 0; i < NSUB; i++)
+            g[i] = wl_sgn(src[i * Np + jt], signs, i);
+        xform(g, y);
+#pragma unroll
+        for (int k = 0; k < NSUB; k++) {
+            dst[k * Np + jt] = y[k];
+            wl_add128(lo, hi, wl_term32(y[k], bad), 0);
+            if (jt >= r0[k] && jt < r1[k])
+                out[ofs[k] + jt] = __fadd_rn(mu, __fmul_rn(sigma, y[k]));
+        }
+    }
+    wl_cta_reduce_to_state(lo, hi, bad, st, red);
+    if (wl_last_cta(st) && threadIdx.x == 0) {
+        double x = (double)__ldcg(&dst[wl_phys(a.nu - 1, N, Np)]);
+        wl_finalise(st, a.n, N, a.nu, x, false, WL_FIN_PASS);
+    }
+}
+
 // Two-phase pass: every sub-vector un-strided into `scratch` (same layout as
 // a pool), then the transform streamed over j.
 template <int NSUB, typename T>
@@ -249,10 +354,18 @@ static cudaError_t launch_twophase(const WlPassArgs &a, void *scratch, int sm_co
         return e;
     WlPassArgs b = a;
     b.src = scratch;
-    int64_t want = (a.N + 255) / 256;
-    int64_t cap = (int64_t)sm_count * 8;
-    int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    gather_kernel<NSUB, T, true><<<grid, 256, 0, stream>>>(b);
+    if constexpr (sizeof(T) == 4) {
+        // four j per thread
+        const int64_t want = (a.N / 4 + 255) / 256;
+        const int64_t cap = (int64_t)sm_count * 8;
+        const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+        stream_kernel<NSUB><<<grid, 256, 0, stream>>>(b);
+    } else {
+        int64_t want = (a.N + 255) / 256;
+        int64_t cap = (int64_t)sm_count * 8;
+        int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+        gather_kernel<NSUB, T, true><<<grid, 256, 0, stream>>>(b);
+    }
     return cudaGetLastError();
 }
 
