@@ -1119,7 +1119,7 @@ def main():
     ap.add_argument("--n8", action="store_true",
                     help="n = 8 pass alone (A = J/4 - I, seed 7, frac = 1/2)")
     ap.add_argument("--n8-log2N", type=int, default=23, help="with --n8: N = 2^k")
-    ap.add_argument("--n8-variant", default="auto", choices=["auto", "tiled_tma", "tiled_cluster"],
+    ap.add_argument("--n8-variant", default="auto", choices=["auto", "tiled_tma", "tiled_cluster", "twophase"],
                     help="with --n8: pass kernel")
     ap.add_argument("--n8-steps", type=int, default=2000, help="with --n8: timed passes")
     ap.add_argument("--n8-no-parity", action="store_true", help="with --n8: skip the first-pass oracle check")
@@ -1162,7 +1162,7 @@ def main():
     if args.n8:
         from paper_1004_3114_gb300 import wallace as W
         var = {"auto": W.VARIANT_AUTO, "tiled_tma": W.VARIANT_TILED_TMA,
-               "tiled_cluster": W.VARIANT_TILED_CLUSTER}[args.n8_variant]
+               "tiled_cluster": W.VARIANT_TILED_CLUSTER, "twophase": W.VARIANT_TWOPHASE}[args.n8_variant]
         print(json.dumps(n8_bench(steps=args.n8_steps, N=1 << args.n8_log2N, variant=var,
                                   parity=not args.n8_no_parity)), flush=True)
         return

@@ -172,12 +172,15 @@ __global__ void __launch_bounds__(US_THREADS) unstride_kernel(const T *__restric
         T *out = tmp + (int64_t)i * Np;
         const int nch = (Tt + 255) >> 8;
         const int items = (int)al * nch;
-        const int64_t q = N / al, rm = N - q * al;
+        // 32-bit lane arithmetic: N < 2^31 and l rm < alpha^2 <= 2^28 (a
+        // 64-bit division costs several times a 32-bit one here)
+        const int al32 = (int)al, N32 = (int)N;
+        const int q = N32 / al32, rm = N32 - q * al32;
         for (int it = warp; it < items; it += US_THREADS / 32) {
             const int l = it / nch, ch = it - l * nch;
             // J_l = l q + ceil(l rm / al); lane length J_{l+1} - J_l
-            const int64_t Jl = (int64_t)l * q + ((int64_t)l * rm + al - 1) / al;
-            const int64_t Jn = (int64_t)(l + 1) * q + ((int64_t)(l + 1) * rm + al - 1) / al;
+            const int64_t Jl = (int64_t)l * q + (l * rm + al32 - 1) / al32;
+            const int64_t Jn = (int64_t)(l + 1) * q + ((l + 1) * rm + al32 - 1) / al32;
             const int rl = (int)(al * Jl - (int64_t)l * N);
             const int tend = (int)min((int64_t)min(Tt, (ch + 1) << 8), Jn - Jl - t0);
             for (int t = (ch << 8) + lane; t < tend; t += 32)
