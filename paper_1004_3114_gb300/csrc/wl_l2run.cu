@@ -159,6 +159,11 @@ __global__ void __launch_bounds__(L2_THREADS, 2) l2run_kernel(L2Args a)
     const uint32_t gt = (uint32_t)b * blockDim.x + tid, GT = (uint32_t)G * blockDim.x;
     const float mu = a.mu, sigma = a.sigma;
     int cur = a.cur;
+    // passes completed before this launch: pass p of the launch is pass k0 + p,
+    // and its strides sit in ahead[(k0 + p) & 1] from the end of the pass before
+    const int64_t k0 = st->passes;
+    float pg[NSUB];      // the thread's first tuple of the pass, loaded during the last end of pass
+    bool pre = false;
     for (int64_t p = 0; p < a.passes; p++) {
         // this pass's parameters become the most recent pass's (warp 0, word
         // by word; nothing reads `last` during the pass)
@@ -188,12 +193,13 @@ __global__ void __launch_bounds__(L2_THREADS, 2) l2run_kernel(L2Args a)
             float g[NSUB], y[NSUB];
 #pragma unroll
             for (int i = 0; i < NSUB; i++) {
-                g[i] = __ldcg(src + i * Np + idx[i]);
+                g[i] = pre ? pg[i] : __ldcg(src + i * Np + idx[i]);
                 if (SG)
                     g[i] = wl_sgn(g[i], signs, i);
                 idx[i] += stp[i];
                 idx[i] -= idx[i] >= N ? N : 0u;
             }
+            pre = false;
             if constexpr (NSUB == 4)
                 wl_xform4(g, c, y);
             else
@@ -219,6 +225,20 @@ __global__ void __launch_bounds__(L2_THREADS, 2) l2run_kernel(L2Args a)
         l2_arrive(sy);
         if (!l2_wait(sy, (unsigned int)((p + 1) * G)))
             break;
+        // the next pass's first tuple of this thread, loaded now so that its
+        // latency passes during the end of pass: the next pass's strides were
+        // drawn a pass ahead (ahead[(k + 1) & 1], which the stride role below
+        // copies but does not write) and its pool is this pass's, complete at
+        // the barrier; only the scale waits for the end of pass
+        if (p + 1 < a.passes && gt < N && tid >= 96) {   // not the warps of the end-of-pass roles
+            const WlStrides &nx = st->ahead[(k0 + p + 1) & 1];
+#pragma unroll
+            for (int i = 0; i < NSUB; i++) {
+                const uint32_t al = (uint32_t)nx.alpha[i], ga = (uint32_t)nx.gamma[i];
+                pg[i] = __ldcg(dst + i * Np + (al * gt + ga) % N);
+            }
+            pre = true;
+        }
         // end of pass from the summed Q: scale (thread 0), strides (32),
         // drift (64), each reading Q and the withheld value together
         if (tid == 0 || tid == 64) {
