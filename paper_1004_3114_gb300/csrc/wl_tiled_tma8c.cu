@@ -42,9 +42,10 @@
 // (4-byte st.async counted on each CTA's slot barrier, whose expected bytes
 // each CTA's producer posts).  Slot q is written again only for iteration
 // k + 4, after every warp of CTA 1 has passed iteration k + 1 (the half-sum
-// exchange keeps the CTAs' warps within one tile of each other).  The sum of squares goes to
-// the generator's accumulators from both CTAs and the last CTA of the grid
-// (by ticket) runs the end of pass, as in the other pass kernels.  Every wait
+// exchange keeps the CTAs' warps within one tile of each other).  The sum of
+// squares goes to the generator's accumulators from both CTAs and the last
+// CTA of the grid (by ticket) runs the end of pass, as in the other pass
+// kernels.  Every wait
 // on an mbarrier is bounded (about a second): on expiry the CTA records
 // WALLACE_ETIMEOUT, stops, waits (bounded) for its own bulk copies in flight,
 // and reaches the final cluster barrier, which every path reaches, so
