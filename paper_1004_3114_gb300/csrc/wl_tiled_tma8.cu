@@ -55,7 +55,9 @@
 // pools above this size leave the returned values to a streaming kernel
 // after the pass; smaller ones stay in L2, where the half-sector stores of
 // a lane's 8-value runs merge cheaply
+#ifndef T8_RETURN_KERNEL_BYTES
 #define T8_RETURN_KERNEL_BYTES (64ll << 20)
+#endif
 
 static_assert(T8_SMEM_BYTES <= 227 * 1024 - 2048, "stage ring exceeds shared memory");
 static_assert((T8_SW * 4) % 128 == 0, "stages must stay 128-byte aligned");
