@@ -35,113 +35,24 @@
 #include <stdint.h>
 
 #include "wl_common.cuh"
+#include "wl_gridsync.cuh"
 #include "wl_launch.h"
 
 #define L2_THREADS 512
-#define L2_WAIT_CYCLES 2000000000ll   /* about one second */
 
 namespace {
-
-struct L2Acc {
-    alignas(128) unsigned long long a0, a1, a2;   // Q limbs: bits 0-31, 32-63, 64-127 of CTA sums
-    unsigned int bad;
-};
-
-// Device scratch of one launch (zeroed by the host before it).
-struct L2Sync {
-    alignas(128) unsigned int arrived;   // barrier arrivals so far
-    alignas(128) int abort;              // a CTA gave up waiting
-    L2Acc acc[3];                        // sum of squares of pass p in set p mod 3
-};
 
 struct L2Args {
     float *buf[2];
     int cur;
     WlDevState *st;
-    L2Sync *sy;
+    WlGridSync *sy;
     int64_t N, Np, R;
     int64_t passes;
     float *out;           // pass p writes its first take values to out + p R (may be null)
     int64_t last_take;    // values the last pass returns (the others return R)
     float mu, sigma;
 };
-
-__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
-{
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Arrival at the grid barrier (thread 0, after a CTA barrier that follows
-// the CTA's writes of the pass): its release publishes them.
-__device__ __forceinline__ void l2_arrive(L2Sync *sy)
-{
-    if (threadIdx.x == 0)
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(&sy->arrived) : "memory");
-}
-
-// Bounded wait for `target` arrivals: true when every CTA has arrived, false
-// when the wait gave up or another CTA did.  Every thread calls.
-__device__ bool l2_wait(L2Sync *sy, unsigned int target)
-{
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        const long long t0 = clock64();
-        int ok = 1;
-        while (ld_acquire_u32(&sy->arrived) < target) {
-            if (*(volatile int *)&sy->abort || clock64() - t0 > L2_WAIT_CYCLES) {
-                ok = 0;
-                atomicExch(&sy->abort, 1);
-                break;
-            }
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// CTA sum of (lo, hi, bad) into one accumulator set (every thread calls).
-__device__ void l2_reduce_to(uint64_t lo, uint64_t hi, uint32_t bad, L2Acc *acc, uint64_t *red)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const uint64_t olo = __shfl_down_sync(0xffffffffu, lo, off);
-        const uint64_t ohi = __shfl_down_sync(0xffffffffu, hi, off);
-        wl_add128(lo, hi, olo, ohi);
-    }
-    bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) {
-        red[warp] = lo;
-        red[nw + warp] = hi;
-        red[2 * nw + warp] = bad;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        lo = lane < nw ? red[lane] : 0ull;
-        hi = lane < nw ? red[nw + lane] : 0ull;
-        bad = lane < nw ? (uint32_t)red[2 * nw + lane] : 0u;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const uint64_t olo = __shfl_down_sync(0xffffffffu, lo, off);
-            const uint64_t ohi = __shfl_down_sync(0xffffffffu, hi, off);
-            wl_add128(lo, hi, olo, ohi);
-        }
-        bad = __any_sync(0xffffffffu, bad) ? 1u : 0u;
-        if (lane == 0) {
-            atomicAdd(&acc->a0, (unsigned long long)(lo & 0xffffffffull));
-            atomicAdd(&acc->a1, (unsigned long long)(lo >> 32));
-            if (hi)
-                atomicAdd(&acc->a2, (unsigned long long)hi);
-            if (bad)
-                atomicOr(&acc->bad, 1u);
-        }
-    }
-    __syncthreads();
-}
-
 
 // SG: the generator draws a sign pattern each pass (matrix A D_k).
 template <int NSUB, bool SG>
@@ -151,7 +62,7 @@ __global__ void __launch_bounds__(L2_THREADS, 2) l2run_kernel(L2Args a)
     __shared__ WlDevState sst;   // this CTA's copy of the generator's state
     wl_state_load(&sst, a.st);
     WlDevState *st = &sst;
-    L2Sync *sy = a.sy;
+    WlGridSync *sy = a.sy;
     const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
     const uint32_t N = (uint32_t)a.N;
     const int64_t Np = a.Np, nu = NSUB * a.N;
@@ -213,17 +124,17 @@ __global__ void __launch_bounds__(L2_THREADS, 2) l2run_kernel(L2Args a)
                     o[q] = __fadd_rn(mu, __fmul_rn(sigma, y[k]));
             }
         }
-        L2Acc *acc = &sy->acc[p % 3];
-        l2_reduce_to(lo, hi, bad, acc, red);
+        WlGridAcc *acc = &sy->acc[p % 3];
+        wl_grid_reduce_to(lo, hi, bad, acc, red);
         if (b == 0 && tid == 0) {
-            L2Acc *nx = &sy->acc[(p + 1) % 3];
+            WlGridAcc *nx = &sy->acc[(p + 1) % 3];
             nx->a0 = 0;
             nx->a1 = 0;
             nx->a2 = 0;
             nx->bad = 0;
         }
-        l2_arrive(sy);
-        if (!l2_wait(sy, (unsigned int)((p + 1) * G)))
+        wl_grid_arrive(sy);
+        if (!wl_grid_wait(sy, (unsigned int)((p + 1) * G)))
             break;
         // the next pass's first tuple of this thread, loaded now so that its
         // latency passes during the end of pass: the next pass's strides were
@@ -273,7 +184,7 @@ bool wl_l2run_supported(int n, int64_t N, int fp64, int64_t max_stride)
            (max_stride + 1) * N < ((int64_t)1 << 32);
 }
 
-size_t wl_l2run_sync_bytes() { return sizeof(L2Sync); }
+size_t wl_l2run_sync_bytes() { return sizeof(WlGridSync); }
 
 int wl_l2run_grid(int64_t nu, int sm_count)
 {
@@ -302,7 +213,7 @@ cudaError_t wl_launch_l2run(void *buf0, void *buf1, int cur, int n, int64_t N, i
     }
     if (grid > g_l2_max_grid)
         grid = g_l2_max_grid;
-    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(L2Sync), stream);
+    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(WlGridSync), stream);
     if (e != cudaSuccess)
         return e;
     L2Args a;
@@ -310,7 +221,7 @@ cudaError_t wl_launch_l2run(void *buf0, void *buf1, int cur, int n, int64_t N, i
     a.buf[1] = (float *)buf1;
     a.cur = cur;
     a.st = st;
-    a.sy = (L2Sync *)sync;
+    a.sy = (WlGridSync *)sync;
     a.N = N;
     a.Np = Np;
     a.R = R;
